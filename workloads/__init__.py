@@ -1,0 +1,134 @@
+"""Seeded synthetic inputs for the Yee + embedded-ROM scheme.
+
+This module only draws random numbers and lays out geometry: grids, per-cell
+materials, region placements, fine-region materials, source waveforms and
+probe positions.  It holds none of the scheme's arithmetic, and it is the only
+code that the FP64 oracle and the GPU library both consume.
+
+All generators use numpy ``Generator(PCG64(seed))`` with
+seed = 1609071140 + workload index unless a seed is given.  Units: metres,
+seconds, S/m, A/m^2.  Layout conventions: cell arrays are [ny][nx] (row j,
+column i); a source drives ``len`` consecutive E edges starting at edge
+(i, j) along the edge direction (comp 0 = Ex, 1 = Ey); a probe (i, j) reads
+Hz of coarse cell (i, j).
+
+The time step is part of a workload's recipe: a stated multiple of the 2D
+CFL limit 1/(c0 sqrt(1/dx^2 + 1/dy^2)) of the fine mesh (dx/r, dy/r).
+"""
+from __future__ import annotations
+
+import math
+import numpy as np
+
+SEED0 = 1609071140
+_C0 = 299792458.0   # exact speed of light in vacuum (m/s), for time-step recipes
+
+
+def rng_for(index: int, seed: int | None = None) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64(SEED0 + index if seed is None else seed))
+
+
+def fine_cfl(dx: float, dy: float, r: int) -> float:
+    """Recipe time step unit: the vacuum CFL limit of a mesh of dx/r x dy/r."""
+    return 1.0 / (_C0 * math.sqrt((r / dx) ** 2 + (r / dy) ** 2))
+
+
+def diff_gaussian(nsteps: int, dt: float, fc: float, t0_mult: float = 4.0) -> np.ndarray:
+    """Differentiated-Gaussian current density J(t) = -sqrt(2e) u exp(-u^2),
+    u = (t - t0)/tau, tau = 1/(sqrt(2) pi fc), t0 = t0_mult * tau; peak 1 A/m^2.
+    Sampled at t = (n + 1/2) dt, n = 0 .. nsteps-1 (FP64)."""
+    tau = 1.0 / (math.sqrt(2.0) * math.pi * fc)
+    t = (np.arange(nsteps) + 0.5) * dt
+    u = (t - t0_mult * tau) / tau
+    return -math.sqrt(2.0 * math.e) * u * np.exp(-u * u)
+
+
+def rect_fine(a, b, r, lo, hi, eps_in, sig_in):
+    """Fine-region materials [r*b][r*a]: vacuum with a rectangle of
+    (eps_in, sig_in) over fine cells [lo[0], hi[0]) x [lo[1], hi[1])."""
+    e = np.ones((r * b, r * a))
+    s = np.zeros((r * b, r * a))
+    e[lo[1]:hi[1], lo[0]:hi[0]] = eps_in
+    s[lo[1]:hi[1], lo[0]:hi[0]] = sig_in
+    return e, s
+
+
+def cavity_60(nsteps: int = 2000):
+    """60 x 60 PEC cavity, dx = dy = 1 mm, vacuum.  One 10 x 10-cell region at
+    [25, 35)^2 refined r = 3 (30 x 30 fine) holding a centred 12 x 12-fine-cell
+    block eps_r = 4, sigma = 0.01 S/m; ROM order 60.  A differentiated-Gaussian
+    Jy current (fc = 30 GHz) on the Ey edge at (15, 30); Hz probes at (45, 30)
+    and (30, 45); dt = 0.9 x the fine-mesh CFL limit."""
+    nx = ny = 60
+    dx = dy = 1e-3
+    r = 3
+    dt = 0.9 * fine_cfl(dx, dy, r)
+    ef, sf = rect_fine(10, 10, r, (9, 9), (21, 21), 4.0, 0.01)
+    return dict(
+        name="cavity_60", nx=nx, ny=ny, dx=dx, dy=dy, dt=dt,
+        eps_r=np.ones((ny, nx)), sigma=np.zeros((ny, nx)),
+        roms=[dict(i0=25, j0=25, a=10, b=10, r=r, eps_r=ef, sigma=sf, q=60, f0=30e9)],
+        sources=[dict(comp=1, i=15, j=30, len=1, wave=diff_gaussian(nsteps, dt, 30e9))],
+        probes=[(45, 30), (30, 45)], nsteps=nsteps)
+
+
+def random_grid(index, nx, ny, n_regions, a, r, q, nsteps, dt_factor=0.95, fc=30e9,
+                n_probes=16, eps_range=(1.0, 4.0), sig_range=(0.0, 0.02), seed=None,
+                inclusion=True, margin=2):
+    """Inhomogeneous lossy grid with seeded non-overlapping a x a regions.
+
+    eps_r ~ U[eps_range], sigma ~ U[sig_range] per coarse cell.  Each region
+    holds a seeded rectangular inclusion (side U[a*r/4, a*r) fine cells,
+    eps_r ~ U[2, 10], sigma ~ U[0.01, 0.1]).  Regions keep `margin` coarse
+    cells from the walls and from each other.  One Jy point source and
+    n_probes Hz probes are placed outside every region."""
+    g = rng_for(index, seed)
+    dx = dy = 1e-3
+    eps = g.uniform(*eps_range, size=(ny, nx))
+    sig = g.uniform(*sig_range, size=(ny, nx))
+    occ = np.zeros((ny, nx), dtype=bool)
+    roms = []
+    tries = 0
+    while len(roms) < n_regions:
+        tries += 1
+        if tries > 10000:
+            raise RuntimeError("cannot place regions")
+        i0 = int(g.integers(margin, nx - a - margin + 1))
+        j0 = int(g.integers(margin, ny - a - margin + 1))
+        if occ[j0 - margin:j0 + a + margin, i0 - margin:i0 + a + margin].any():
+            continue
+        occ[j0 - 1:j0 + a + 1, i0 - 1:i0 + a + 1] = True
+        nf = a * r
+        if inclusion:
+            w = int(g.integers(max(1, nf // 4), nf))
+            h = int(g.integers(max(1, nf // 4), nf))
+            x0 = int(g.integers(0, nf - w + 1))
+            y0 = int(g.integers(0, nf - h + 1))
+            ef, sf = rect_fine(a, a, r, (x0, y0), (x0 + w, y0 + h),
+                               g.uniform(2.0, 10.0), g.uniform(0.01, 0.1))
+        else:
+            ef, sf = np.ones((nf, nf)), np.zeros((nf, nf))
+        roms.append(dict(i0=i0, j0=j0, a=a, b=a, r=r, eps_r=ef, sigma=sf, q=q, f0=fc))
+    dt = dt_factor * fine_cfl(dx, dy, r)
+
+    def free_cell():
+        while True:
+            i = int(g.integers(1, nx - 1))
+            j = int(g.integers(1, ny - 1))
+            if not occ[max(j - 1, 0):j + 2, max(i - 1, 0):i + 2].any():
+                return i, j
+
+    si, sj = free_cell()
+    probes = [free_cell() for _ in range(n_probes)]
+    return dict(
+        name=f"random_{nx}x{ny}", nx=nx, ny=ny, dx=dx, dy=dy, dt=dt, eps_r=eps, sigma=sig,
+        roms=roms, sources=[dict(comp=1, i=si, j=sj, len=1, wave=diff_gaussian(nsteps, dt, fc))],
+        probes=probes, nsteps=nsteps)
+
+
+def grid_4096(nsteps: int = 20000):
+    """4096^2 cells at dx = 1 mm, eps_r ~ U[1,4], sigma ~ U[0,0.02] per cell;
+    8 regions of 16 x 16 coarse cells refined r = 4, each with a seeded lossy
+    inclusion; ROM order 200; one Jy point source (fc = 30 GHz) and 16 probes;
+    dt = 0.95 x the fine-mesh CFL limit."""
+    return random_grid(1, 4096, 4096, 8, 16, 4, 200, nsteps, dt_factor=0.95)
