@@ -24,7 +24,11 @@ pencil, nor its deflation rule):
   two Gram-Schmidt passes against the basis so far; a direction is kept when
   its singular value exceeds tol times the block's largest singular value
   before orthogonalisation; columns are taken in order of decreasing singular
-  value, and the last block is truncated so that the basis has k columns.
+  value.  When the last block must be truncated to stay within k columns, the
+  cut is moved down to the nearest gap in the singular values (relative gap
+  above gap_tol), so that the kept subspace is uniquely defined even when a
+  symmetric region gives equal singular values; the basis may then hold
+  fewer than k columns.
 * B_in selects the model inputs: the identity (all n_u fine hanging
   variables, Eq. (16)) or T (one input per coarse interface edge, the dual
   interpolation; see ``couple``).
@@ -105,7 +109,8 @@ def full_order(fs: FineSystem) -> ReducedModel:
     return project(fs, np.eye(fs.nE), np.eye(fs.nH))
 
 
-def block_arnoldi(apply_A, R0: np.ndarray, k: int, tol: float = 1e-12) -> np.ndarray:
+def block_arnoldi(apply_A, R0: np.ndarray, k: int, tol: float = 1e-12,
+                  gap_tol: float = 1e-8) -> np.ndarray:
     """Orthonormal basis of K_k(A, R0) with SVD deflation (see module header)."""
     N = R0.shape[0]
     Q = np.zeros((N, 0))
@@ -121,8 +126,15 @@ def block_arnoldi(apply_A, R0: np.ndarray, k: int, tol: float = 1e-12) -> np.nda
         if keep == 0:
             break
         take = min(keep, k - Q.shape[1])
+        if take < keep:
+            while take > 0 and s[take - 1] - s[take] <= gap_tol * s[take - 1]:
+                take -= 1
+            if take == 0:
+                break
         U = U[:, :take]
         Q = np.hstack([Q, U])
+        if take < keep:
+            break
         W = apply_A(U)
     return Q
 
