@@ -1,0 +1,314 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the Yee + embedded-ROM forward time march on GB300.
+
+Workload (the large single-run configuration): a 4096 x 4096 coarse grid at
+dx = 1 mm with per-cell eps_r ~ U[1,4] and sigma ~ U[0,0.02] S/m, eight
+16 x 16-cell regions refined r = 4 with seeded lossy inclusions, each
+replaced by a q = 200 reduced model, one differentiated-Gaussian Jy point
+source and 16 Hz probes, dt = 0.95 x the fine-mesh CFL limit.  One benchmark
+step = one fdtd_run of --tsteps time steps (default 2000, so the ten timed
+steps cover the configuration's 20000 time steps).
+
+Metric: Gcell-steps/s = coarse cells x time steps / device time (CUDA events
+on the library's stream), reduced-model build excluded.  Multi-GPU runs are
+independent replicas (the path has no exchange step): value = cells x steps
+summed over ranks / max time over ranks.
+
+--impl reference times the FP64 oracle on the host cores (the method's
+reference implementation in this repository) on a bounded sample of the same
+workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Yee+ROM Gcell-steps/s"
+UNIT = "Gcell-steps/s"
+BYTES_PER_CELL_STEP = 32   # read Ex, Ey, Hz, eps, sigma; write Ex, Ey, Hz (FP32)
+FALLBACK_HBM_GBS = 6800.0
+WORKLOAD = ("grid_4096: 4096x4096 coarse cells (dx=1mm, eps_r~U[1,4], sigma~U[0,0.02]), "
+            "8 regions 16x16 r=4 with lossy inclusions, ROM q=200 (dual rule), 1 Jy source, "
+            "16 Hz probes, dt=0.95 fine CFL")
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    return ws, int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def profile_traffic():
+    """DRAM bytes per stencil launch from the committed ncu summary, if it
+    was taken on the current kernel source."""
+    src = os.path.join(ROOT, "paper_1609_07114_gb300", "csrc", "fdtd.cu")
+    summ = os.path.join(ROOT, "profiles", "yee_step_grid4096.md")
+    if not (os.path.exists(src) and os.path.exists(summ)):
+        return None
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    txt = open(summ).read()
+    m_sha = re.search(r"kernel source sha256\[:16\]:\s*([0-9a-f]+)", txt)
+    m_b = re.search(r"dram bytes per full-size launch:\s*([0-9.eE+]+)", txt)
+    if m_sha and m_b and m_sha.group(1) == sha:
+        return float(m_b.group(1))
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid=None):
+        self.uuid = uuid
+        self.p = None
+
+    def __enter__(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if self.uuid:
+            cmd += ["-i", self.uuid]
+        try:
+            self.p = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.p:
+            self.p.terminate()
+            try:
+                self.out, _ = self.p.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+
+    def summary(self):
+        rows = [r.split(",") for r in getattr(self, "out", "").strip().splitlines() if r.count(",") >= 8]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = sorted(float(r[1]) for r in rows)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].strip() == "Active"})
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": float(rows[0][2]), "reasons": reasons,
+                "samples": len(rows)}
+
+
+def build_problem(nsteps_total):
+    import workloads
+    return workloads.grid_4096(nsteps_total)
+
+
+def cpu_sample(w, steps):
+    """Times the FP64 oracle (as it stands) stepping the full grid with all
+    its embedded models; the models are built first, untimed, as for the
+    GPU metric."""
+    from oracle import problem, scheme
+    grid, emb, _ = problem.build(w)
+    st = scheme.State(*grid.zeros())
+    out = [[0.0] * len(w["probes"])] * steps
+    import numpy as np
+    out = np.zeros((steps, len(w["probes"])))
+    t0 = time.perf_counter()
+    for n in range(steps):
+        scheme.step(grid, st, emb, w["sources"], n, w["probes"], out)
+    dt = time.perf_counter() - t0
+    cells = w["nx"] * w["ny"]
+    return {"value": cells * steps / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{steps} time steps of the full 4096x4096 grid with its 8 models (numpy FP64, "
+                      f"{dt:.1f} s; model build untimed)"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    w = build_problem(args.cpu_sample_steps * (args.steps + args.warmup) + 1)
+    from oracle import problem, scheme
+    import numpy as np
+    grid, emb, _ = problem.build(w)
+    st = scheme.State(*grid.zeros())
+    out = np.zeros((args.cpu_sample_steps * (args.steps + args.warmup), len(w["probes"])))
+    n = 0
+    for _ in range(args.warmup):
+        for _ in range(args.cpu_sample_steps):
+            scheme.step(grid, st, emb, w["sources"], n, w["probes"], out)
+            n += 1
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for _ in range(args.cpu_sample_steps):
+            scheme.step(grid, st, emb, w["sources"], n, w["probes"], out)
+            n += 1
+    el = time.perf_counter() - t0
+    cells = w["nx"] * w["ny"]
+    value = cells * args.cpu_sample_steps * args.steps / el / 1e9
+    sample = (f"each step = {args.cpu_sample_steps} time steps of the full 4096x4096 grid with its 8 "
+              f"models, FP64 numpy on 1 host core")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "time_steps_per_step": args.cpu_sample_steps},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--tsteps", type=int, default=2000, help="time steps per benchmark step")
+    ap.add_argument("--cpu-sample-steps", type=int, default=8)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import numpy as np
+    import torch
+    import paper_1609_07114_gb300 as pg
+    from paper_1609_07114_gb300 import build as pbuild
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0:
+        pbuild.build()
+    if dist:
+        dist.barrier()
+
+    K, W, T = args.steps, args.warmup, args.tsteps
+    total = (W + K) * T
+    w = build_problem(total)
+    ctx = pg.FdtdContext(w["dx"], w["dy"], w["dt"], [(w["eps_r"], w["sigma"])])
+    models = []
+    t0 = time.perf_counter()
+    for rd in w["roms"]:
+        m = pg.rom_build(rd["a"], rd["b"], rd["r"], w["dx"], w["dy"], w["dt"], rd["eps_r"],
+                         rd["sigma"], rd["q"], f0=rd["f0"])
+        ctx.rom_embed(m, 0, rd["i0"], rd["j0"])
+        models.append(m)
+    rom_seconds = time.perf_counter() - t0
+    wave = torch.tensor(w["sources"][0]["wave"].astype(np.float32), device="cuda")
+    probes = [(0, i, j) for (i, j) in w["probes"]]
+    out = torch.zeros((T, len(probes)), dtype=torch.float32, device="cuda")
+    src0 = w["sources"][0]
+
+    def one_step(k):
+        src = [dict(src0, sim=0, wave=wave[k * T:(k + 1) * T])]
+        ctx.fdtd_run(T, src, probes, out)
+
+    for k in range(W):
+        one_step(k)
+    torch.cuda.synchronize()
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(local).uuid)
+        uuid = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+    except Exception:
+        uuid = None
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(uuid) as clk:
+        e0.record(stream)
+        for k in range(W, W + K):
+            one_step(k)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    el_ms = e0.elapsed_time(e1)
+    if dist:
+        t = torch.tensor([el_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        el_ms = float(t.item())
+    cells = w["nx"] * w["ny"]
+    value = cells * T * K * ws / (el_ms / 1e3) / 1e9
+
+    # Per-kernel device time of the dominant (stencil) kernel, CUDA events on
+    # the launching stream, over a second pass of the same K steps.
+    ctx.set_timing(True)
+    for k in range(K):
+        one_step(k)
+    yee_ms, n_yee, post_ms, n_post = ctx.kernel_times()
+    ctx.set_timing(False)
+    yee_avg_s = yee_ms / n_yee / 1e3
+    alg_bytes = BYTES_PER_CELL_STEP * cells
+    hbm, kind = peaks()
+    achieved = alg_bytes / yee_avg_s / 1e9
+    traffic = profile_traffic()
+
+    # End to end through the host-buffer entry point: H2D of the step's
+    # source samples from pinned memory, D2H of its probe samples.
+    hw = torch.empty(T, dtype=torch.float32, pin_memory=True)
+    hw.copy_(torch.tensor(src0["wave"][:T].astype(np.float32)))
+    hwn = hw.numpy()
+    ctx.fdtd_run_host(T, [dict(src0, sim=0, wave=hwn)], probes)   # warm the host path
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(K):
+        ctx.fdtd_run_host(T, [dict(src0, sim=0, wave=hwn)], probes)
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": cells * T * K * ws / e2e_s / 1e9, "unit": UNIT,
+           "h2d_bytes_per_step": 4 * T, "d2h_bytes_per_step": 4 * T * len(probes)}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_sample(build_problem(args.cpu_sample_steps + 1), args.cpu_sample_steps)
+
+    launches_per_run = 2 * T + T // 16
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": W,
+        "ms_per_step": el_ms / K, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "time_steps_per_step": T, "nx": w["nx"], "ny": w["ny"],
+                   "roms": len(w["roms"]), "rom_q": [m.q for m in models],
+                   "rom_build_s": round(rom_seconds, 3),
+                   "l2": "inputs larger than L2: 0.47 GB of fields+materials per time step (L2 129 MB)",
+                   "parallelism": "replicas" if ws > 1 else "single"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "traffic": traffic, "peak_kind": kind,
+                     "kernel": "yee_step_kernel", "kernel_avg_ms": yee_avg_s * 1e3,
+                     "alg_bytes_per_launch": alg_bytes, "rom_post_avg_ms": post_ms / max(n_post, 1)},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": K * launches_per_run,
+        "clocks": clk.summary(),
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

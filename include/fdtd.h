@@ -1,0 +1,231 @@
+/*
+ * fdtd.h -- C ABI of the GB300 Yee + embedded reduced-order-model library.
+ *
+ * Method: Zhang, Bekmambetova, Triverio, "A Stable FDTD Method with Embedded
+ * Reduced-Order Models" (arXiv:1609.07114).  A 2D TEz Yee leapfrog (Ex, Ey,
+ * Hz) runs on a coarse mesh with perfect-electric-conductor walls
+ * (Sec. II-A, Eqs. (3), (5)); fine-mesh regions are replaced by passive
+ * reduced models (Sec. III, Eq. (11)) coupled to the coarse interface edges
+ * (Sec. IV, Eq. (23)) and stepped every time step.
+ *
+ * Conventions shared by every call
+ *   - All calls return int status: FDTD_OK (0) or a negative FDTD_E* code.
+ *     A failing call leaves its outputs untouched and records a message,
+ *     read with fdtd_last_error(ctx) (or fdtd_last_error(NULL) for calls
+ *     without a context).
+ *   - Host input arrays are copied during the call; the caller keeps them.
+ *   - Device pointers passed in (waveforms, probe outputs) are owned by the
+ *     caller and must stay valid until the work queued on the context's
+ *     stream has finished.  Device work is queued on the stream given to
+ *     fdtd_create (NULL = legacy default stream); calls that return host
+ *     data synchronise that stream.
+ *   - Grid indexing (0-based): coarse cell (i, j), i < nx, j < ny; Hz[j][i];
+ *     Ex[j][i] on the x-edge from node (i, j) to (i+1, j), j <= ny;
+ *     Ey[j][i] on the y-edge from node (i, j) to (i, j+1), i <= nx.
+ *     Host field buffers are dense row-major: Ex (ny+1) x nx,
+ *     Ey ny x (nx+1), Hz ny x nx.
+ *   - Units: SI (m, s, S/m, A/m^2); relative permittivity is dimensionless.
+ */
+#ifndef FDTD_ROM_H
+#define FDTD_ROM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  FDTD_OK = 0,
+  FDTD_EINVAL = -1,       /* malformed argument or descriptor */
+  FDTD_ENOMEM = -2,       /* host or device allocation failed */
+  FDTD_ECFL = -3,         /* dt not below the coarse CFL limit, Eq. (1) */
+  FDTD_ENOTPASSIVE = -4,  /* reduced model violates Eq. (26a)-(26c) at this dt */
+  FDTD_ESINGULAR = -5,    /* coupling system of Eq. (19) inconsistent or degenerate */
+  FDTD_EUNSTABLE = -6,    /* non-finite field value detected */
+  FDTD_ETIMEOUT = -7,     /* a bounded device wait gave up */
+  FDTD_ECUDA = -8         /* a CUDA runtime call failed */
+};
+
+/* Interpolation rule between coarse interface and fine boundary. */
+enum {
+  FDTD_RULE_DUAL = 0,  /* y = (1/r) T^T y_hat, u_hat = T U (lossless; any order) */
+  FDTD_RULE_PAPER = 1  /* y_hat = T y, U = (1/r) T^T u_hat, Eqs. (15)-(16) */
+};
+
+enum { FDTD_SRC_JX = 0, FDTD_SRC_JY = 1 };
+
+typedef struct fdtd_ctx fdtd_ctx;
+typedef struct rom_model rom_model;
+
+/* ------------------------------------------------------------------ grids */
+
+/* One independent coarse simulation.  eps_r, sigma: host [ny][nx] per-cell
+ * relative permittivity (> 0) and conductivity (>= 0, S/m).  Edge values
+ * are the mean of the two adjacent cells (Sec. II-A, text below Eq. (3)). */
+typedef struct {
+  int nx, ny;
+  const double* eps_r;
+  const double* sigma;
+} fdtd_sim_desc;
+
+/* A batch of simulations sharing cell size and time step.  Grid sizes may
+ * differ between simulations; all of them advance together in fdtd_run. */
+typedef struct {
+  double dx, dy, dt;
+  int nsim;
+  const fdtd_sim_desc* sims;
+} fdtd_grid_desc;
+
+/* Creates a context, allocates all device state (fields zeroed) on the
+ * current CUDA device.  Checks dt < 1/(c0 sqrt(1/dx^2+1/dy^2)) (Eq. (1));
+ * FDTD_ECFL otherwise.  cuda_stream: a cudaStream_t or NULL. */
+int fdtd_create(const fdtd_grid_desc* grid, void* cuda_stream, fdtd_ctx** out);
+void fdtd_destroy(fdtd_ctx* ctx);
+
+/* Eq. (1): the 2D vacuum CFL limit of a dx x dy mesh (seconds). */
+int fdtd_cfl_limit(double dx, double dy, double* out);
+
+/* --------------------------------------------------------- reduced models */
+
+/* A fine-mesh region of a x b coarse cells refined r times (Sec. II):
+ * fine cells (r*a) x (r*b) of size dx/r x dy/r; eps_r, sigma host
+ * [r*b][r*a].  q: reduced order q_E + q_H of the SPRIM projection
+ * (Sec. III); 0 keeps the full fine model (V = I).  dt: the time step the
+ * model will run at (must equal the context's).  f0: frequency (Hz) of the
+ * real Krylov expansion point psi0 = tan(pi f0 dt_b).  gamma: CFL-extension
+ * margin of Sec. V-E (singular values of Eq. (27) above gamma*2/dt are
+ * clamped to it); gamma <= 0 disables the extension.  defl_tol: relative
+ * deflation tolerance of the block Arnoldi process (0 selects 1e-12). */
+typedef struct {
+  int a, b, r;
+  double dx, dy, dt;
+  const double* eps_r;
+  const double* sigma;
+  int q;
+  int rule;
+  double f0;
+  double gamma;
+  double defl_tol;
+} rom_desc;
+
+typedef struct {
+  int qE, qH;              /* achieved block orders of V1, V2 (Eq. (9)) */
+  int n_inputs;            /* Krylov start-block width: n_u (paper) or n_y (dual) */
+  int n_clamped;           /* singular values clamped by the CFL extension */
+  double smax_before;      /* max s_k * dt/2 of Eq. (27) before the extension */
+  double smax_after;       /* ... and after it (< 1 means Eq. (26a) holds) */
+  double min_eig_R;        /* smallest eigenvalue of R~ / largest (Eq. (26a)) */
+  double cond3_residual;   /* ||B~ - L~ S_hat|| / ||B~|| (Eq. (26c)) */
+  double seconds;          /* host wall time of the build */
+} rom_build_report;
+
+/* Builds a reduced model on the host in FP64: fine-system assembly
+ * (Sec. II), block-Krylov SPRIM projection (Sec. III), passivity check and
+ * optional CFL extension (Sec. V).  rep may be NULL.  The model is
+ * independent of any context and may be embedded many times. */
+int rom_build(const rom_desc* desc, rom_model** out, rom_build_report* rep);
+void rom_free(rom_model* model);
+
+/* Achieved orders and port count of a built model. */
+int rom_get_info(const rom_model* model, int* qE, int* qH, int* n_u);
+
+/* Copies the reduced blocks (row-major, FP64, caller-owned host buffers):
+ * R11 qE x qE (= V1^T D_eps V1), R22 qH x qH (= V2^T D_mu V2),
+ * Kt qE x qH (= V1^T K V2, after any CFL extension), Sig qE x qE
+ * (= V1^T D_sigma V1), LE qE x n_u (= V1^T L_E).  Eq. (12):
+ * R~ = [[R11/dt, -Kt/2], [-Kt^T/2, R22/dt]], F~ = [[Sig/2, -Kt/2],
+ * [Kt^T/2, 0]], B~ = [LE S_hat; 0].  Any pointer may be NULL. */
+int rom_get_blocks(const rom_model* model, double* R11, double* R22, double* Kt,
+                   double* Sig, double* LE);
+
+/* Places a model into simulation `sim` with its lower-left coarse cell at
+ * (i0, j0); the region is [i0, i0+a) x [j0, j0+b).  The region must keep
+ * one coarse cell from the walls and from every other region.  Precomputes
+ * in FP64 the run-time map of Eq. (23),
+ *     [y; x~]^{n+1} = P [y; x~]^n + Q h^{n+1/2},
+ * with the coarse half-cell materials of the cells just outside
+ * (Eq. (13)), uploads P and Q in FP32, and zeroes the fields inside.
+ * Returns the instance index through inst (may be NULL).
+ * FDTD_ENOTPASSIVE if R~ is not positive definite at the context's dt;
+ * FDTD_ESINGULAR if the coupling system is inconsistent or (paper rule)
+ * leaves the interface unable to carry any field. */
+int rom_embed(fdtd_ctx* ctx, const rom_model* model, int sim, int i0, int j0, int* inst);
+
+/* Host-only form of the coupling done by rom_embed: the FP64 run-time map
+ * of Eq. (23) for a model whose interface edges (ordered S, N, W, E; n_y =
+ * 2(a+b)) see coarse half cells of relative permittivity ring_eps_r[k] and
+ * conductivity ring_sigma[k] (Eq. (13)).  P (n_y+q)^2 and Q (n_y+q) x n_y,
+ * row-major, caller-owned.  No device work. */
+int rom_couple(const rom_model* model, const double* ring_eps_r, const double* ring_sigma,
+               double* P, double* Q);
+
+/* The FP64 run-time map of an embedded instance: n = n_y + q.  P n x n,
+ * Q n x n_y row-major host buffers (either may be NULL to query sizes). */
+int fdtd_get_rom_map(const fdtd_ctx* ctx, int inst, int* n, int* n_y, double* P, double* Q);
+
+/* ---------------------------------------------------------- time marching */
+
+/* An electric current density J (A/m^2) on `len` consecutive edges of one
+ * component, starting at edge (i, j) and running along the edge direction
+ * (Jx: i, i+1, ...; Jy: j, j+1, ...).  It enters Eq. (3) as the term
+ * -dx dy J on the right-hand side.  wave: samples J(t^{n+1/2}) for the
+ * n = 0 .. nsteps-1 steps of this run (device FP32 for fdtd_run, host FP32
+ * for fdtd_run_host).  Edges must be updated coarse edges (not PEC, not on
+ * or inside a region). */
+typedef struct {
+  int sim;
+  int comp;
+  int i, j;
+  int len;
+  const float* wave;
+} fdtd_source;
+
+/* Records Hz^{n+1/2} of coarse cell (i, j) of simulation sim every step. */
+typedef struct {
+  int sim, i, j;
+} fdtd_probe;
+
+/* Advances every simulation of the context by nsteps (Sec. IV-C: coarse
+ * H, coarse E with sources, then Eq. (23) for every embedded model).
+ * probe_out: device FP32 [nsteps][nprobe] (may be NULL when nprobe = 0).
+ * Asynchronous on the context's stream. */
+int fdtd_run(fdtd_ctx* ctx, long long nsteps, const fdtd_source* src, int nsrc,
+             const fdtd_probe* probes, int nprobe, float* probe_out);
+
+/* Same as fdtd_run with host buffers: copies the source waveforms to the
+ * device, runs, copies the probe samples back, and synchronises. */
+int fdtd_run_host(fdtd_ctx* ctx, long long nsteps, const fdtd_source* src, int nsrc,
+                  const fdtd_probe* probes, int nprobe, float* probe_out_host);
+
+/* ------------------------------------------------------------------ state */
+
+/* Host copies of the current fields of one simulation (E^n, Hz^{n-1/2}). */
+int fdtd_get_fields(fdtd_ctx* ctx, int sim, float* Ex, float* Ey, float* Hz);
+/* Overwrites the fields; values on PEC walls and inside regions are
+ * ignored (held at 0); interface values become each model's y. */
+int fdtd_set_fields(fdtd_ctx* ctx, int sim, const float* Ex, const float* Ey,
+                    const float* Hz);
+/* Reduced state x~ (length q) of an embedded instance. */
+int fdtd_get_rom_state(fdtd_ctx* ctx, int inst, float* x);
+int fdtd_set_rom_state(fdtd_ctx* ctx, int inst, const float* x);
+/* Number of steps taken since creation. */
+int fdtd_get_step(const fdtd_ctx* ctx, long long* n);
+
+/* ------------------------------------------------------------ measurement */
+
+/* When on, fdtd_run launches every step directly (no CUDA graph) and records
+ * CUDA events around each kernel on the context's stream; the device time of
+ * the stencil kernel and of the reduced-model/probe kernel accumulates until
+ * timing is switched on again (which resets it). */
+int fdtd_set_timing(fdtd_ctx* ctx, int on);
+/* Accumulated device time (ms) and launch counts; synchronises the stream. */
+int fdtd_get_kernel_times(fdtd_ctx* ctx, double* yee_ms, long long* yee_launches,
+                          double* post_ms, long long* post_launches);
+
+const char* fdtd_last_error(const fdtd_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FDTD_ROM_H */

@@ -1,0 +1,921 @@
+// GB300 (sm_103a) Yee + embedded-ROM time marching: kernels, context and C ABI.
+//
+// Method: Zhang, Bekmambetova, Triverio, arXiv:1609.07114.  The coarse mesh
+// is stepped with the integral-form Yee updates (Sec. II-A, Eqs. (3), (5));
+// each embedded reduced model is stepped with its precomputed explicit map
+// (Sec. IV-C, Eq. (23)).  See kernels.cuh for the data layout.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "internal.hpp"
+#include "kernels.cuh"
+
+using namespace fdtdrom;
+
+// ============================================================== device code
+
+namespace {
+
+__device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
+__device__ __forceinline__ float comp(const float4& v, int t) {
+  return t == 0 ? v.x : (t == 1 ? v.y : (t == 2 ? v.z : v.w));
+}
+
+// E-edge coefficients from the two adjacent cells {eps/dt, sigma/2}
+// (edge material = mean of the two cells, Sec. II-A).
+__device__ __forceinline__ void edge_coef(float2 m1, float2 m2, float& ca, float& cb) {
+  const float A = 0.5f * (m1.x + m2.x);
+  const float S = 0.5f * (m1.y + m2.y);
+  cb = __frcp_rn(A + S);
+  ca = (A - S) * cb;
+}
+
+// Fused coarse H and E half steps over one tile (module header).
+// Each warp marches up a strip of 128 columns x kTileRows rows, keeping the
+// previous row's fields and new Hz in registers; lane l owns columns
+// c0 + 4l .. c0 + 4l + 3.  The first iteration recomputes the halo row
+// j0 - 1 of Hz^{n+1/2}; lane 0 also recomputes the halo column c0 - 1.
+__global__ void __launch_bounds__(kWarpsPerCta * 32)
+yee_step_kernel(const SimDev* __restrict__ sims, const TileWork* __restrict__ work,
+                const RunDev* __restrict__ run, int par, int c) {
+  const TileWork tw = work[blockIdx.x];
+  const SimDev sd = sims[tw.sim];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int c0 = tw.x0 + warp * kStripCols;
+  const int nx = sd.nx, ny = sd.ny, P = sd.pitch;
+  // (ternaries, not sd.ex[par]: a dynamic index would put sd in local memory)
+  const float* __restrict__ ex = par ? sd.ex[1] : sd.ex[0];
+  const float* __restrict__ ey = par ? sd.ey[1] : sd.ey[0];
+  const float* __restrict__ hz = par ? sd.hz[1] : sd.hz[0];
+  float* __restrict__ exo = par ? sd.ex[0] : sd.ex[1];
+  float* __restrict__ eyo = par ? sd.ey[0] : sd.ey[1];
+  float* __restrict__ hzo = par ? sd.hz[0] : sd.hz[1];
+  const float2* __restrict__ mat = sd.mat;
+  const unsigned FULL = 0xffffffffu;
+  if (c0 < nx) {
+    const int cl = c0 + 4 * lane;
+    const int j0 = tw.y0, j1 = min(j0 + kTileRows, ny);
+    int j = j0 > 0 ? j0 - 1 : 0;
+    const bool halo = (lane == 0) && (c0 > 0);
+    float4 exc = ld4(ex + (size_t)j * P + cl);
+    float exLc = halo ? ex[(size_t)j * P + c0 - 1] : 0.f;
+    float4 hzp = make_float4(0.f, 0.f, 0.f, 0.f);
+    float2 mp[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) mp[t] = make_float2(0.f, 0.f);
+    for (; j < j1; ++j) {
+      const size_t row = (size_t)j * P;
+      const float4 exn = ld4(ex + row + P + cl);
+      const float4 eyv = ld4(ey + row + cl);
+      const float4 hzv = ld4(hz + row + cl);
+      const float4 ma = ld4(reinterpret_cast<const float*>(mat + row + cl));
+      const float4 mb = ld4(reinterpret_cast<const float*>(mat + row + cl + 2));
+      const float2 m[4] = {make_float2(ma.x, ma.y), make_float2(ma.z, ma.w),
+                           make_float2(mb.x, mb.y), make_float2(mb.z, mb.w)};
+      float eyR = __shfl_down_sync(FULL, eyv.x, 1);
+      if (lane == 31) eyR = (c0 + kStripCols <= nx) ? ey[row + c0 + kStripCols] : 0.f;
+      const float eyA[5] = {eyv.x, eyv.y, eyv.z, eyv.w, eyR};
+      // Eq. (5): Hz^{n+1/2} = Hz^{n-1/2} + dt/(mu0 dy)(Ex_{j+1} - Ex_j)
+      //                                  - dt/(mu0 dx)(Ey_{i+1} - Ey_i)
+      float hn[4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const bool live = (cl + t < nx) && (m[t].x >= 0.f);
+        hn[t] = live ? comp(hzv, t) + sd.chx * (comp(exn, t) - comp(exc, t)) -
+                           sd.chy * (eyA[t + 1] - eyA[t])
+                     : 0.f;
+      }
+      // Left neighbour of column cl: lane - 1's last cell, or the halo column.
+      float hnL = __shfl_up_sync(FULL, hn[3], 1);
+      float2 mL;
+      mL.x = __shfl_up_sync(FULL, m[3].x, 1);
+      mL.y = __shfl_up_sync(FULL, m[3].y, 1);
+      float exLn = 0.f;
+      if (lane == 0) {
+        hnL = 0.f;
+        mL = make_float2(-1.f, 0.f);
+        if (halo) {
+          exLn = ex[row + P + c0 - 1];
+          const float eyL = ey[row + c0 - 1];
+          const float hzL = hz[row + c0 - 1];
+          mL = mat[row + c0 - 1];
+          hnL = (mL.x >= 0.f) ? hzL + sd.chx * (exLn - exLc) - sd.chy * (eyv.x - eyL) : 0.f;
+        }
+      }
+      if (j >= j0) {
+        st4(hzo + row + cl, make_float4(hn[0], hn[1], hn[2], hn[3]));
+        // Eq. (3): Ex^{n+1} = ca Ex^n + cb (Hz_j - Hz_{j-1}) / dy on edge (i, j),
+        // between cells (i, j-1) and (i, j).
+        float exw[4], eyw[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          float v = comp(exc, t);
+          if (j >= 1 && cl + t < nx && mp[t].x >= 0.f && m[t].x >= 0.f) {
+            float ca, cb;
+            edge_coef(mp[t], m[t], ca, cb);
+            v = ca * v + cb * sd.rdy * (hn[t] - comp(hzp, t));
+          }
+          exw[t] = v;
+        }
+        // Ey^{n+1} = ca Ey^n - cb (Hz_i - Hz_{i-1}) / dx on edge (i, j),
+        // between cells (i-1, j) and (i, j).
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          const int i = cl + t;
+          const float2 ml = t == 0 ? mL : m[t - 1];
+          const float hl = t == 0 ? hnL : hn[t - 1];
+          float v = eyA[t];
+          if (i >= 1 && i < nx && ml.x >= 0.f && m[t].x >= 0.f) {
+            float ca, cb;
+            edge_coef(ml, m[t], ca, cb);
+            v = ca * v - cb * sd.rdx * (hn[t] - hl);
+          }
+          eyw[t] = v;
+        }
+        st4(exo + row + cl, make_float4(exw[0], exw[1], exw[2], exw[3]));
+        st4(eyo + row + cl, make_float4(eyw[0], eyw[1], eyw[2], eyw[3]));
+      }
+      exc = exn;
+      exLc = exLn;
+      hzp = make_float4(hn[0], hn[1], hn[2], hn[3]);
+#pragma unroll
+      for (int t = 0; t < 4; ++t) mp[t] = m[t];
+    }
+  }
+  // Source currents on this tile's edges: E^{n+1} -= cb J(t^{n+1/2}).
+  const int2 rg = run->src_range[blockIdx.x];
+  if (rg.y > rg.x) {
+    __syncthreads();
+    const long long n = run->base + c;
+    for (int e = rg.x + threadIdx.x; e < rg.y; e += blockDim.x) {
+      const SrcEdge se = run->src_edges[e];
+      const size_t off = (size_t)se.j * P + se.i;
+      const float2 m2 = mat[off];
+      const float2 m1 = se.comp == 0 ? mat[off - P] : mat[off - 1];
+      float ca, cb;
+      edge_coef(m1, m2, ca, cb);
+      float* dst = se.comp == 0 ? exo : eyo;
+      dst[off] -= cb * run->waves[se.src][n];
+    }
+  }
+}
+
+// Eq. (23) for every embedded model, then the probes.
+__global__ void __launch_bounds__(256)
+rom_post_kernel(const SimDev* __restrict__ sims, const RomInstDev* __restrict__ insts,
+                const RomWork* __restrict__ work, int nwork, const RunDev* __restrict__ run,
+                int par, int c) {
+  extern __shared__ float smem[];
+  const unsigned FULL = 0xffffffffu;
+  if ((int)blockIdx.x < nwork) {
+    const RomWork w = work[blockIdx.x];
+    const RomInstDev ri = insts[w.inst];
+    const SimDev sd = sims[ri.sim];
+    const float* __restrict__ s = par ? ri.state[1] : ri.state[0];
+    float* __restrict__ so = par ? ri.state[0] : ri.state[1];
+    const float* __restrict__ hzn = par ? sd.hz[0] : sd.hz[1];
+    float* __restrict__ exo = par ? sd.ex[0] : sd.ex[1];
+    float* __restrict__ eyo = par ? sd.ey[0] : sd.ey[1];
+    float* sv = smem;
+    float* hv = smem + ri.n;
+    for (int k = threadIdx.x; k < ri.n; k += blockDim.x) sv[k] = s[k];
+    for (int k = threadIdx.x; k < ri.ny; k += blockDim.x) hv[k] = hzn[ri.h_cell[k]];
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int r = w.row0 + warp; r < w.row1; r += nw) {
+      const float* __restrict__ Pr = ri.P + (size_t)r * ri.n;
+      const float* __restrict__ Qr = ri.Q + (size_t)r * ri.ny;
+      float acc = 0.f;
+      for (int k = lane; k < ri.n; k += 32) acc = fmaf(Pr[k], sv[k], acc);
+      for (int k = lane; k < ri.ny; k += 32) acc = fmaf(Qr[k], hv[k], acc);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
+      if (lane == 0) {
+        so[r] = acc;
+        if (r < ri.ny) {
+          const int code = ri.y_edge[r];
+          float* base = (code >> 30) ? eyo : exo;
+          base[code & 0x3fffffff] = acc;
+        }
+      }
+    }
+  } else {
+    const int p = (blockIdx.x - nwork) * blockDim.x + threadIdx.x;
+    if (p < run->nprobe) {
+      const long long n = run->base + c;
+      const SimDev* sd = sims + run->probe_sim[p];
+      const float* hzn = par ? sd->hz[0] : sd->hz[1];
+      run->probe_out[n * run->nprobe + p] = hzn[run->probe_cell[p]];
+    }
+  }
+}
+
+__global__ void advance_kernel(RunDev* run, int by) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) run->base += by;
+}
+
+}  // namespace
+
+// ============================================================== host side
+
+namespace fdtdrom {
+
+static std::mutex g_err_mu;
+static std::string g_err;
+
+int set_global_error(int code, const std::string& msg) {
+  std::lock_guard<std::mutex> lk(g_err_mu);
+  g_err = msg;
+  return code;
+}
+
+}  // namespace fdtdrom
+
+namespace {
+
+constexpr int kChunk = 16;  // steps per captured graph (even: parity repeats)
+
+struct SimHost {
+  int nx = 0, ny = 0, pitch = 0;
+  std::vector<double> eps_r, sigma;
+  std::vector<unsigned char> region;   // 1 = cell covered by a reduced model
+  std::vector<float2> mat;
+  float* ex[2] = {nullptr, nullptr};
+  float* ey[2] = {nullptr, nullptr};
+  float* hz[2] = {nullptr, nullptr};
+  float2* mat_d = nullptr;
+  int tile_base = 0, ncx = 0, ncy = 0;
+};
+
+struct Instance {
+  int sim = 0, i0 = 0, j0 = 0, a = 0, b = 0, q = 0, ny = 0, n = 0;
+  InterfaceDesc itf;
+  la::Mat P, Q;
+  float* P_d = nullptr;
+  float* Q_d = nullptr;
+  float* state_d[2] = {nullptr, nullptr};
+  int* y_edge_d = nullptr;
+  int* h_cell_d = nullptr;
+  std::vector<int> y_edge, h_cell;
+};
+
+template <class T>
+struct DevBuf {
+  T* p = nullptr;
+  size_t cap = 0;
+  cudaError_t reserve(size_t n) {
+    if (n <= cap) return cudaSuccess;
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+    cudaError_t e = cudaMalloc(&p, std::max<size_t>(n, 1) * sizeof(T));
+    if (e == cudaSuccess) cap = std::max<size_t>(n, 1);
+    return e;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+  }
+};
+
+}  // namespace
+
+struct fdtd_ctx {
+  cudaStream_t stream = nullptr;
+  cudaStream_t capture_stream = nullptr;
+  double dx = 0, dy = 0, dt = 0;
+  std::vector<SimHost> sims;
+  std::vector<TileWork> tiles;
+  SimDev* sims_d = nullptr;
+  TileWork* tiles_d = nullptr;
+  std::vector<Instance> insts;
+  RomInstDev* insts_d = nullptr;
+  RomWork* romwork_d = nullptr;
+  int nromwork = 0;
+  size_t post_smem = 0;
+  RunDev* run_d = nullptr;
+  DevBuf<int2> src_range;
+  DevBuf<SrcEdge> src_edges;
+  DevBuf<const float*> waves;
+  DevBuf<int> probe_sim, probe_cell;
+  DevBuf<float> host_waves, host_probes;
+  int cur = 0;
+  long long step = 0;
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  int graph_nprobe_blocks[2] = {-1, -1};
+  // measurement mode (fdtd_set_timing)
+  bool timing = false;
+  std::vector<cudaEvent_t> ev;
+  int ev_used = 0;
+  double t_yee = 0, t_post = 0;
+  long long n_yee = 0, n_post = 0;
+  std::string err;
+};
+
+namespace {
+
+int fail(fdtd_ctx* ctx, int code, const std::string& msg) {
+  if (ctx) ctx->err = msg;
+  set_global_error(code, msg);
+  return code;
+}
+
+#define CK(call)                                                                    \
+  do {                                                                              \
+    cudaError_t e_ = (call);                                                        \
+    if (e_ != cudaSuccess)                                                          \
+      return fail(ctx, FDTD_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+void drop_graphs(fdtd_ctx* ctx) {
+  for (int p = 0; p < 2; ++p) {
+    if (ctx->graph[p]) cudaGraphExecDestroy(ctx->graph[p]);
+    ctx->graph[p] = nullptr;
+    ctx->graph_nprobe_blocks[p] = -1;
+  }
+}
+
+int upload_instances(fdtd_ctx* ctx) {
+  std::vector<RomInstDev> h(ctx->insts.size());
+  std::vector<RomWork> wk;
+  size_t smem = 0;
+  for (size_t k = 0; k < ctx->insts.size(); ++k) {
+    const Instance& in = ctx->insts[k];
+    RomInstDev& d = h[k];
+    d.P = in.P_d, d.Q = in.Q_d;
+    d.state[0] = in.state_d[0], d.state[1] = in.state_d[1];
+    d.y_edge = in.y_edge_d, d.h_cell = in.h_cell_d;
+    d.n = in.n, d.ny = in.ny, d.sim = in.sim;
+    const int rows_per = 64;
+    for (int r0 = 0; r0 < in.n; r0 += rows_per) wk.push_back({(int)k, r0, std::min(in.n, r0 + rows_per), 0});
+    smem = std::max(smem, sizeof(float) * (size_t)(in.n + in.ny));
+  }
+  if (ctx->insts_d) cudaFree(ctx->insts_d);
+  if (ctx->romwork_d) cudaFree(ctx->romwork_d);
+  ctx->insts_d = nullptr;
+  ctx->romwork_d = nullptr;
+  if (!h.empty()) {
+    CK(cudaMalloc(&ctx->insts_d, sizeof(RomInstDev) * h.size()));
+    CK(cudaMemcpy(ctx->insts_d, h.data(), sizeof(RomInstDev) * h.size(), cudaMemcpyHostToDevice));
+    CK(cudaMalloc(&ctx->romwork_d, sizeof(RomWork) * wk.size()));
+    CK(cudaMemcpy(ctx->romwork_d, wk.data(), sizeof(RomWork) * wk.size(), cudaMemcpyHostToDevice));
+  }
+  ctx->nromwork = (int)wk.size();
+  ctx->post_smem = smem;
+  if (smem > 48 * 1024) {
+    if (smem > 200 * 1024) return fail(ctx, FDTD_EINVAL, "reduced model too large for one CTA's shared memory");
+    CK(cudaFuncSetAttribute(rom_post_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  }
+  drop_graphs(ctx);
+  return FDTD_OK;
+}
+
+// Launches one step (chunk index c) on stream s.
+void launch_step(fdtd_ctx* ctx, cudaStream_t s, int par, int c, int nprobe_blocks) {
+  yee_step_kernel<<<(unsigned)ctx->tiles.size(), kWarpsPerCta * 32, 0, s>>>(
+      ctx->sims_d, ctx->tiles_d, ctx->run_d, par, c);
+  const int nb = ctx->nromwork + nprobe_blocks;
+  if (nb > 0)
+    rom_post_kernel<<<nb, 256, ctx->post_smem, s>>>(ctx->sims_d, ctx->insts_d, ctx->romwork_d,
+                                                    ctx->nromwork, ctx->run_d, par, c);
+}
+
+int ensure_graph(fdtd_ctx* ctx, int par, int nprobe_blocks) {
+  if (ctx->graph[par] && ctx->graph_nprobe_blocks[par] == nprobe_blocks) return FDTD_OK;
+  if (ctx->graph[par]) cudaGraphExecDestroy(ctx->graph[par]);
+  ctx->graph[par] = nullptr;
+  cudaGraph_t g = nullptr;
+  CK(cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal));
+  for (int c = 0; c < kChunk; ++c) launch_step(ctx, ctx->capture_stream, par ^ (c & 1), c, nprobe_blocks);
+  advance_kernel<<<1, 32, 0, ctx->capture_stream>>>(ctx->run_d, kChunk);
+  CK(cudaStreamEndCapture(ctx->capture_stream, &g));
+  cudaError_t e = cudaGraphInstantiate(&ctx->graph[par], g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return fail(ctx, FDTD_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+  ctx->graph_nprobe_blocks[par] = nprobe_blocks;
+  return FDTD_OK;
+}
+
+bool edge_updated(const SimHost& s, int comp, int i, int j) {
+  if (comp == 0) {
+    if (i < 0 || i >= s.nx || j < 1 || j > s.ny - 1) return false;
+    return !s.region[(size_t)(j - 1) * s.nx + i] && !s.region[(size_t)j * s.nx + i];
+  }
+  if (j < 0 || j >= s.ny || i < 1 || i > s.nx - 1) return false;
+  return !s.region[(size_t)j * s.nx + i - 1] && !s.region[(size_t)j * s.nx + i];
+}
+
+// Uploads the per-run source and probe tables (wave pointers already device).
+int prepare_run(fdtd_ctx* ctx, long long nsteps, const fdtd_source* src, int nsrc,
+                const float* const* wave_dev, const fdtd_probe* probes, int nprobe,
+                float* probe_out) {
+  const int ntiles = (int)ctx->tiles.size();
+  std::vector<std::vector<SrcEdge>> per(ntiles);
+  std::vector<unsigned char> seen;
+  for (int s = 0; s < nsrc; ++s) {
+    const fdtd_source& so = src[s];
+    if (so.sim < 0 || so.sim >= (int)ctx->sims.size() || (so.comp != 0 && so.comp != 1) ||
+        so.len < 1 || !wave_dev[s])
+      return fail(ctx, FDTD_EINVAL, "fdtd_run: malformed source " + std::to_string(s));
+    const SimHost& sh = ctx->sims[so.sim];
+    for (int t = 0; t < so.len; ++t) {
+      const int i = so.comp == 0 ? so.i + t : so.i;
+      const int j = so.comp == 0 ? so.j : so.j + t;
+      if (!edge_updated(sh, so.comp, i, j))
+        return fail(ctx, FDTD_EINVAL, "fdtd_run: source " + std::to_string(s) +
+                                          " drives a PEC, interface or covered edge");
+      const int tile = sh.tile_base + (j / kTileRows) * sh.ncx + i / kCtaCols;
+      for (const SrcEdge& o : per[tile])
+        if (o.sim == so.sim && o.comp == so.comp && o.i == i && o.j == j)
+          return fail(ctx, FDTD_EINVAL, "fdtd_run: two sources drive the same edge");
+      per[tile].push_back({so.sim, so.comp, i, j, s, {0, 0, 0}});
+    }
+  }
+  std::vector<int2> range(ntiles);
+  std::vector<SrcEdge> edges;
+  for (int t = 0; t < ntiles; ++t) {
+    range[t].x = (int)edges.size();
+    edges.insert(edges.end(), per[t].begin(), per[t].end());
+    range[t].y = (int)edges.size();
+  }
+  std::vector<int> psim(nprobe), pcell(nprobe);
+  for (int p = 0; p < nprobe; ++p) {
+    const fdtd_probe& pr = probes[p];
+    if (pr.sim < 0 || pr.sim >= (int)ctx->sims.size())
+      return fail(ctx, FDTD_EINVAL, "fdtd_run: probe sim out of range");
+    const SimHost& sh = ctx->sims[pr.sim];
+    if (pr.i < 0 || pr.i >= sh.nx || pr.j < 0 || pr.j >= sh.ny)
+      return fail(ctx, FDTD_EINVAL, "fdtd_run: probe outside the grid");
+    psim[p] = pr.sim;
+    pcell[p] = pr.j * sh.pitch + pr.i;
+  }
+  if (nprobe > 0 && !probe_out) return fail(ctx, FDTD_EINVAL, "fdtd_run: probe_out is NULL");
+  CK(ctx->src_range.reserve(ntiles));
+  CK(ctx->src_edges.reserve(edges.size()));
+  CK(ctx->waves.reserve(std::max(nsrc, 1)));
+  CK(ctx->probe_sim.reserve(std::max(nprobe, 1)));
+  CK(ctx->probe_cell.reserve(std::max(nprobe, 1)));
+  cudaStream_t st = ctx->stream;
+  CK(cudaMemcpyAsync(ctx->src_range.p, range.data(), sizeof(int2) * ntiles, cudaMemcpyHostToDevice, st));
+  if (!edges.empty())
+    CK(cudaMemcpyAsync(ctx->src_edges.p, edges.data(), sizeof(SrcEdge) * edges.size(), cudaMemcpyHostToDevice, st));
+  if (nsrc > 0)
+    CK(cudaMemcpyAsync(ctx->waves.p, wave_dev, sizeof(float*) * nsrc, cudaMemcpyHostToDevice, st));
+  if (nprobe > 0) {
+    CK(cudaMemcpyAsync(ctx->probe_sim.p, psim.data(), sizeof(int) * nprobe, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(ctx->probe_cell.p, pcell.data(), sizeof(int) * nprobe, cudaMemcpyHostToDevice, st));
+  }
+  RunDev rd{};
+  rd.base = 0;
+  rd.nsteps = nsteps;
+  rd.waves = ctx->waves.p;
+  rd.src_range = ctx->src_range.p;
+  rd.src_edges = ctx->src_edges.p;
+  rd.probe_out = probe_out;
+  rd.probe_sim = ctx->probe_sim.p;
+  rd.probe_cell = ctx->probe_cell.p;
+  rd.nprobe = nprobe;
+  // Pageable host sources: cudaMemcpyAsync returns once the data are staged,
+  // so the host vectors may go out of scope; the copies stay stream-ordered.
+  CK(cudaMemcpyAsync(ctx->run_d, &rd, sizeof(RunDev), cudaMemcpyHostToDevice, st));
+  return FDTD_OK;
+}
+
+// Sums the elapsed times of the recorded event triples (yee, post).
+int drain_events(fdtd_ctx* ctx) {
+  for (int k = 0; k + 2 < ctx->ev_used; k += 3) {
+    CK(cudaEventSynchronize(ctx->ev[k + 2]));
+    float a = 0.f, b = 0.f;
+    CK(cudaEventElapsedTime(&a, ctx->ev[k], ctx->ev[k + 1]));
+    CK(cudaEventElapsedTime(&b, ctx->ev[k + 1], ctx->ev[k + 2]));
+    ctx->t_yee += a;
+    ctx->t_post += b;
+  }
+  ctx->ev_used = 0;
+  return FDTD_OK;
+}
+
+int march_timed(fdtd_ctx* ctx, long long nsteps, int nprobe) {
+  const int nprobe_blocks = (nprobe + 255) / 256;
+  const bool post = ctx->nromwork + nprobe_blocks > 0;
+  while ((int)ctx->ev.size() < 3 * 64) {
+    cudaEvent_t e;
+    CK(cudaEventCreate(&e));
+    ctx->ev.push_back(e);
+  }
+  for (long long t = 0; t < nsteps; ++t) {
+    const int par = ctx->cur ^ (int)(t & 1);
+    cudaEvent_t* e = &ctx->ev[ctx->ev_used];
+    CK(cudaEventRecord(e[0], ctx->stream));
+    // the step index for sources/probes is base + c with base = 0 here
+    yee_step_kernel<<<(unsigned)ctx->tiles.size(), kWarpsPerCta * 32, 0, ctx->stream>>>(
+        ctx->sims_d, ctx->tiles_d, ctx->run_d, par, 0);
+    CK(cudaEventRecord(e[1], ctx->stream));
+    if (post)
+      rom_post_kernel<<<ctx->nromwork + nprobe_blocks, 256, ctx->post_smem, ctx->stream>>>(
+          ctx->sims_d, ctx->insts_d, ctx->romwork_d, ctx->nromwork, ctx->run_d, par, 0);
+    CK(cudaEventRecord(e[2], ctx->stream));
+    advance_kernel<<<1, 32, 0, ctx->stream>>>(ctx->run_d, 1);
+    CK(cudaGetLastError());
+    ctx->n_yee += 1;
+    ctx->n_post += post ? 1 : 0;
+    ctx->ev_used += 3;
+    if (ctx->ev_used == (int)ctx->ev.size()) {
+      int rc = drain_events(ctx);
+      if (rc) return rc;
+    }
+  }
+  ctx->cur ^= (int)(nsteps & 1);
+  ctx->step += nsteps;
+  return FDTD_OK;
+}
+
+int march(fdtd_ctx* ctx, long long nsteps, int nprobe) {
+  if (ctx->timing) return march_timed(ctx, nsteps, nprobe);
+  const int nprobe_blocks = (nprobe + 255) / 256;
+  long long done = 0;
+  if (nsteps >= kChunk) {
+    int rc = ensure_graph(ctx, ctx->cur, nprobe_blocks);
+    if (rc) return rc;
+    for (; done + kChunk <= nsteps; done += kChunk) CK(cudaGraphLaunch(ctx->graph[ctx->cur], ctx->stream));
+  }
+  const int rem = (int)(nsteps - done);
+  for (int c = 0; c < rem; ++c) launch_step(ctx, ctx->stream, ctx->cur ^ (c & 1), c, nprobe_blocks);
+  CK(cudaGetLastError());
+  ctx->cur ^= (rem & 1);
+  ctx->step += nsteps;
+  return FDTD_OK;
+}
+
+}  // namespace
+
+// ============================================================== C ABI
+
+extern "C" {
+
+const char* fdtd_last_error(const fdtd_ctx* ctx) {
+  if (ctx) return ctx->err.c_str();
+  std::lock_guard<std::mutex> lk(g_err_mu);
+  static thread_local std::string copy;
+  copy = g_err;
+  return copy.c_str();
+}
+
+int fdtd_cfl_limit(double dx, double dy, double* out) {
+  if (!(dx > 0) || !(dy > 0) || !out) return set_global_error(FDTD_EINVAL, "fdtd_cfl_limit: bad argument");
+  const double c0 = 1.0 / std::sqrt(kEps0 * kMu0);
+  *out = 1.0 / (c0 * std::sqrt(1.0 / (dx * dx) + 1.0 / (dy * dy)));
+  return FDTD_OK;
+}
+
+void fdtd_destroy(fdtd_ctx* ctx) {
+  if (!ctx) return;
+  drop_graphs(ctx);
+  for (SimHost& s : ctx->sims) {
+    for (int p = 0; p < 2; ++p) {
+      cudaFree(s.ex[p]);
+      cudaFree(s.ey[p]);
+      cudaFree(s.hz[p]);
+    }
+    cudaFree(s.mat_d);
+  }
+  for (Instance& in : ctx->insts) {
+    cudaFree(in.P_d);
+    cudaFree(in.Q_d);
+    cudaFree(in.state_d[0]);
+    cudaFree(in.state_d[1]);
+    cudaFree(in.y_edge_d);
+    cudaFree(in.h_cell_d);
+  }
+  cudaFree(ctx->sims_d);
+  cudaFree(ctx->tiles_d);
+  cudaFree(ctx->insts_d);
+  cudaFree(ctx->romwork_d);
+  cudaFree(ctx->run_d);
+  ctx->src_range.release();
+  ctx->src_edges.release();
+  ctx->waves.release();
+  ctx->probe_sim.release();
+  ctx->probe_cell.release();
+  ctx->host_waves.release();
+  ctx->host_probes.release();
+  for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
+  if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
+  delete ctx;
+}
+
+int fdtd_create(const fdtd_grid_desc* g, void* cuda_stream, fdtd_ctx** out) {
+  fdtd_ctx* ctx = nullptr;
+  if (!g || !out || g->nsim < 1 || !g->sims) return fail(ctx, FDTD_EINVAL, "fdtd_create: null or empty descriptor");
+  if (!(g->dx > 0) || !(g->dy > 0) || !(g->dt > 0)) return fail(ctx, FDTD_EINVAL, "fdtd_create: dx, dy, dt must be > 0");
+  double lim;
+  fdtd_cfl_limit(g->dx, g->dy, &lim);
+  if (!(g->dt < lim)) return fail(ctx, FDTD_ECFL, "fdtd_create: dt is not below the coarse CFL limit (Eq. (1))");
+  for (int s = 0; s < g->nsim; ++s) {
+    const fdtd_sim_desc& sd = g->sims[s];
+    if (sd.nx < 2 || sd.ny < 2 || !sd.eps_r || !sd.sigma)
+      return fail(ctx, FDTD_EINVAL, "fdtd_create: simulation " + std::to_string(s) + " malformed");
+    if ((long long)(sd.ny + 1) * (((sd.nx + 1 + 127) / 128) * 128) >= (1ll << 30))
+      return fail(ctx, FDTD_EINVAL, "fdtd_create: grid too large (2^30 floats per field)");
+    for (long long k = 0; k < (long long)sd.nx * sd.ny; ++k)
+      if (!(sd.eps_r[k] > 0) || !(sd.sigma[k] >= 0))
+        return fail(ctx, FDTD_EINVAL, "fdtd_create: eps_r must be > 0 and sigma >= 0");
+  }
+  ctx = new (std::nothrow) fdtd_ctx();
+  if (!ctx) return set_global_error(FDTD_ENOMEM, "fdtd_create: out of host memory");
+  ctx->stream = (cudaStream_t)cuda_stream;
+  ctx->dx = g->dx, ctx->dy = g->dy, ctx->dt = g->dt;
+  auto bail = [&](int code) {
+    std::string m = ctx->err;
+    fdtd_destroy(ctx);
+    set_global_error(code, m);
+    return code;
+  };
+  if (cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    ctx->err = "fdtd_create: cannot create a CUDA stream";
+    return bail(FDTD_ECUDA);
+  }
+  ctx->sims.resize(g->nsim);
+  std::vector<SimDev> sdev(g->nsim);
+  for (int s = 0; s < g->nsim; ++s) {
+    const fdtd_sim_desc& d = g->sims[s];
+    SimHost& sh = ctx->sims[s];
+    sh.nx = d.nx, sh.ny = d.ny;
+    sh.pitch = ((d.nx + 1 + 127) / 128) * 128;
+    const size_t ncell = (size_t)d.nx * d.ny;
+    sh.eps_r.assign(d.eps_r, d.eps_r + ncell);
+    sh.sigma.assign(d.sigma, d.sigma + ncell);
+    sh.region.assign(ncell, 0);
+    sh.mat.assign((size_t)(d.ny + 1) * sh.pitch, make_float2(0.f, 0.f));
+    for (int j = 0; j < d.ny; ++j)
+      for (int i = 0; i < d.nx; ++i) {
+        const size_t k = (size_t)j * d.nx + i;
+        sh.mat[(size_t)j * sh.pitch + i] =
+            make_float2((float)(kEps0 * d.eps_r[k] / g->dt), (float)(0.5 * d.sigma[k]));
+      }
+    const size_t bytes = sizeof(float) * (size_t)(d.ny + 1) * sh.pitch;
+    for (int p = 0; p < 2; ++p) {
+      if (cudaMalloc(&sh.ex[p], bytes) != cudaSuccess || cudaMalloc(&sh.ey[p], bytes) != cudaSuccess ||
+          cudaMalloc(&sh.hz[p], bytes) != cudaSuccess) {
+        ctx->err = "fdtd_create: device allocation failed";
+        return bail(FDTD_ENOMEM);
+      }
+      cudaMemset(sh.ex[p], 0, bytes);
+      cudaMemset(sh.ey[p], 0, bytes);
+      cudaMemset(sh.hz[p], 0, bytes);
+    }
+    if (cudaMalloc(&sh.mat_d, sizeof(float2) * sh.mat.size()) != cudaSuccess) {
+      ctx->err = "fdtd_create: device allocation failed";
+      return bail(FDTD_ENOMEM);
+    }
+    cudaMemcpy(sh.mat_d, sh.mat.data(), sizeof(float2) * sh.mat.size(), cudaMemcpyHostToDevice);
+    SimDev& sd = sdev[s];
+    for (int p = 0; p < 2; ++p) sd.ex[p] = sh.ex[p], sd.ey[p] = sh.ey[p], sd.hz[p] = sh.hz[p];
+    sd.mat = sh.mat_d;
+    sd.nx = d.nx, sd.ny = d.ny, sd.pitch = sh.pitch;
+    sd.chx = (float)(g->dt / (kMu0 * g->dy));
+    sd.chy = (float)(g->dt / (kMu0 * g->dx));
+    sd.rdy = (float)(1.0 / g->dy);
+    sd.rdx = (float)(1.0 / g->dx);
+    sh.ncx = (d.nx + kCtaCols - 1) / kCtaCols;
+    sh.ncy = (d.ny + kTileRows - 1) / kTileRows;
+    sh.tile_base = (int)ctx->tiles.size();
+    for (int ty = 0; ty < sh.ncy; ++ty)
+      for (int tx = 0; tx < sh.ncx; ++tx) ctx->tiles.push_back({s, tx * kCtaCols, ty * kTileRows, 0});
+  }
+  if (cudaMalloc(&ctx->sims_d, sizeof(SimDev) * sdev.size()) != cudaSuccess ||
+      cudaMalloc(&ctx->tiles_d, sizeof(TileWork) * ctx->tiles.size()) != cudaSuccess ||
+      cudaMalloc(&ctx->run_d, sizeof(RunDev)) != cudaSuccess) {
+    ctx->err = "fdtd_create: device allocation failed";
+    return bail(FDTD_ENOMEM);
+  }
+  cudaMemcpy(ctx->sims_d, sdev.data(), sizeof(SimDev) * sdev.size(), cudaMemcpyHostToDevice);
+  cudaMemcpy(ctx->tiles_d, ctx->tiles.data(), sizeof(TileWork) * ctx->tiles.size(), cudaMemcpyHostToDevice);
+  cudaMemset(ctx->run_d, 0, sizeof(RunDev));
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    ctx->err = std::string("fdtd_create: ") + cudaGetErrorString(e);
+    return bail(FDTD_ECUDA);
+  }
+  *out = ctx;
+  return FDTD_OK;
+}
+
+int rom_embed(fdtd_ctx* ctx, const rom_model* m, int sim, int i0, int j0, int* inst_out) {
+  if (!ctx || !m) return fail(ctx, FDTD_EINVAL, "rom_embed: null argument");
+  if (sim < 0 || sim >= (int)ctx->sims.size()) return fail(ctx, FDTD_EINVAL, "rom_embed: sim out of range");
+  if (std::fabs(m->dt - ctx->dt) > 1e-12 * ctx->dt || std::fabs(m->dx - ctx->dx) > 1e-12 * ctx->dx ||
+      std::fabs(m->dy - ctx->dy) > 1e-12 * ctx->dy)
+    return fail(ctx, FDTD_EINVAL, "rom_embed: model built for another dx, dy or dt");
+  SimHost& sh = ctx->sims[sim];
+  const int a = m->a, b = m->b;
+  if (i0 < 1 || j0 < 1 || i0 + a > sh.nx - 1 || j0 + b > sh.ny - 1)
+    return fail(ctx, FDTD_EINVAL, "rom_embed: region must keep one coarse cell from the walls");
+  for (int j = j0 - 1; j <= j0 + b; ++j)
+    for (int i = i0 - 1; i <= i0 + a; ++i)
+      if (sh.region[(size_t)j * sh.nx + i])
+        return fail(ctx, FDTD_EINVAL, "rom_embed: region overlaps or touches another region");
+  Instance in;
+  in.sim = sim, in.i0 = i0, in.j0 = j0, in.a = a, in.b = b, in.q = m->qE + m->qH;
+  in.itf = make_interface(i0, j0, a, b, ctx->dx, ctx->dy, ctx->dt, sh.eps_r.data(), sh.sigma.data(), sh.nx);
+  std::string msg;
+  int rc = couple(*m, in.itf, ctx->dt, in.P, in.Q, msg);
+  if (rc) return fail(ctx, rc, "rom_embed: " + msg);
+  in.ny = in.itf.ny;
+  in.n = in.ny + in.q;
+  for (int k = 0; k < in.ny; ++k) {
+    in.y_edge.push_back((in.itf.comp[k] << 30) | (in.itf.ej[k] * sh.pitch + in.itf.ei[k]));
+    in.h_cell.push_back(in.itf.hj[k] * sh.pitch + in.itf.hi[k]);
+  }
+  std::vector<float> Pf(in.P.a.begin(), in.P.a.end()), Qf(in.Q.a.begin(), in.Q.a.end());
+  CK(cudaMalloc(&in.P_d, sizeof(float) * Pf.size()));
+  CK(cudaMalloc(&in.Q_d, sizeof(float) * Qf.size()));
+  CK(cudaMalloc(&in.state_d[0], sizeof(float) * in.n));
+  CK(cudaMalloc(&in.state_d[1], sizeof(float) * in.n));
+  CK(cudaMalloc(&in.y_edge_d, sizeof(int) * in.ny));
+  CK(cudaMalloc(&in.h_cell_d, sizeof(int) * in.ny));
+  CK(cudaMemcpy(in.P_d, Pf.data(), sizeof(float) * Pf.size(), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(in.Q_d, Qf.data(), sizeof(float) * Qf.size(), cudaMemcpyHostToDevice));
+  CK(cudaMemset(in.state_d[0], 0, sizeof(float) * in.n));
+  CK(cudaMemset(in.state_d[1], 0, sizeof(float) * in.n));
+  CK(cudaMemcpy(in.y_edge_d, in.y_edge.data(), sizeof(int) * in.ny, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(in.h_cell_d, in.h_cell.data(), sizeof(int) * in.ny, cudaMemcpyHostToDevice));
+  // Mark the covered cells and zero every field on and inside the region.
+  CK(cudaStreamSynchronize(ctx->stream));
+  for (int j = j0; j < j0 + b; ++j)
+    for (int i = i0; i < i0 + a; ++i) {
+      sh.region[(size_t)j * sh.nx + i] = 1;
+      sh.mat[(size_t)j * sh.pitch + i].x = -1.f;
+    }
+  CK(cudaMemcpy(sh.mat_d, sh.mat.data(), sizeof(float2) * sh.mat.size(), cudaMemcpyHostToDevice));
+  for (int p = 0; p < 2; ++p) {
+    for (int j = j0; j <= j0 + b; ++j) {
+      CK(cudaMemset(sh.ex[p] + (size_t)j * sh.pitch + i0, 0, sizeof(float) * a));
+      if (j < j0 + b) {
+        CK(cudaMemset(sh.ey[p] + (size_t)j * sh.pitch + i0, 0, sizeof(float) * (a + 1)));
+        CK(cudaMemset(sh.hz[p] + (size_t)j * sh.pitch + i0, 0, sizeof(float) * a));
+      }
+    }
+  }
+  ctx->insts.push_back(std::move(in));
+  rc = upload_instances(ctx);
+  if (rc) return rc;
+  if (inst_out) *inst_out = (int)ctx->insts.size() - 1;
+  return FDTD_OK;
+}
+
+int fdtd_get_rom_map(const fdtd_ctx* ctx, int inst, int* n, int* ny, double* P, double* Q) {
+  if (!ctx || inst < 0 || inst >= (int)ctx->insts.size())
+    return set_global_error(FDTD_EINVAL, "fdtd_get_rom_map: bad instance");
+  const Instance& in = ctx->insts[inst];
+  if (n) *n = in.n;
+  if (ny) *ny = in.ny;
+  if (P) std::memcpy(P, in.P.a.data(), sizeof(double) * in.P.a.size());
+  if (Q) std::memcpy(Q, in.Q.a.data(), sizeof(double) * in.Q.a.size());
+  return FDTD_OK;
+}
+
+int fdtd_run(fdtd_ctx* ctx, long long nsteps, const fdtd_source* src, int nsrc,
+             const fdtd_probe* probes, int nprobe, float* probe_out) {
+  if (!ctx || nsteps < 0 || nsrc < 0 || nprobe < 0 || (nsrc && !src) || (nprobe && !probes))
+    return fail(ctx, FDTD_EINVAL, "fdtd_run: bad argument");
+  if (nsteps == 0) return FDTD_OK;
+  std::vector<const float*> w(std::max(nsrc, 1));
+  for (int s = 0; s < nsrc; ++s) w[s] = src[s].wave;
+  int rc = prepare_run(ctx, nsteps, src, nsrc, w.data(), probes, nprobe, probe_out);
+  if (rc) return rc;
+  return march(ctx, nsteps, nprobe);
+}
+
+int fdtd_run_host(fdtd_ctx* ctx, long long nsteps, const fdtd_source* src, int nsrc,
+                  const fdtd_probe* probes, int nprobe, float* probe_out_host) {
+  if (!ctx || nsteps < 0 || nsrc < 0 || nprobe < 0 || (nsrc && !src) || (nprobe && !probes) ||
+      (nprobe && !probe_out_host))
+    return fail(ctx, FDTD_EINVAL, "fdtd_run_host: bad argument");
+  if (nsteps == 0) return FDTD_OK;
+  for (int s = 0; s < nsrc; ++s)
+    if (!src[s].wave) return fail(ctx, FDTD_EINVAL, "fdtd_run_host: null waveform");
+  CK(ctx->host_waves.reserve((size_t)std::max(nsrc, 1) * nsteps));
+  CK(ctx->host_probes.reserve((size_t)std::max(nprobe, 1) * nsteps));
+  std::vector<const float*> w(std::max(nsrc, 1));
+  for (int s = 0; s < nsrc; ++s) {
+    w[s] = ctx->host_waves.p + (size_t)s * nsteps;
+    CK(cudaMemcpyAsync((void*)w[s], src[s].wave, sizeof(float) * nsteps, cudaMemcpyHostToDevice, ctx->stream));
+  }
+  int rc = prepare_run(ctx, nsteps, src, nsrc, w.data(), probes, nprobe, ctx->host_probes.p);
+  if (rc) return rc;
+  rc = march(ctx, nsteps, nprobe);
+  if (rc) return rc;
+  if (nprobe > 0)
+    CK(cudaMemcpyAsync(probe_out_host, ctx->host_probes.p, sizeof(float) * nsteps * nprobe,
+                       cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return FDTD_OK;
+}
+
+int fdtd_get_fields(fdtd_ctx* ctx, int sim, float* Ex, float* Ey, float* Hz) {
+  if (!ctx || sim < 0 || sim >= (int)ctx->sims.size()) return fail(ctx, FDTD_EINVAL, "fdtd_get_fields: bad sim");
+  const SimHost& sh = ctx->sims[sim];
+  const int c = ctx->cur;
+  const size_t sp = sizeof(float) * sh.pitch;
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (Ex) CK(cudaMemcpy2D(Ex, sizeof(float) * sh.nx, sh.ex[c], sp, sizeof(float) * sh.nx, sh.ny + 1, cudaMemcpyDeviceToHost));
+  if (Ey) CK(cudaMemcpy2D(Ey, sizeof(float) * (sh.nx + 1), sh.ey[c], sp, sizeof(float) * (sh.nx + 1), sh.ny, cudaMemcpyDeviceToHost));
+  if (Hz) CK(cudaMemcpy2D(Hz, sizeof(float) * sh.nx, sh.hz[c], sp, sizeof(float) * sh.nx, sh.ny, cudaMemcpyDeviceToHost));
+  return FDTD_OK;
+}
+
+int fdtd_set_fields(fdtd_ctx* ctx, int sim, const float* Ex, const float* Ey, const float* Hz) {
+  if (!ctx || sim < 0 || sim >= (int)ctx->sims.size() || !Ex || !Ey || !Hz)
+    return fail(ctx, FDTD_EINVAL, "fdtd_set_fields: bad argument");
+  const SimHost& sh = ctx->sims[sim];
+  const int nx = sh.nx, ny = sh.ny;
+  // Clean copies: PEC walls and covered cells/edges held at 0.
+  std::vector<float> ex((size_t)(ny + 1) * nx, 0.f), ey((size_t)ny * (nx + 1), 0.f), hz((size_t)ny * nx, 0.f);
+  auto reg = [&](int i, int j) { return sh.region[(size_t)j * nx + i] != 0; };
+  for (int j = 1; j < ny; ++j)
+    for (int i = 0; i < nx; ++i)
+      if (!(reg(i, j - 1) && reg(i, j))) ex[(size_t)j * nx + i] = Ex[(size_t)j * nx + i];
+  for (int j = 0; j < ny; ++j)
+    for (int i = 1; i < nx; ++i)
+      if (!(reg(i - 1, j) && reg(i, j))) ey[(size_t)j * (nx + 1) + i] = Ey[(size_t)j * (nx + 1) + i];
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i)
+      if (!reg(i, j)) hz[(size_t)j * nx + i] = Hz[(size_t)j * nx + i];
+  const size_t dp = sizeof(float) * sh.pitch;
+  CK(cudaStreamSynchronize(ctx->stream));
+  for (int p = 0; p < 2; ++p) {
+    CK(cudaMemcpy2D(sh.ex[p], dp, ex.data(), sizeof(float) * nx, sizeof(float) * nx, ny + 1, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy2D(sh.ey[p], dp, ey.data(), sizeof(float) * (nx + 1), sizeof(float) * (nx + 1), ny, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy2D(sh.hz[p], dp, hz.data(), sizeof(float) * nx, sizeof(float) * nx, ny, cudaMemcpyHostToDevice));
+  }
+  // Interface values become each model's y.
+  for (Instance& in : ctx->insts) {
+    if (in.sim != sim) continue;
+    std::vector<float> y(in.ny);
+    for (int k = 0; k < in.ny; ++k)
+      y[k] = in.itf.comp[k] == 0 ? ex[(size_t)in.itf.ej[k] * nx + in.itf.ei[k]]
+                                 : ey[(size_t)in.itf.ej[k] * (nx + 1) + in.itf.ei[k]];
+    for (int p = 0; p < 2; ++p) CK(cudaMemcpy(in.state_d[p], y.data(), sizeof(float) * in.ny, cudaMemcpyHostToDevice));
+  }
+  return FDTD_OK;
+}
+
+int fdtd_get_rom_state(fdtd_ctx* ctx, int inst, float* x) {
+  if (!ctx || inst < 0 || inst >= (int)ctx->insts.size() || !x) return fail(ctx, FDTD_EINVAL, "fdtd_get_rom_state: bad argument");
+  const Instance& in = ctx->insts[inst];
+  CK(cudaStreamSynchronize(ctx->stream));
+  CK(cudaMemcpy(x, in.state_d[ctx->cur] + in.ny, sizeof(float) * in.q, cudaMemcpyDeviceToHost));
+  return FDTD_OK;
+}
+
+int fdtd_set_rom_state(fdtd_ctx* ctx, int inst, const float* x) {
+  if (!ctx || inst < 0 || inst >= (int)ctx->insts.size() || !x) return fail(ctx, FDTD_EINVAL, "fdtd_set_rom_state: bad argument");
+  const Instance& in = ctx->insts[inst];
+  CK(cudaStreamSynchronize(ctx->stream));
+  for (int p = 0; p < 2; ++p) CK(cudaMemcpy(in.state_d[p] + in.ny, x, sizeof(float) * in.q, cudaMemcpyHostToDevice));
+  return FDTD_OK;
+}
+
+int fdtd_set_timing(fdtd_ctx* ctx, int on) {
+  if (!ctx) return set_global_error(FDTD_EINVAL, "fdtd_set_timing: null context");
+  if (ctx->timing) {
+    int rc = drain_events(ctx);
+    if (rc) return rc;
+  }
+  ctx->timing = on != 0;
+  ctx->t_yee = ctx->t_post = 0;
+  ctx->n_yee = ctx->n_post = 0;
+  ctx->ev_used = 0;
+  return FDTD_OK;
+}
+
+int fdtd_get_kernel_times(fdtd_ctx* ctx, double* yee_ms, long long* yee_launches, double* post_ms,
+                          long long* post_launches) {
+  if (!ctx) return set_global_error(FDTD_EINVAL, "fdtd_get_kernel_times: null context");
+  int rc = drain_events(ctx);
+  if (rc) return rc;
+  if (yee_ms) *yee_ms = ctx->t_yee;
+  if (yee_launches) *yee_launches = ctx->n_yee;
+  if (post_ms) *post_ms = ctx->t_post;
+  if (post_launches) *post_launches = ctx->n_post;
+  return FDTD_OK;
+}
+
+int fdtd_get_step(const fdtd_ctx* ctx, long long* n) {
+  if (!ctx || !n) return set_global_error(FDTD_EINVAL, "fdtd_get_step: bad argument");
+  *n = ctx->step;
+  return FDTD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,75 @@
+// Device kernels of the time-marching hot path (sm_103a).
+//
+// One time step n -> n+1 (Sec. IV-C) is two launches:
+//   yee_step   : coarse Hz^{n+1/2} (Eq. (5)) and coarse E^{n+1} (Eq. (3))
+//                fused per tile, plus the source current on its edges;
+//   rom_post   : every embedded model's run-time map (Eq. (23)),
+//                [y; x~]^{n+1} = P [y; x~]^n + Q h^{n+1/2}, and the probes.
+// Fields are ping-ponged between two buffers (read p, write 1-p), so tiles
+// can recompute their one-cell H halo without racing their neighbours.
+//
+// Memory layout per simulation: Ex, Ey, Hz each (ny+1) rows x pitch floats,
+// row-major, pitch a multiple of 128 floats (512 B) and > nx; cell materials
+// as float2 {eps0 eps_r / dt, sigma/2}, the first component set to -1 for
+// cells covered by a reduced model.  An E edge is updated only if both its
+// cells are coarse cells and it is not on the PEC wall.
+#pragma once
+
+#include <cstdint>
+
+namespace fdtdrom {
+
+constexpr int kStripCols = 128;   // columns per warp strip (32 lanes x float4)
+constexpr int kTileRows = 32;     // rows per tile
+constexpr int kWarpsPerCta = 4;   // strips per CTA
+constexpr int kCtaCols = kStripCols * kWarpsPerCta;
+
+struct SimDev {
+  float* ex[2];
+  float* ey[2];
+  float* hz[2];
+  const float2* mat;
+  int nx, ny, pitch, pad;
+  float chx;   // dt / (mu0 dy):  Hz += chx (Ex_{j+1} - Ex_j)
+  float chy;   // dt / (mu0 dx):  Hz -= chy (Ey_{i+1} - Ey_i)
+  float rdy;   // 1/dy: Ex += cb (Hz_j - Hz_{j-1}) / dy
+  float rdx;   // 1/dx: Ey -= cb (Hz_i - Hz_{i-1}) / dx
+};
+
+struct TileWork {   // one CTA of yee_step
+  int sim, x0, y0, pad;
+};
+
+struct SrcEdge {    // one driven edge
+  int sim, comp, i, j;
+  int src;          // index of the waveform
+  int pad[3];
+};
+
+struct RomInstDev {
+  const float* P;     // n x n row-major
+  const float* Q;     // n x ny row-major
+  float* state[2];    // [y; x~], ping-ponged with the fields
+  const int* y_edge;  // ny: (comp << 30) | (j * pitch + i)
+  const int* h_cell;  // ny: j * pitch + i
+  int n, ny, sim, pad;
+};
+
+struct RomWork {    // one CTA of rom_post: rows [row0, row1) of one instance
+  int inst, row0, row1, pad;
+};
+
+struct RunDev {
+  long long base;            // step index, relative to the run start, of chunk step 0
+  long long nsteps;
+  const float* const* waves; // per source: device samples J(t^{n+1/2})
+  const int2* src_range;     // per yee_step CTA: [begin, end) into src_edges
+  const SrcEdge* src_edges;
+  float* probe_out;          // [nsteps][nprobe]
+  const int* probe_sim;
+  const int* probe_cell;     // j * pitch + i
+  int nprobe;
+  int pad;
+};
+
+}  // namespace fdtdrom
