@@ -111,9 +111,12 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
-def build_problem(nsteps_total):
+def build_problem(nsteps_total, grid=4096):
     import workloads
-    return workloads.grid_4096(nsteps_total)
+    if grid == 4096:
+        return workloads.grid_4096(nsteps_total)
+    # same recipe at another size (profiling captures of a smaller case)
+    return workloads.random_grid(1, grid, grid, 8, 16, 4, 200, nsteps_total, dt_factor=0.95)
 
 
 def cpu_sample(w, steps):
@@ -179,6 +182,7 @@ def main():
     ap.add_argument("--tsteps", type=int, default=2000, help="time steps per benchmark step")
     ap.add_argument("--cpu-sample-steps", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--grid", type=int, default=4096, help="coarse grid size (4096 = the benchmark)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -204,7 +208,7 @@ def main():
 
     K, W, T = args.steps, args.warmup, args.tsteps
     total = (W + K) * T
-    w = build_problem(total)
+    w = build_problem(total, args.grid)
     ctx = pg.FdtdContext(w["dx"], w["dy"], w["dt"], [(w["eps_r"], w["sigma"])])
     models = []
     t0 = time.perf_counter()
@@ -289,7 +293,8 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": W,
         "ms_per_step": el_ms / K, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "time_steps_per_step": T, "nx": w["nx"], "ny": w["ny"],
+        "config": {"workload": WORKLOAD if args.grid == 4096 else f"grid {args.grid}^2, same recipe",
+                   "time_steps_per_step": T, "nx": w["nx"], "ny": w["ny"],
                    "roms": len(w["roms"]), "rom_q": [m.q for m in models],
                    "rom_build_s": round(rom_seconds, 3),
                    "l2": "inputs larger than L2: 0.47 GB of fields+materials per time step (L2 129 MB)",

@@ -44,7 +44,37 @@ __device__ __forceinline__ void edge_coef(float2 m1, float2 m2, float& ca, float
 // previous row's fields and new Hz in registers; lane l owns columns
 // c0 + 4l .. c0 + 4l + 3.  The first iteration recomputes the halo row
 // j0 - 1 of Hz^{n+1/2}; lane 0 also recomputes the halo column c0 - 1.
-__global__ void __launch_bounds__(kWarpsPerCta * 32)
+// The loads of row j+1 are issued before row j is computed (two rows in
+// flight per warp).
+struct RowIn {
+  float4 exn, eyv, hzv, ma, mb;  // Ex(j+1), Ey(j), Hz(j), mat(j) for the lane's 4 columns
+  float eyR;                     // lane 31: Ey(c0+128, j)
+  float exLn, eyL, hzL;          // lane 0: halo column c0-1
+  float2 mL;
+};
+
+__device__ __forceinline__ void load_row(RowIn& r, const float* __restrict__ ex,
+                                         const float* __restrict__ ey, const float* __restrict__ hz,
+                                         const float2* __restrict__ mat, size_t row, int P, int cl,
+                                         int c0, int nx, int lane, bool halo) {
+  r.exn = ld4(ex + row + P + cl);
+  r.eyv = ld4(ey + row + cl);
+  r.hzv = ld4(hz + row + cl);
+  r.ma = ld4(reinterpret_cast<const float*>(mat + row + cl));
+  r.mb = ld4(reinterpret_cast<const float*>(mat + row + cl + 2));
+  r.eyR = (lane == 31 && c0 + kStripCols <= nx) ? ey[row + c0 + kStripCols] : 0.f;
+  if (halo) {
+    r.exLn = ex[row + P + c0 - 1];
+    r.eyL = ey[row + c0 - 1];
+    r.hzL = hz[row + c0 - 1];
+    r.mL = mat[row + c0 - 1];
+  } else {
+    r.exLn = r.eyL = r.hzL = 0.f;
+    r.mL = make_float2(-1.f, 0.f);
+  }
+}
+
+__global__ void __launch_bounds__(kWarpsPerCta * 32, 4)
 yee_step_kernel(const SimDev* __restrict__ sims, const TileWork* __restrict__ work,
                 const RunDev* __restrict__ run, int par, int c) {
   const TileWork tw = work[blockIdx.x];
@@ -72,17 +102,16 @@ yee_step_kernel(const SimDev* __restrict__ sims, const TileWork* __restrict__ wo
     float2 mp[4];
 #pragma unroll
     for (int t = 0; t < 4; ++t) mp[t] = make_float2(0.f, 0.f);
+    RowIn cur, nxt;
+    load_row(cur, ex, ey, hz, mat, (size_t)j * P, P, cl, c0, nx, lane, halo);
     for (; j < j1; ++j) {
       const size_t row = (size_t)j * P;
-      const float4 exn = ld4(ex + row + P + cl);
-      const float4 eyv = ld4(ey + row + cl);
-      const float4 hzv = ld4(hz + row + cl);
-      const float4 ma = ld4(reinterpret_cast<const float*>(mat + row + cl));
-      const float4 mb = ld4(reinterpret_cast<const float*>(mat + row + cl + 2));
-      const float2 m[4] = {make_float2(ma.x, ma.y), make_float2(ma.z, ma.w),
-                           make_float2(mb.x, mb.y), make_float2(mb.z, mb.w)};
+      if (j + 1 < j1) load_row(nxt, ex, ey, hz, mat, row + P, P, cl, c0, nx, lane, halo);
+      const float4 exn = cur.exn, eyv = cur.eyv, hzv = cur.hzv;
+      const float2 m[4] = {make_float2(cur.ma.x, cur.ma.y), make_float2(cur.ma.z, cur.ma.w),
+                           make_float2(cur.mb.x, cur.mb.y), make_float2(cur.mb.z, cur.mb.w)};
       float eyR = __shfl_down_sync(FULL, eyv.x, 1);
-      if (lane == 31) eyR = (c0 + kStripCols <= nx) ? ey[row + c0 + kStripCols] : 0.f;
+      if (lane == 31) eyR = cur.eyR;
       const float eyA[5] = {eyv.x, eyv.y, eyv.z, eyv.w, eyR};
       // Eq. (5): Hz^{n+1/2} = Hz^{n-1/2} + dt/(mu0 dy)(Ex_{j+1} - Ex_j)
       //                                  - dt/(mu0 dx)(Ey_{i+1} - Ey_i)
@@ -99,17 +128,11 @@ yee_step_kernel(const SimDev* __restrict__ sims, const TileWork* __restrict__ wo
       float2 mL;
       mL.x = __shfl_up_sync(FULL, m[3].x, 1);
       mL.y = __shfl_up_sync(FULL, m[3].y, 1);
-      float exLn = 0.f;
       if (lane == 0) {
-        hnL = 0.f;
-        mL = make_float2(-1.f, 0.f);
-        if (halo) {
-          exLn = ex[row + P + c0 - 1];
-          const float eyL = ey[row + c0 - 1];
-          const float hzL = hz[row + c0 - 1];
-          mL = mat[row + c0 - 1];
-          hnL = (mL.x >= 0.f) ? hzL + sd.chx * (exLn - exLc) - sd.chy * (eyv.x - eyL) : 0.f;
-        }
+        mL = cur.mL;
+        hnL = (halo && mL.x >= 0.f)
+                  ? cur.hzL + sd.chx * (cur.exLn - exLc) - sd.chy * (eyv.x - cur.eyL)
+                  : 0.f;
       }
       if (j >= j0) {
         st4(hzo + row + cl, make_float4(hn[0], hn[1], hn[2], hn[3]));
@@ -145,10 +168,11 @@ yee_step_kernel(const SimDev* __restrict__ sims, const TileWork* __restrict__ wo
         st4(eyo + row + cl, make_float4(eyw[0], eyw[1], eyw[2], eyw[3]));
       }
       exc = exn;
-      exLc = exLn;
+      exLc = cur.exLn;
       hzp = make_float4(hn[0], hn[1], hn[2], hn[3]);
 #pragma unroll
       for (int t = 0; t < 4; ++t) mp[t] = m[t];
+      cur = nxt;
     }
   }
   // Source currents on this tile's edges: E^{n+1} -= cb J(t^{n+1/2}).
@@ -169,12 +193,15 @@ yee_step_kernel(const SimDev* __restrict__ sims, const TileWork* __restrict__ wo
   }
 }
 
-// Eq. (23) for every embedded model, then the probes.
-__global__ void __launch_bounds__(256)
+// Eq. (23) for every embedded model, then the probes.  A CTA takes
+// kRomRowsPerCta rows of one model, one row per warp: v = [y; x~; h] is staged
+// in shared memory and each warp forms one dot product with [P | Q] using
+// float4 loads (all of a row's loads are in flight together).
+__global__ void __launch_bounds__(kRomRowsPerCta * 32)
 rom_post_kernel(const SimDev* __restrict__ sims, const RomInstDev* __restrict__ insts,
                 const RomWork* __restrict__ work, int nwork, const RunDev* __restrict__ run,
                 int par, int c) {
-  extern __shared__ float smem[];
+  extern __shared__ float4 smem4[];
   const unsigned FULL = 0xffffffffu;
   if ((int)blockIdx.x < nwork) {
     const RomWork w = work[blockIdx.x];
@@ -185,18 +212,29 @@ rom_post_kernel(const SimDev* __restrict__ sims, const RomInstDev* __restrict__ 
     const float* __restrict__ hzn = par ? sd.hz[0] : sd.hz[1];
     float* __restrict__ exo = par ? sd.ex[0] : sd.ex[1];
     float* __restrict__ eyo = par ? sd.ey[0] : sd.ey[1];
-    float* sv = smem;
-    float* hv = smem + ri.n;
-    for (int k = threadIdx.x; k < ri.n; k += blockDim.x) sv[k] = s[k];
-    for (int k = threadIdx.x; k < ri.ny; k += blockDim.x) hv[k] = hzn[ri.h_cell[k]];
+    float* v = reinterpret_cast<float*>(smem4);
+    for (int k = threadIdx.x; k < ri.ld; k += blockDim.x) {
+      float x = 0.f;
+      if (k < ri.n) x = s[k];
+      else if (k < ri.n + ri.ny) x = hzn[ri.h_cell[k - ri.n]];
+      v[k] = x;
+    }
     __syncthreads();
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    for (int r = w.row0 + warp; r < w.row1; r += nw) {
-      const float* __restrict__ Pr = ri.P + (size_t)r * ri.n;
-      const float* __restrict__ Qr = ri.Q + (size_t)r * ri.ny;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int r = w.row0 + warp;
+    if (r < w.row1) {
+      const float4* __restrict__ Mr = reinterpret_cast<const float4*>(ri.M + (size_t)r * ri.ld);
+      const int l4 = ri.ld >> 2;
       float acc = 0.f;
-      for (int k = lane; k < ri.n; k += 32) acc = fmaf(Pr[k], sv[k], acc);
-      for (int k = lane; k < ri.ny; k += 32) acc = fmaf(Qr[k], hv[k], acc);
+#pragma unroll 4
+      for (int k = lane; k < l4; k += 32) {
+        const float4 m = Mr[k];
+        const float4 x = smem4[k];
+        acc = fmaf(m.x, x.x, acc);
+        acc = fmaf(m.y, x.y, acc);
+        acc = fmaf(m.z, x.z, acc);
+        acc = fmaf(m.w, x.w, acc);
+      }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
       if (lane == 0) {
@@ -260,8 +298,8 @@ struct Instance {
   int sim = 0, i0 = 0, j0 = 0, a = 0, b = 0, q = 0, ny = 0, n = 0;
   InterfaceDesc itf;
   la::Mat P, Q;
-  float* P_d = nullptr;
-  float* Q_d = nullptr;
+  int ld = 0;
+  float* M_d = nullptr;
   float* state_d[2] = {nullptr, nullptr};
   int* y_edge_d = nullptr;
   int* h_cell_d = nullptr;
@@ -352,13 +390,13 @@ int upload_instances(fdtd_ctx* ctx) {
   for (size_t k = 0; k < ctx->insts.size(); ++k) {
     const Instance& in = ctx->insts[k];
     RomInstDev& d = h[k];
-    d.P = in.P_d, d.Q = in.Q_d;
+    d.M = in.M_d;
     d.state[0] = in.state_d[0], d.state[1] = in.state_d[1];
     d.y_edge = in.y_edge_d, d.h_cell = in.h_cell_d;
-    d.n = in.n, d.ny = in.ny, d.sim = in.sim;
-    const int rows_per = 64;
-    for (int r0 = 0; r0 < in.n; r0 += rows_per) wk.push_back({(int)k, r0, std::min(in.n, r0 + rows_per), 0});
-    smem = std::max(smem, sizeof(float) * (size_t)(in.n + in.ny));
+    d.n = in.n, d.ny = in.ny, d.ld = in.ld, d.sim = in.sim;
+    for (int r0 = 0; r0 < in.n; r0 += kRomRowsPerCta)
+      wk.push_back({(int)k, r0, std::min(in.n, r0 + kRomRowsPerCta), 0});
+    smem = std::max(smem, sizeof(float) * (size_t)in.ld);
   }
   if (ctx->insts_d) cudaFree(ctx->insts_d);
   if (ctx->romwork_d) cudaFree(ctx->romwork_d);
@@ -386,8 +424,8 @@ void launch_step(fdtd_ctx* ctx, cudaStream_t s, int par, int c, int nprobe_block
       ctx->sims_d, ctx->tiles_d, ctx->run_d, par, c);
   const int nb = ctx->nromwork + nprobe_blocks;
   if (nb > 0)
-    rom_post_kernel<<<nb, 256, ctx->post_smem, s>>>(ctx->sims_d, ctx->insts_d, ctx->romwork_d,
-                                                    ctx->nromwork, ctx->run_d, par, c);
+    rom_post_kernel<<<nb, kRomRowsPerCta * 32, ctx->post_smem, s>>>(
+        ctx->sims_d, ctx->insts_d, ctx->romwork_d, ctx->nromwork, ctx->run_d, par, c);
 }
 
 int ensure_graph(fdtd_ctx* ctx, int par, int nprobe_blocks) {
@@ -506,7 +544,7 @@ int drain_events(fdtd_ctx* ctx) {
 }
 
 int march_timed(fdtd_ctx* ctx, long long nsteps, int nprobe) {
-  const int nprobe_blocks = (nprobe + 255) / 256;
+  const int nprobe_blocks = (nprobe + kRomRowsPerCta * 32 - 1) / (kRomRowsPerCta * 32);
   const bool post = ctx->nromwork + nprobe_blocks > 0;
   while ((int)ctx->ev.size() < 3 * 64) {
     cudaEvent_t e;
@@ -522,7 +560,7 @@ int march_timed(fdtd_ctx* ctx, long long nsteps, int nprobe) {
         ctx->sims_d, ctx->tiles_d, ctx->run_d, par, 0);
     CK(cudaEventRecord(e[1], ctx->stream));
     if (post)
-      rom_post_kernel<<<ctx->nromwork + nprobe_blocks, 256, ctx->post_smem, ctx->stream>>>(
+      rom_post_kernel<<<ctx->nromwork + nprobe_blocks, kRomRowsPerCta * 32, ctx->post_smem, ctx->stream>>>(
           ctx->sims_d, ctx->insts_d, ctx->romwork_d, ctx->nromwork, ctx->run_d, par, 0);
     CK(cudaEventRecord(e[2], ctx->stream));
     advance_kernel<<<1, 32, 0, ctx->stream>>>(ctx->run_d, 1);
@@ -542,7 +580,7 @@ int march_timed(fdtd_ctx* ctx, long long nsteps, int nprobe) {
 
 int march(fdtd_ctx* ctx, long long nsteps, int nprobe) {
   if (ctx->timing) return march_timed(ctx, nsteps, nprobe);
-  const int nprobe_blocks = (nprobe + 255) / 256;
+  const int nprobe_blocks = (nprobe + kRomRowsPerCta * 32 - 1) / (kRomRowsPerCta * 32);
   long long done = 0;
   if (nsteps >= kChunk) {
     int rc = ensure_graph(ctx, ctx->cur, nprobe_blocks);
@@ -590,8 +628,7 @@ void fdtd_destroy(fdtd_ctx* ctx) {
     cudaFree(s.mat_d);
   }
   for (Instance& in : ctx->insts) {
-    cudaFree(in.P_d);
-    cudaFree(in.Q_d);
+    cudaFree(in.M_d);
     cudaFree(in.state_d[0]);
     cudaFree(in.state_d[1]);
     cudaFree(in.y_edge_d);
@@ -737,15 +774,19 @@ int rom_embed(fdtd_ctx* ctx, const rom_model* m, int sim, int i0, int j0, int* i
     in.y_edge.push_back((in.itf.comp[k] << 30) | (in.itf.ej[k] * sh.pitch + in.itf.ei[k]));
     in.h_cell.push_back(in.itf.hj[k] * sh.pitch + in.itf.hi[k]);
   }
-  std::vector<float> Pf(in.P.a.begin(), in.P.a.end()), Qf(in.Q.a.begin(), in.Q.a.end());
-  CK(cudaMalloc(&in.P_d, sizeof(float) * Pf.size()));
-  CK(cudaMalloc(&in.Q_d, sizeof(float) * Qf.size()));
+  // [P | Q] in FP32, rows padded to a multiple of 4 floats (16-B aligned).
+  in.ld = ((in.n + in.ny + 3) / 4) * 4;
+  std::vector<float> Mf((size_t)in.n * in.ld, 0.f);
+  for (int r = 0; r < in.n; ++r) {
+    for (int k = 0; k < in.n; ++k) Mf[(size_t)r * in.ld + k] = (float)in.P(r, k);
+    for (int k = 0; k < in.ny; ++k) Mf[(size_t)r * in.ld + in.n + k] = (float)in.Q(r, k);
+  }
+  CK(cudaMalloc(&in.M_d, sizeof(float) * Mf.size()));
   CK(cudaMalloc(&in.state_d[0], sizeof(float) * in.n));
   CK(cudaMalloc(&in.state_d[1], sizeof(float) * in.n));
   CK(cudaMalloc(&in.y_edge_d, sizeof(int) * in.ny));
   CK(cudaMalloc(&in.h_cell_d, sizeof(int) * in.ny));
-  CK(cudaMemcpy(in.P_d, Pf.data(), sizeof(float) * Pf.size(), cudaMemcpyHostToDevice));
-  CK(cudaMemcpy(in.Q_d, Qf.data(), sizeof(float) * Qf.size(), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(in.M_d, Mf.data(), sizeof(float) * Mf.size(), cudaMemcpyHostToDevice));
   CK(cudaMemset(in.state_d[0], 0, sizeof(float) * in.n));
   CK(cudaMemset(in.state_d[1], 0, sizeof(float) * in.n));
   CK(cudaMemcpy(in.y_edge_d, in.y_edge.data(), sizeof(int) * in.ny, cudaMemcpyHostToDevice));

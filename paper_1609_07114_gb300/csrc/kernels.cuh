@@ -47,13 +47,14 @@ struct SrcEdge {    // one driven edge
 };
 
 struct RomInstDev {
-  const float* P;     // n x n row-major
-  const float* Q;     // n x ny row-major
+  const float* M;     // n x ld row-major: [P | Q | 0], ld = roundup(n + ny, 4)
   float* state[2];    // [y; x~], ping-ponged with the fields
   const int* y_edge;  // ny: (comp << 30) | (j * pitch + i)
   const int* h_cell;  // ny: j * pitch + i
-  int n, ny, sim, pad;
+  int n, ny, ld, sim;
 };
+
+constexpr int kRomRowsPerCta = 8;   // one row per warp
 
 struct RomWork {    // one CTA of rom_post: rows [row0, row1) of one instance
   int inst, row0, row1, pad;
