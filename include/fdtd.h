@@ -212,6 +212,17 @@ int fdtd_set_rom_state(fdtd_ctx* ctx, int inst, const float* x);
 /* Number of steps taken since creation. */
 int fdtd_get_step(const fdtd_ctx* ctx, long long* n);
 
+/* Discrete storage function (Sec. V, Appendix A) of every simulation at the
+ * current step, x = [E^n; Hz^{n-1/2}]:
+ *   W = 1/2 E^T D_eps E + 1/2 H^T D_mu H - dt/2 E^T K H      (coarse system,
+ *       interface edges on their coarse half cell, Eqs. (13)-(14))
+ *     + dt/2 x~^T R~ x~                                      (each model, Eq. (12)).
+ * Lossless and source-free, W is constant; with losses it does not
+ * increase.  FP32 state, FP64 accumulation.  out: host double[nsim].
+ * Uses a device scratch buffer owned by the context (allocated on first
+ * use).  Synchronises the context's stream. */
+int fdtd_energy(fdtd_ctx* ctx, double* out);
+
 /* ------------------------------------------------------------ measurement */
 
 /* When on, fdtd_run launches every step directly (no CUDA graph) and records

@@ -95,6 +95,7 @@ def lib() -> C.CDLL:
         "fdtd_get_rom_state": (i, [vp, i, _fp]),
         "fdtd_set_rom_state": (i, [vp, i, _fp]),
         "fdtd_get_step": (i, [vp, C.POINTER(ll)]),
+        "fdtd_energy": (i, [vp, _dp]),
         "fdtd_set_timing": (i, [vp, i]),
         "fdtd_get_kernel_times": (i, [vp, _dp, C.POINTER(ll), _dp, C.POINTER(ll)]),
         "fdtd_last_error": (C.c_char_p, [vp]),
@@ -306,6 +307,12 @@ class FdtdContext:
         n = C.c_longlong()
         self._ck(lib().fdtd_get_step(self._h, C.byref(n)))
         return n.value
+
+    def energy(self):
+        """Storage function W of every simulation (``fdtd_energy``)."""
+        out = np.zeros(len(self.shapes))
+        self._ck(lib().fdtd_energy(self._h, out.ctypes.data_as(_dp)))
+        return out
 
     def set_timing(self, on: bool):
         self._ck(lib().fdtd_set_timing(self._h, int(bool(on))))

@@ -9,6 +9,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -19,6 +20,10 @@
 #include "kernels.cuh"
 
 using namespace fdtdrom;
+
+namespace {
+__device__ constexpr double kMu0d = 1.25663706212e-6;   // CODATA 2018
+}
 
 // ============================================================== device code
 
@@ -40,29 +45,46 @@ __device__ __forceinline__ void edge_coef(float2 m1, float2 m2, float& ca, float
 }
 
 // Fused coarse H and E half steps over one tile (module header).
-// Each warp marches up a strip of 128 columns x kTileRows rows, keeping the
+// Each warp marches up a strip of 32 V columns x (y1 - y0) rows, keeping the
 // previous row's fields and new Hz in registers; lane l owns columns
-// c0 + 4l .. c0 + 4l + 3.  The first iteration recomputes the halo row
-// j0 - 1 of Hz^{n+1/2}; lane 0 also recomputes the halo column c0 - 1.
+// c0 + V l .. c0 + V l + V - 1.  The first iteration recomputes the halo row
+// y0 - 1 of Hz^{n+1/2}; lane 0 also recomputes the halo column c0 - 1.
 // The loads of row j+1 are issued before row j is computed (two rows in
 // flight per warp).
+template <int V>
+struct Vec;
+template <>
+struct Vec<4> {
+  using T = float4;
+  __device__ static float get(const float4& v, int t) { return comp(v, t); }
+};
+template <>
+struct Vec<2> {
+  using T = float2;
+  __device__ static float get(const float2& v, int t) { return t == 0 ? v.x : v.y; }
+};
+
+template <int V>
 struct RowIn {
-  float4 exn, eyv, hzv, ma, mb;  // Ex(j+1), Ey(j), Hz(j), mat(j) for the lane's 4 columns
-  float eyR;                     // lane 31: Ey(c0+128, j)
-  float exLn, eyL, hzL;          // lane 0: halo column c0-1
+  typename Vec<V>::T exn, eyv, hzv;  // Ex(j+1), Ey(j), Hz(j) of the lane's V columns
+  float4 m4[V / 2];                  // mat(j) of the lane's V cells (2 cells per float4)
+  float eyR;                         // lane 31: Ey(c0 + 32V, j)
+  float exLn, eyL, hzL;              // lane 0: halo column c0 - 1
   float2 mL;
 };
 
-__device__ __forceinline__ void load_row(RowIn& r, const float* __restrict__ ex,
+template <int V>
+__device__ __forceinline__ void load_row(RowIn<V>& r, const float* __restrict__ ex,
                                          const float* __restrict__ ey, const float* __restrict__ hz,
                                          const float2* __restrict__ mat, size_t row, int P, int cl,
                                          int c0, int nx, int lane, bool halo) {
-  r.exn = ld4(ex + row + P + cl);
-  r.eyv = ld4(ey + row + cl);
-  r.hzv = ld4(hz + row + cl);
-  r.ma = ld4(reinterpret_cast<const float*>(mat + row + cl));
-  r.mb = ld4(reinterpret_cast<const float*>(mat + row + cl + 2));
-  r.eyR = (lane == 31 && c0 + kStripCols <= nx) ? ey[row + c0 + kStripCols] : 0.f;
+  using T = typename Vec<V>::T;
+  r.exn = *reinterpret_cast<const T*>(ex + row + P + cl);
+  r.eyv = *reinterpret_cast<const T*>(ey + row + cl);
+  r.hzv = *reinterpret_cast<const T*>(hz + row + cl);
+#pragma unroll
+  for (int h = 0; h < V / 2; ++h) r.m4[h] = ld4(reinterpret_cast<const float*>(mat + row + cl + 2 * h));
+  r.eyR = (lane == 31 && c0 + 32 * V <= nx) ? ey[row + c0 + 32 * V] : 0.f;
   if (halo) {
     r.exLn = ex[row + P + c0 - 1];
     r.eyL = ey[row + c0 - 1];
@@ -74,14 +96,17 @@ __device__ __forceinline__ void load_row(RowIn& r, const float* __restrict__ ex,
   }
 }
 
-__global__ void __launch_bounds__(kWarpsPerCta * 32, 4)
+template <int V>
+__global__ void __launch_bounds__(kCtaCols / V, V == 4 ? 4 : 3)
 yee_step_kernel(const SimDev* __restrict__ sims, const TileWork* __restrict__ work,
                 const RunDev* __restrict__ run, int par, int c) {
+  using VT = Vec<V>;
+  constexpr int kStrip = 32 * V;
   const TileWork tw = work[blockIdx.x];
   const SimDev sd = sims[tw.sim];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int c0 = tw.x0 + warp * kStripCols;
-  const int nx = sd.nx, ny = sd.ny, P = sd.pitch;
+  const int c0 = tw.x0 + warp * kStrip;
+  const int nx = sd.nx, P = sd.pitch;
   // (ternaries, not sd.ex[par]: a dynamic index would put sd in local memory)
   const float* __restrict__ ex = par ? sd.ex[1] : sd.ex[0];
   const float* __restrict__ ey = par ? sd.ey[1] : sd.ey[0];
@@ -92,67 +117,74 @@ yee_step_kernel(const SimDev* __restrict__ sims, const TileWork* __restrict__ wo
   const float2* __restrict__ mat = sd.mat;
   const unsigned FULL = 0xffffffffu;
   if (c0 < nx) {
-    const int cl = c0 + 4 * lane;
-    const int j0 = tw.y0, j1 = min(j0 + kTileRows, ny);
+    const int cl = c0 + V * lane;
+    const int j0 = tw.y0, j1 = tw.y1;
     int j = j0 > 0 ? j0 - 1 : 0;
     const bool halo = (lane == 0) && (c0 > 0);
-    float4 exc = ld4(ex + (size_t)j * P + cl);
-    float exLc = halo ? ex[(size_t)j * P + c0 - 1] : 0.f;
-    float4 hzp = make_float4(0.f, 0.f, 0.f, 0.f);
-    float2 mp[4];
+    float exc[V], hzp[V];
+    float2 mp[V];
 #pragma unroll
-    for (int t = 0; t < 4; ++t) mp[t] = make_float2(0.f, 0.f);
-    RowIn cur, nxt;
-    load_row(cur, ex, ey, hz, mat, (size_t)j * P, P, cl, c0, nx, lane, halo);
+    for (int t = 0; t < V; ++t) {
+      exc[t] = ex[(size_t)j * P + cl + t];
+      hzp[t] = 0.f;
+      mp[t] = make_float2(0.f, 0.f);
+    }
+    float exLc = halo ? ex[(size_t)j * P + c0 - 1] : 0.f;
+    RowIn<V> cur, nxt;
+    load_row<V>(cur, ex, ey, hz, mat, (size_t)j * P, P, cl, c0, nx, lane, halo);
     for (; j < j1; ++j) {
       const size_t row = (size_t)j * P;
-      if (j + 1 < j1) load_row(nxt, ex, ey, hz, mat, row + P, P, cl, c0, nx, lane, halo);
-      const float4 exn = cur.exn, eyv = cur.eyv, hzv = cur.hzv;
-      const float2 m[4] = {make_float2(cur.ma.x, cur.ma.y), make_float2(cur.ma.z, cur.ma.w),
-                           make_float2(cur.mb.x, cur.mb.y), make_float2(cur.mb.z, cur.mb.w)};
-      float eyR = __shfl_down_sync(FULL, eyv.x, 1);
-      if (lane == 31) eyR = cur.eyR;
-      const float eyA[5] = {eyv.x, eyv.y, eyv.z, eyv.w, eyR};
+      if (j + 1 < j1) load_row<V>(nxt, ex, ey, hz, mat, row + P, P, cl, c0, nx, lane, halo);
+      float2 m[V];
+#pragma unroll
+      for (int h = 0; h < V / 2; ++h) {
+        m[2 * h] = make_float2(cur.m4[h].x, cur.m4[h].y);
+        m[2 * h + 1] = make_float2(cur.m4[h].z, cur.m4[h].w);
+      }
+      float eyA[V + 1];
+#pragma unroll
+      for (int t = 0; t < V; ++t) eyA[t] = VT::get(cur.eyv, t);
+      eyA[V] = __shfl_down_sync(FULL, eyA[0], 1);
+      if (lane == 31) eyA[V] = cur.eyR;
       // Eq. (5): Hz^{n+1/2} = Hz^{n-1/2} + dt/(mu0 dy)(Ex_{j+1} - Ex_j)
       //                                  - dt/(mu0 dx)(Ey_{i+1} - Ey_i)
-      float hn[4];
+      float hn[V];
 #pragma unroll
-      for (int t = 0; t < 4; ++t) {
+      for (int t = 0; t < V; ++t) {
         const bool live = (cl + t < nx) && (m[t].x >= 0.f);
-        hn[t] = live ? comp(hzv, t) + sd.chx * (comp(exn, t) - comp(exc, t)) -
+        hn[t] = live ? VT::get(cur.hzv, t) + sd.chx * (VT::get(cur.exn, t) - exc[t]) -
                            sd.chy * (eyA[t + 1] - eyA[t])
                      : 0.f;
       }
       // Left neighbour of column cl: lane - 1's last cell, or the halo column.
-      float hnL = __shfl_up_sync(FULL, hn[3], 1);
+      float hnL = __shfl_up_sync(FULL, hn[V - 1], 1);
       float2 mL;
-      mL.x = __shfl_up_sync(FULL, m[3].x, 1);
-      mL.y = __shfl_up_sync(FULL, m[3].y, 1);
+      mL.x = __shfl_up_sync(FULL, m[V - 1].x, 1);
+      mL.y = __shfl_up_sync(FULL, m[V - 1].y, 1);
       if (lane == 0) {
         mL = cur.mL;
         hnL = (halo && mL.x >= 0.f)
-                  ? cur.hzL + sd.chx * (cur.exLn - exLc) - sd.chy * (eyv.x - cur.eyL)
+                  ? cur.hzL + sd.chx * (cur.exLn - exLc) - sd.chy * (eyA[0] - cur.eyL)
                   : 0.f;
       }
       if (j >= j0) {
-        st4(hzo + row + cl, make_float4(hn[0], hn[1], hn[2], hn[3]));
+        float exw[V], eyw[V];
         // Eq. (3): Ex^{n+1} = ca Ex^n + cb (Hz_j - Hz_{j-1}) / dy on edge (i, j),
         // between cells (i, j-1) and (i, j).
-        float exw[4], eyw[4];
 #pragma unroll
-        for (int t = 0; t < 4; ++t) {
-          float v = comp(exc, t);
+        for (int t = 0; t < V; ++t) {
+          float v = exc[t];
           if (j >= 1 && cl + t < nx && mp[t].x >= 0.f && m[t].x >= 0.f) {
             float ca, cb;
             edge_coef(mp[t], m[t], ca, cb);
-            v = ca * v + cb * sd.rdy * (hn[t] - comp(hzp, t));
+            v = ca * v + cb * sd.rdy * (hn[t] - hzp[t]);
           }
           exw[t] = v;
         }
         // Ey^{n+1} = ca Ey^n - cb (Hz_i - Hz_{i-1}) / dx on edge (i, j),
         // between cells (i-1, j) and (i, j).
 #pragma unroll
-        for (int t = 0; t < 4; ++t) {
+        for (int t = 0; t < V; ++t) {
           const int i = cl + t;
           const float2 ml = t == 0 ? mL : m[t - 1];
           const float hl = t == 0 ? hnL : hn[t - 1];
@@ -164,14 +196,23 @@ yee_step_kernel(const SimDev* __restrict__ sims, const TileWork* __restrict__ wo
           }
           eyw[t] = v;
         }
-        st4(exo + row + cl, make_float4(exw[0], exw[1], exw[2], exw[3]));
-        st4(eyo + row + cl, make_float4(eyw[0], eyw[1], eyw[2], eyw[3]));
+        if constexpr (V == 4) {
+          st4(hzo + row + cl, make_float4(hn[0], hn[1], hn[2], hn[3]));
+          st4(exo + row + cl, make_float4(exw[0], exw[1], exw[2], exw[3]));
+          st4(eyo + row + cl, make_float4(eyw[0], eyw[1], eyw[2], eyw[3]));
+        } else {
+          *reinterpret_cast<float2*>(hzo + row + cl) = make_float2(hn[0], hn[1]);
+          *reinterpret_cast<float2*>(exo + row + cl) = make_float2(exw[0], exw[1]);
+          *reinterpret_cast<float2*>(eyo + row + cl) = make_float2(eyw[0], eyw[1]);
+        }
       }
-      exc = exn;
-      exLc = cur.exLn;
-      hzp = make_float4(hn[0], hn[1], hn[2], hn[3]);
 #pragma unroll
-      for (int t = 0; t < 4; ++t) mp[t] = m[t];
+      for (int t = 0; t < V; ++t) {
+        exc[t] = VT::get(cur.exn, t);
+        hzp[t] = hn[t];
+        mp[t] = m[t];
+      }
+      exLc = cur.exLn;
       cur = nxt;
     }
   }
@@ -212,6 +253,20 @@ rom_post_kernel(const SimDev* __restrict__ sims, const RomInstDev* __restrict__ 
     const float* __restrict__ hzn = par ? sd.hz[0] : sd.hz[1];
     float* __restrict__ exo = par ? sd.ex[0] : sd.ex[1];
     float* __restrict__ eyo = par ? sd.ey[0] : sd.ey[1];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int r = w.row0 + warp;
+    const bool has = r < w.row1;
+    const float4* __restrict__ Mr = reinterpret_cast<const float4*>(ri.M + (size_t)(has ? r : w.row0) * ri.ld);
+    const int l4 = ri.ld >> 2;
+    // The first 128 float4 of this warp's row go to registers before the
+    // input vector is staged, so both sets of loads are in flight together.
+    constexpr int kPre = 4;
+    float4 mpre[kPre];
+#pragma unroll
+    for (int u = 0; u < kPre; ++u) {
+      const int k = lane + 32 * u;
+      mpre[u] = (has && k < l4) ? Mr[k] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
     float* v = reinterpret_cast<float*>(smem4);
     for (int k = threadIdx.x; k < ri.ld; k += blockDim.x) {
       float x = 0.f;
@@ -220,14 +275,20 @@ rom_post_kernel(const SimDev* __restrict__ sims, const RomInstDev* __restrict__ 
       v[k] = x;
     }
     __syncthreads();
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int r = w.row0 + warp;
-    if (r < w.row1) {
-      const float4* __restrict__ Mr = reinterpret_cast<const float4*>(ri.M + (size_t)r * ri.ld);
-      const int l4 = ri.ld >> 2;
+    if (has) {
       float acc = 0.f;
-#pragma unroll 4
-      for (int k = lane; k < l4; k += 32) {
+#pragma unroll
+      for (int u = 0; u < kPre; ++u) {
+        const int k = lane + 32 * u;
+        if (k < l4) {
+          const float4 x = smem4[k];
+          acc = fmaf(mpre[u].x, x.x, acc);
+          acc = fmaf(mpre[u].y, x.y, acc);
+          acc = fmaf(mpre[u].z, x.z, acc);
+          acc = fmaf(mpre[u].w, x.w, acc);
+        }
+      }
+      for (int k = lane + 32 * kPre; k < l4; k += 32) {
         const float4 m = Mr[k];
         const float4 x = smem4[k];
         acc = fmaf(m.x, x.x, acc);
@@ -255,6 +316,111 @@ rom_post_kernel(const SimDev* __restrict__ sims, const RomInstDev* __restrict__ 
       run->probe_out[n * run->nprobe + p] = hzn[run->probe_cell[p]];
     }
   }
+}
+
+// ---- storage function (Sec. V, Appendix A), FP64 accumulation -------------
+
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  const unsigned FULL = 0xffffffffu;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  v = 0.0;
+  if (warp == 0) {
+    v = lane < nw ? red[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+  }
+  return v;  // valid in thread 0
+}
+
+// Coarse part over one stencil tile: 1/2 eps A E^2 - dt/2 E (K H) on every
+// updated edge, 1/2 mu0 A H^2 on every coarse cell.
+__global__ void __launch_bounds__(256)
+energy_cells_kernel(const SimDev* __restrict__ sims, const TileWork* __restrict__ work, int par,
+                    double dt, double dx, double dy, double* __restrict__ partial) {
+  __shared__ double red[32];
+  const TileWork tw = work[blockIdx.x];
+  const SimDev sd = sims[tw.sim];
+  const float* __restrict__ ex = par ? sd.ex[1] : sd.ex[0];
+  const float* __restrict__ ey = par ? sd.ey[1] : sd.ey[0];
+  const float* __restrict__ hz = par ? sd.hz[1] : sd.hz[0];
+  const float2* __restrict__ mat = sd.mat;
+  const int P = sd.pitch;
+  const int nxs = min(kCtaCols, sd.nx - tw.x0), nys = tw.y1 - tw.y0;
+  const double area = dx * dy;
+  double acc = 0.0;
+  for (int k = threadIdx.x; k < nxs * nys; k += blockDim.x) {
+    const int i = tw.x0 + k % nxs, j = tw.y0 + k / nxs;
+    const size_t off = (size_t)j * P + i;
+    const float2 m = mat[off];
+    if (m.x < 0.f) continue;
+    const double h = hz[off];
+    acc += 0.5 * area * kMu0d * h * h;
+    if (j >= 1) {
+      const float2 mb = mat[off - P];
+      if (mb.x >= 0.f) {
+        const double e = ex[off];
+        const double eps = 0.5 * ((double)m.x + (double)mb.x) * dt;
+        acc += 0.5 * area * eps * e * e - 0.5 * dt * e * dx * (h - (double)hz[off - P]);
+      }
+    }
+    if (i >= 1) {
+      const float2 ml = mat[off - 1];
+      if (ml.x >= 0.f) {
+        const double e = ey[off];
+        const double eps = 0.5 * ((double)m.x + (double)ml.x) * dt;
+        acc += 0.5 * area * eps * e * e + 0.5 * dt * e * dy * (h - (double)hz[off - 1]);
+      }
+    }
+  }
+  acc = block_sum(acc, red);
+  if (threadIdx.x == 0) partial[blockIdx.x] = acc;
+}
+
+// One model: dt/2 x~^T R~ x~ plus its interface half cells.
+__global__ void __launch_bounds__(256)
+energy_rom_kernel(const SimDev* __restrict__ sims, const RomInstDev* __restrict__ insts,
+                  const EnergyInstDev* __restrict__ einst, int par, double dt,
+                  double* __restrict__ partial) {
+  __shared__ double red[32];
+  const RomInstDev ri = insts[blockIdx.x];
+  const EnergyInstDev ei = einst[blockIdx.x];
+  const SimDev sd = sims[ri.sim];
+  const float* __restrict__ st = par ? ri.state[1] : ri.state[0];
+  const float* __restrict__ hz = par ? sd.hz[1] : sd.hz[0];
+  const float* __restrict__ x = st + ri.ny;
+  double acc = 0.0;
+  for (int r = threadIdx.x; r < ei.q; r += blockDim.x) {
+    double s = 0.0;
+    const double* Rr = ei.R + (size_t)r * ei.q;
+    for (int k = 0; k < ei.q; ++k) s += Rr[k] * (double)x[k];
+    acc += 0.5 * dt * (double)x[r] * s;
+  }
+  for (int k = threadIdx.x; k < ri.ny; k += blockDim.x) {
+    const double y = st[k];
+    const double h = hz[ri.h_cell[k]];
+    acc += ei.c1[k] * y * y - ei.c2[k] * y * h;
+  }
+  acc = block_sum(acc, red);
+  if (threadIdx.x == 0) partial[blockIdx.x] = acc;
+}
+
+// Per simulation: sum of its tiles' and models' partial sums.
+__global__ void __launch_bounds__(256)
+energy_sum_kernel(const double* __restrict__ tile_part, const int* __restrict__ tile_base,
+                  const double* __restrict__ inst_part, const RomInstDev* __restrict__ insts,
+                  int ninst, double* __restrict__ out) {
+  __shared__ double red[32];
+  const int s = blockIdx.x;
+  double acc = 0.0;
+  for (int t = tile_base[s] + threadIdx.x; t < tile_base[s + 1]; t += blockDim.x) acc += tile_part[t];
+  for (int k = threadIdx.x; k < ninst; k += blockDim.x)
+    if (insts[k].sim == s) acc += inst_part[k];
+  acc = block_sum(acc, red);
+  if (threadIdx.x == 0) out[s] = acc;
 }
 
 __global__ void advance_kernel(RunDev* run, int by) {
@@ -291,7 +457,7 @@ struct SimHost {
   float* ey[2] = {nullptr, nullptr};
   float* hz[2] = {nullptr, nullptr};
   float2* mat_d = nullptr;
-  int tile_base = 0, ncx = 0, ncy = 0;
+  int tile_base = 0, ncx = 0, ncy = 0, th = 0;   // tiles: ncx x ncy of kCtaCols x th cells
 };
 
 struct Instance {
@@ -304,6 +470,8 @@ struct Instance {
   int* y_edge_d = nullptr;
   int* h_cell_d = nullptr;
   std::vector<int> y_edge, h_cell;
+  double* R_d = nullptr;   // R~ (q x q, FP64) for the storage function
+  double* c_d = nullptr;   // c1 (ny) then c2 (ny)
 };
 
 template <class T>
@@ -334,6 +502,7 @@ struct fdtd_ctx {
   double dx = 0, dy = 0, dt = 0;
   std::vector<SimHost> sims;
   std::vector<TileWork> tiles;
+  int vec = 4;                     // columns per lane of the stencil kernel (2 or 4)
   SimDev* sims_d = nullptr;
   TileWork* tiles_d = nullptr;
   std::vector<Instance> insts;
@@ -342,6 +511,9 @@ struct fdtd_ctx {
   int nromwork = 0;
   size_t post_smem = 0;
   RunDev* run_d = nullptr;
+  EnergyInstDev* einst_d = nullptr;
+  DevBuf<double> energy_scratch;   // per-tile and per-model partial sums, per-sim totals
+  int* tile_base_d = nullptr;      // nsim + 1 tile offsets
   DevBuf<int2> src_range;
   DevBuf<SrcEdge> src_edges;
   DevBuf<const float*> waves;
@@ -400,9 +572,18 @@ int upload_instances(fdtd_ctx* ctx) {
   }
   if (ctx->insts_d) cudaFree(ctx->insts_d);
   if (ctx->romwork_d) cudaFree(ctx->romwork_d);
+  if (ctx->einst_d) cudaFree(ctx->einst_d);
   ctx->insts_d = nullptr;
   ctx->romwork_d = nullptr;
+  ctx->einst_d = nullptr;
   if (!h.empty()) {
+    std::vector<EnergyInstDev> eh(ctx->insts.size());
+    for (size_t k = 0; k < ctx->insts.size(); ++k) {
+      const Instance& in = ctx->insts[k];
+      eh[k] = {in.R_d, in.c_d, in.c_d + in.ny, in.q, in.sim, 0, 0};
+    }
+    CK(cudaMalloc(&ctx->einst_d, sizeof(EnergyInstDev) * eh.size()));
+    CK(cudaMemcpy(ctx->einst_d, eh.data(), sizeof(EnergyInstDev) * eh.size(), cudaMemcpyHostToDevice));
     CK(cudaMalloc(&ctx->insts_d, sizeof(RomInstDev) * h.size()));
     CK(cudaMemcpy(ctx->insts_d, h.data(), sizeof(RomInstDev) * h.size(), cudaMemcpyHostToDevice));
     CK(cudaMalloc(&ctx->romwork_d, sizeof(RomWork) * wk.size()));
@@ -418,10 +599,17 @@ int upload_instances(fdtd_ctx* ctx) {
   return FDTD_OK;
 }
 
+void launch_yee(fdtd_ctx* ctx, cudaStream_t s, int par, int c) {
+  const unsigned nb = (unsigned)ctx->tiles.size();
+  if (ctx->vec == 2)
+    yee_step_kernel<2><<<nb, kCtaCols / 2, 0, s>>>(ctx->sims_d, ctx->tiles_d, ctx->run_d, par, c);
+  else
+    yee_step_kernel<4><<<nb, kCtaCols / 4, 0, s>>>(ctx->sims_d, ctx->tiles_d, ctx->run_d, par, c);
+}
+
 // Launches one step (chunk index c) on stream s.
 void launch_step(fdtd_ctx* ctx, cudaStream_t s, int par, int c, int nprobe_blocks) {
-  yee_step_kernel<<<(unsigned)ctx->tiles.size(), kWarpsPerCta * 32, 0, s>>>(
-      ctx->sims_d, ctx->tiles_d, ctx->run_d, par, c);
+  launch_yee(ctx, s, par, c);
   const int nb = ctx->nromwork + nprobe_blocks;
   if (nb > 0)
     rom_post_kernel<<<nb, kRomRowsPerCta * 32, ctx->post_smem, s>>>(
@@ -472,7 +660,7 @@ int prepare_run(fdtd_ctx* ctx, long long nsteps, const fdtd_source* src, int nsr
       if (!edge_updated(sh, so.comp, i, j))
         return fail(ctx, FDTD_EINVAL, "fdtd_run: source " + std::to_string(s) +
                                           " drives a PEC, interface or covered edge");
-      const int tile = sh.tile_base + (j / kTileRows) * sh.ncx + i / kCtaCols;
+      const int tile = sh.tile_base + (j / sh.th) * sh.ncx + i / kCtaCols;
       for (const SrcEdge& o : per[tile])
         if (o.sim == so.sim && o.comp == so.comp && o.i == i && o.j == j)
           return fail(ctx, FDTD_EINVAL, "fdtd_run: two sources drive the same edge");
@@ -556,8 +744,7 @@ int march_timed(fdtd_ctx* ctx, long long nsteps, int nprobe) {
     cudaEvent_t* e = &ctx->ev[ctx->ev_used];
     CK(cudaEventRecord(e[0], ctx->stream));
     // the step index for sources/probes is base + c with base = 0 here
-    yee_step_kernel<<<(unsigned)ctx->tiles.size(), kWarpsPerCta * 32, 0, ctx->stream>>>(
-        ctx->sims_d, ctx->tiles_d, ctx->run_d, par, 0);
+    launch_yee(ctx, ctx->stream, par, 0);
     CK(cudaEventRecord(e[1], ctx->stream));
     if (post)
       rom_post_kernel<<<ctx->nromwork + nprobe_blocks, kRomRowsPerCta * 32, ctx->post_smem, ctx->stream>>>(
@@ -597,6 +784,52 @@ int march(fdtd_ctx* ctx, long long nsteps, int nprobe) {
 
 }  // namespace
 
+// Tile plan of the stencil kernel.  A CTA covers kCtaCols columns; the tile
+// height th (same for every simulation) is chosen so that the tiles fill
+// whole waves of resident CTAs: minimise ceil(T / slots) * (th + 1) (the +1
+// is the recomputed halo row), T = total tiles, slots = SMs x resident CTAs.
+// FDTD_VEC (2 or 4) and FDTD_TILE_ROWS override the choice (results are
+// identical; only speed changes).
+void plan_tiles(fdtd_ctx* ctx) {
+  int vec = 4;
+  if (const char* e = getenv("FDTD_VEC")) vec = (atoi(e) == 2) ? 2 : 4;
+  ctx->vec = vec;
+  int dev = 0, nsm = 1, occ = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (vec == 2)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, yee_step_kernel<2>, kCtaCols / 2, 0);
+  else
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, yee_step_kernel<4>, kCtaCols / 4, 0);
+  const long long slots = (long long)nsm * std::max(occ, 1);
+  auto total = [&](int th) {
+    long long t = 0;
+    for (const SimHost& sh : ctx->sims) t += (long long)((sh.nx + kCtaCols - 1) / kCtaCols) * ((sh.ny + th - 1) / th);
+    return t;
+  };
+  int best = 32;
+  if (const char* e = getenv("FDTD_TILE_ROWS")) {
+    best = std::max(4, atoi(e));
+  } else {
+    long long best_cost = -1;
+    for (int th = 8; th <= 128; ++th) {
+      const long long cost = ((total(th) + slots - 1) / slots) * (th + 1);
+      if (best_cost < 0 || cost <= best_cost) best_cost = cost, best = th;
+    }
+  }
+  ctx->tiles.clear();
+  for (int s = 0; s < (int)ctx->sims.size(); ++s) {
+    SimHost& sh = ctx->sims[s];
+    sh.th = best;
+    sh.ncx = (sh.nx + kCtaCols - 1) / kCtaCols;
+    sh.ncy = (sh.ny + best - 1) / best;
+    sh.tile_base = (int)ctx->tiles.size();
+    for (int ty = 0; ty < sh.ncy; ++ty)
+      for (int tx = 0; tx < sh.ncx; ++tx)
+        ctx->tiles.push_back({s, tx * kCtaCols, ty * best, std::min(sh.ny, (ty + 1) * best)});
+  }
+}
+
 // ============================================================== C ABI
 
 extern "C" {
@@ -633,12 +866,17 @@ void fdtd_destroy(fdtd_ctx* ctx) {
     cudaFree(in.state_d[1]);
     cudaFree(in.y_edge_d);
     cudaFree(in.h_cell_d);
+    cudaFree(in.R_d);
+    cudaFree(in.c_d);
   }
   cudaFree(ctx->sims_d);
   cudaFree(ctx->tiles_d);
   cudaFree(ctx->insts_d);
   cudaFree(ctx->romwork_d);
   cudaFree(ctx->run_d);
+  cudaFree(ctx->einst_d);
+  cudaFree(ctx->tile_base_d);
+  ctx->energy_scratch.release();
   ctx->src_range.release();
   ctx->src_edges.release();
   ctx->waves.release();
@@ -724,12 +962,8 @@ int fdtd_create(const fdtd_grid_desc* g, void* cuda_stream, fdtd_ctx** out) {
     sd.chy = (float)(g->dt / (kMu0 * g->dx));
     sd.rdy = (float)(1.0 / g->dy);
     sd.rdx = (float)(1.0 / g->dx);
-    sh.ncx = (d.nx + kCtaCols - 1) / kCtaCols;
-    sh.ncy = (d.ny + kTileRows - 1) / kTileRows;
-    sh.tile_base = (int)ctx->tiles.size();
-    for (int ty = 0; ty < sh.ncy; ++ty)
-      for (int tx = 0; tx < sh.ncx; ++tx) ctx->tiles.push_back({s, tx * kCtaCols, ty * kTileRows, 0});
   }
+  plan_tiles(ctx);
   if (cudaMalloc(&ctx->sims_d, sizeof(SimDev) * sdev.size()) != cudaSuccess ||
       cudaMalloc(&ctx->tiles_d, sizeof(TileWork) * ctx->tiles.size()) != cudaSuccess ||
       cudaMalloc(&ctx->run_d, sizeof(RunDev)) != cudaSuccess) {
@@ -738,6 +972,16 @@ int fdtd_create(const fdtd_grid_desc* g, void* cuda_stream, fdtd_ctx** out) {
   }
   cudaMemcpy(ctx->sims_d, sdev.data(), sizeof(SimDev) * sdev.size(), cudaMemcpyHostToDevice);
   cudaMemcpy(ctx->tiles_d, ctx->tiles.data(), sizeof(TileWork) * ctx->tiles.size(), cudaMemcpyHostToDevice);
+  {
+    std::vector<int> tb(g->nsim + 1);
+    for (int s = 0; s < g->nsim; ++s) tb[s] = ctx->sims[s].tile_base;
+    tb[g->nsim] = (int)ctx->tiles.size();
+    if (cudaMalloc(&ctx->tile_base_d, sizeof(int) * tb.size()) != cudaSuccess) {
+      ctx->err = "fdtd_create: device allocation failed";
+      return bail(FDTD_ENOMEM);
+    }
+    cudaMemcpy(ctx->tile_base_d, tb.data(), sizeof(int) * tb.size(), cudaMemcpyHostToDevice);
+  }
   cudaMemset(ctx->run_d, 0, sizeof(RunDev));
   cudaError_t e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
@@ -790,6 +1034,25 @@ int rom_embed(fdtd_ctx* ctx, const rom_model* m, int sim, int i0, int j0, int* i
   CK(cudaMemset(in.state_d[0], 0, sizeof(float) * in.n));
   CK(cudaMemset(in.state_d[1], 0, sizeof(float) * in.n));
   CK(cudaMemcpy(in.y_edge_d, in.y_edge.data(), sizeof(int) * in.ny, cudaMemcpyHostToDevice));
+  {  // storage-function data: R~ at the run dt (Eq. (12)) and the half cells
+    const int q = in.q, qE = m->qE, qH = m->qH;
+    std::vector<double> R((size_t)q * q, 0.0), cc(2 * (size_t)in.ny);
+    for (int i = 0; i < qE; ++i)
+      for (int j = 0; j < qE; ++j) R[(size_t)i * q + j] = m->R11(i, j) / ctx->dt;
+    for (int i = 0; i < qH; ++i)
+      for (int j = 0; j < qH; ++j) R[(size_t)(qE + i) * q + qE + j] = m->R22(i, j) / ctx->dt;
+    for (int i = 0; i < qE; ++i)
+      for (int j = 0; j < qH; ++j) R[(size_t)i * q + qE + j] = R[(size_t)(qE + j) * q + i] = -0.5 * m->Kt(i, j);
+    for (int k = 0; k < in.ny; ++k) {
+      // dplus = Dl Dl' (eps_b/dt + sig_b/2), dminus = Dl Dl' (eps_b/dt - sig_b/2)
+      cc[k] = 0.25 * (in.itf.dplus[k] + in.itf.dminus[k]) * ctx->dt;   // 1/2 Dl Dl' eps_b
+      cc[in.ny + k] = 0.5 * ctx->dt * in.itf.dlg[k];
+    }
+    CK(cudaMalloc(&in.R_d, sizeof(double) * R.size()));
+    CK(cudaMalloc(&in.c_d, sizeof(double) * cc.size()));
+    CK(cudaMemcpy(in.R_d, R.data(), sizeof(double) * R.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(in.c_d, cc.data(), sizeof(double) * cc.size(), cudaMemcpyHostToDevice));
+  }
   CK(cudaMemcpy(in.h_cell_d, in.h_cell.data(), sizeof(int) * in.ny, cudaMemcpyHostToDevice));
   // Mark the covered cells and zero every field on and inside the region.
   CK(cudaStreamSynchronize(ctx->stream));
@@ -925,6 +1188,26 @@ int fdtd_set_rom_state(fdtd_ctx* ctx, int inst, const float* x) {
   const Instance& in = ctx->insts[inst];
   CK(cudaStreamSynchronize(ctx->stream));
   for (int p = 0; p < 2; ++p) CK(cudaMemcpy(in.state_d[p] + in.ny, x, sizeof(float) * in.q, cudaMemcpyHostToDevice));
+  return FDTD_OK;
+}
+
+int fdtd_energy(fdtd_ctx* ctx, double* out) {
+  if (!ctx || !out) return fail(ctx, FDTD_EINVAL, "fdtd_energy: bad argument");
+  const int ntiles = (int)ctx->tiles.size(), ninst = (int)ctx->insts.size();
+  const int nsim = (int)ctx->sims.size();
+  CK(ctx->energy_scratch.reserve((size_t)ntiles + ninst + nsim));
+  double* tp = ctx->energy_scratch.p;
+  double* ip = tp + ntiles;
+  double* op = ip + ninst;
+  energy_cells_kernel<<<ntiles, 256, 0, ctx->stream>>>(ctx->sims_d, ctx->tiles_d, ctx->cur, ctx->dt,
+                                                       ctx->dx, ctx->dy, tp);
+  if (ninst > 0)
+    energy_rom_kernel<<<ninst, 256, 0, ctx->stream>>>(ctx->sims_d, ctx->insts_d, ctx->einst_d, ctx->cur,
+                                                      ctx->dt, ip);
+  energy_sum_kernel<<<nsim, 256, 0, ctx->stream>>>(tp, ctx->tile_base_d, ip, ctx->insts_d, ninst, op);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(out, op, sizeof(double) * nsim, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
   return FDTD_OK;
 }
 

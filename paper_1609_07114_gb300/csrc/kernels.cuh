@@ -19,10 +19,10 @@
 
 namespace fdtdrom {
 
-constexpr int kStripCols = 128;   // columns per warp strip (32 lanes x float4)
-constexpr int kTileRows = 32;     // rows per tile
-constexpr int kWarpsPerCta = 4;   // strips per CTA
-constexpr int kCtaCols = kStripCols * kWarpsPerCta;
+// A stencil CTA covers kCtaCols columns x (per-simulation) tile rows.  Lanes
+// own V = 2 or 4 consecutive columns, so a warp strip is 32 V columns and a
+// CTA has kCtaCols / (32 V) warps.
+constexpr int kCtaCols = 512;
 
 struct SimDev {
   float* ex[2];
@@ -36,8 +36,8 @@ struct SimDev {
   float rdx;   // 1/dx: Ey -= cb (Hz_i - Hz_{i-1}) / dx
 };
 
-struct TileWork {   // one CTA of yee_step
-  int sim, x0, y0, pad;
+struct TileWork {   // one CTA of yee_step: columns [x0, x0 + kCtaCols), rows [y0, y1)
+  int sim, x0, y0, y1;
 };
 
 struct SrcEdge {    // one driven edge
@@ -58,6 +58,13 @@ constexpr int kRomRowsPerCta = 8;   // one row per warp
 
 struct RomWork {    // one CTA of rom_post: rows [row0, row1) of one instance
   int inst, row0, row1, pad;
+};
+
+struct EnergyInstDev {  // storage-function data of one embedded model
+  const double* R;      // q x q: R~ of Eq. (12) at the run dt
+  const double* c1;     // ny: 1/2 Dl Dl' eps_b  (interface half cells)
+  const double* c2;     // ny: dt/2 * (Dl G^T)_k
+  int q, sim, pad0, pad1;
 };
 
 struct RunDev {

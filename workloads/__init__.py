@@ -132,3 +132,38 @@ def grid_4096(nsteps: int = 20000):
     inclusion; ROM order 200; one Jy point source (fc = 30 GHz) and 16 probes;
     dt = 0.95 x the fine-mesh CFL limit."""
     return random_grid(1, 4096, 4096, 8, 16, 4, 200, nsteps, dt_factor=0.95)
+
+
+def lattice_lossless(n=256, nsteps=1_000_000, seed=None, lossless=True):
+    """Scaled-down form of the many-heterogeneous-ROM workload with CFL
+    extension: an n x n vacuum grid (dx = 1 mm), a 2 x 2 lattice of regions
+    drawn from three fine-region types refined r = 5 (regions of 6, 12 and 20
+    coarse cells, ROM orders 60, 180, 400), each holding a seeded dielectric
+    scatterer; dt = 2 x the fine-mesh CFL limit (0.4 x the coarse one).  One
+    Jy pulse (fc = 10 GHz) that has died out after ~1000 steps.  lossless:
+    sigma = 0 everywhere (energy must stay constant)."""
+    g = rng_for(4, seed)
+    dx = dy = 1e-3
+    r = 5
+    types = [(6, 60), (12, 180), (20, 400)]
+    roms = []
+    pitch = n // 2
+    k = 0
+    for ty in range(2):
+        for tx in range(2):
+            a, q = types[k % 3]
+            k += 1
+            i0 = tx * pitch + int(g.integers(4, pitch - a - 4))
+            j0 = ty * pitch + int(g.integers(4, pitch - a - 4))
+            nf = a * r
+            w = int(g.integers(nf // 4, nf // 2))
+            x0 = int(g.integers(0, nf - w))
+            y0 = int(g.integers(0, nf - w))
+            ef, sf = rect_fine(a, a, r, (x0, y0), (x0 + w, y0 + w), g.uniform(2.0, 6.0),
+                               0.0 if lossless else g.uniform(0.0, 0.05))
+            roms.append(dict(i0=i0, j0=j0, a=a, b=a, r=r, eps_r=ef, sigma=sf, q=q, f0=10e9))
+    dt = 2.0 * fine_cfl(dx, dy, r)
+    src = dict(comp=1, i=n // 2, j=n // 2 + 3, len=1, wave=diff_gaussian(min(nsteps, 4000), dt, 10e9))
+    return dict(name=f"lattice_{n}", nx=n, ny=n, dx=dx, dy=dy, dt=dt,
+                eps_r=np.ones((n, n)), sigma=np.zeros((n, n)) if lossless else 0.01 * g.random((n, n)),
+                roms=roms, sources=[src], probes=[(n // 4, n // 4), (3 * n // 4, n // 4)], nsteps=nsteps)
