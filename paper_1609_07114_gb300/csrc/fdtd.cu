@@ -11,6 +11,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <memory>
 #include <mutex>
 #include <new>
 #include <string>
@@ -460,18 +461,32 @@ struct SimHost {
   int tile_base = 0, ncx = 0, ncy = 0, th = 0;   // tiles: ncx x ncy of kCtaCols x th cells
 };
 
+// The run-time map of one (model, interface materials) pair.  Instances of
+// the same model whose outside half cells carry identical materials share it
+// (one copy of [P | Q] in HBM/L2 for a whole batch).
+struct CoupledMap {
+  long long model_id = 0;
+  std::vector<double> key;   // dplus, dminus, dlg of the interface
+  la::Mat P, Q;
+  int ld = 0;
+  float* M_d = nullptr;      // [P | Q | 0] FP32, n x ld
+  double* R_d = nullptr;     // R~ (q x q, FP64) for the storage function
+  double* c_d = nullptr;     // c1 (ny) then c2 (ny)
+  ~CoupledMap() {
+    cudaFree(M_d);
+    cudaFree(R_d);
+    cudaFree(c_d);
+  }
+};
+
 struct Instance {
   int sim = 0, i0 = 0, j0 = 0, a = 0, b = 0, q = 0, ny = 0, n = 0;
   InterfaceDesc itf;
-  la::Mat P, Q;
-  int ld = 0;
-  float* M_d = nullptr;
+  std::shared_ptr<CoupledMap> map;
   float* state_d[2] = {nullptr, nullptr};
   int* y_edge_d = nullptr;
   int* h_cell_d = nullptr;
   std::vector<int> y_edge, h_cell;
-  double* R_d = nullptr;   // R~ (q x q, FP64) for the storage function
-  double* c_d = nullptr;   // c1 (ny) then c2 (ny)
 };
 
 template <class T>
@@ -562,13 +577,13 @@ int upload_instances(fdtd_ctx* ctx) {
   for (size_t k = 0; k < ctx->insts.size(); ++k) {
     const Instance& in = ctx->insts[k];
     RomInstDev& d = h[k];
-    d.M = in.M_d;
+    d.M = in.map->M_d;
     d.state[0] = in.state_d[0], d.state[1] = in.state_d[1];
     d.y_edge = in.y_edge_d, d.h_cell = in.h_cell_d;
-    d.n = in.n, d.ny = in.ny, d.ld = in.ld, d.sim = in.sim;
+    d.n = in.n, d.ny = in.ny, d.ld = in.map->ld, d.sim = in.sim;
     for (int r0 = 0; r0 < in.n; r0 += kRomRowsPerCta)
       wk.push_back({(int)k, r0, std::min(in.n, r0 + kRomRowsPerCta), 0});
-    smem = std::max(smem, sizeof(float) * (size_t)in.ld);
+    smem = std::max(smem, sizeof(float) * (size_t)in.map->ld);
   }
   if (ctx->insts_d) cudaFree(ctx->insts_d);
   if (ctx->romwork_d) cudaFree(ctx->romwork_d);
@@ -580,7 +595,7 @@ int upload_instances(fdtd_ctx* ctx) {
     std::vector<EnergyInstDev> eh(ctx->insts.size());
     for (size_t k = 0; k < ctx->insts.size(); ++k) {
       const Instance& in = ctx->insts[k];
-      eh[k] = {in.R_d, in.c_d, in.c_d + in.ny, in.q, in.sim, 0, 0};
+      eh[k] = {in.map->R_d, in.map->c_d, in.map->c_d + in.ny, in.q, in.sim, 0, 0};
     }
     CK(cudaMalloc(&ctx->einst_d, sizeof(EnergyInstDev) * eh.size()));
     CK(cudaMemcpy(ctx->einst_d, eh.data(), sizeof(EnergyInstDev) * eh.size(), cudaMemcpyHostToDevice));
@@ -861,14 +876,12 @@ void fdtd_destroy(fdtd_ctx* ctx) {
     cudaFree(s.mat_d);
   }
   for (Instance& in : ctx->insts) {
-    cudaFree(in.M_d);
     cudaFree(in.state_d[0]);
     cudaFree(in.state_d[1]);
     cudaFree(in.y_edge_d);
     cudaFree(in.h_cell_d);
-    cudaFree(in.R_d);
-    cudaFree(in.c_d);
   }
+  ctx->insts.clear();   // releases the shared maps
   cudaFree(ctx->sims_d);
   cudaFree(ctx->tiles_d);
   cudaFree(ctx->insts_d);
@@ -1009,32 +1022,33 @@ int rom_embed(fdtd_ctx* ctx, const rom_model* m, int sim, int i0, int j0, int* i
   Instance in;
   in.sim = sim, in.i0 = i0, in.j0 = j0, in.a = a, in.b = b, in.q = m->qE + m->qH;
   in.itf = make_interface(i0, j0, a, b, ctx->dx, ctx->dy, ctx->dt, sh.eps_r.data(), sh.sigma.data(), sh.nx);
-  std::string msg;
-  int rc = couple(*m, in.itf, ctx->dt, in.P, in.Q, msg);
-  if (rc) return fail(ctx, rc, "rom_embed: " + msg);
   in.ny = in.itf.ny;
   in.n = in.ny + in.q;
-  for (int k = 0; k < in.ny; ++k) {
-    in.y_edge.push_back((in.itf.comp[k] << 30) | (in.itf.ej[k] * sh.pitch + in.itf.ei[k]));
-    in.h_cell.push_back(in.itf.hj[k] * sh.pitch + in.itf.hi[k]);
-  }
-  // [P | Q] in FP32, rows padded to a multiple of 4 floats (16-B aligned).
-  in.ld = ((in.n + in.ny + 3) / 4) * 4;
-  std::vector<float> Mf((size_t)in.n * in.ld, 0.f);
-  for (int r = 0; r < in.n; ++r) {
-    for (int k = 0; k < in.n; ++k) Mf[(size_t)r * in.ld + k] = (float)in.P(r, k);
-    for (int k = 0; k < in.ny; ++k) Mf[(size_t)r * in.ld + in.n + k] = (float)in.Q(r, k);
-  }
-  CK(cudaMalloc(&in.M_d, sizeof(float) * Mf.size()));
-  CK(cudaMalloc(&in.state_d[0], sizeof(float) * in.n));
-  CK(cudaMalloc(&in.state_d[1], sizeof(float) * in.n));
-  CK(cudaMalloc(&in.y_edge_d, sizeof(int) * in.ny));
-  CK(cudaMalloc(&in.h_cell_d, sizeof(int) * in.ny));
-  CK(cudaMemcpy(in.M_d, Mf.data(), sizeof(float) * Mf.size(), cudaMemcpyHostToDevice));
-  CK(cudaMemset(in.state_d[0], 0, sizeof(float) * in.n));
-  CK(cudaMemset(in.state_d[1], 0, sizeof(float) * in.n));
-  CK(cudaMemcpy(in.y_edge_d, in.y_edge.data(), sizeof(int) * in.ny, cudaMemcpyHostToDevice));
-  {  // storage-function data: R~ at the run dt (Eq. (12)) and the half cells
+  std::vector<double> key(in.itf.dplus);
+  key.insert(key.end(), in.itf.dminus.begin(), in.itf.dminus.end());
+  key.insert(key.end(), in.itf.dlg.begin(), in.itf.dlg.end());
+  for (const Instance& o : ctx->insts)
+    if (o.map->model_id == m->id && o.map->key == key) {
+      in.map = o.map;
+      break;
+    }
+  if (!in.map) {
+    auto cm = std::make_shared<CoupledMap>();
+    cm->model_id = m->id;
+    cm->key = key;
+    std::string msg;
+    int rc = couple(*m, in.itf, ctx->dt, cm->P, cm->Q, msg);
+    if (rc) return fail(ctx, rc, "rom_embed: " + msg);
+    // [P | Q] in FP32, rows padded to a multiple of 4 floats (16-B aligned).
+    cm->ld = ((in.n + in.ny + 3) / 4) * 4;
+    std::vector<float> Mf((size_t)in.n * cm->ld, 0.f);
+    for (int r = 0; r < in.n; ++r) {
+      for (int k = 0; k < in.n; ++k) Mf[(size_t)r * cm->ld + k] = (float)cm->P(r, k);
+      for (int k = 0; k < in.ny; ++k) Mf[(size_t)r * cm->ld + in.n + k] = (float)cm->Q(r, k);
+    }
+    CK(cudaMalloc(&cm->M_d, sizeof(float) * Mf.size()));
+    CK(cudaMemcpy(cm->M_d, Mf.data(), sizeof(float) * Mf.size(), cudaMemcpyHostToDevice));
+    // storage-function data: R~ at the run dt (Eq. (12)) and the half cells
     const int q = in.q, qE = m->qE, qH = m->qH;
     std::vector<double> R((size_t)q * q, 0.0), cc(2 * (size_t)in.ny);
     for (int i = 0; i < qE; ++i)
@@ -1048,11 +1062,23 @@ int rom_embed(fdtd_ctx* ctx, const rom_model* m, int sim, int i0, int j0, int* i
       cc[k] = 0.25 * (in.itf.dplus[k] + in.itf.dminus[k]) * ctx->dt;   // 1/2 Dl Dl' eps_b
       cc[in.ny + k] = 0.5 * ctx->dt * in.itf.dlg[k];
     }
-    CK(cudaMalloc(&in.R_d, sizeof(double) * R.size()));
-    CK(cudaMalloc(&in.c_d, sizeof(double) * cc.size()));
-    CK(cudaMemcpy(in.R_d, R.data(), sizeof(double) * R.size(), cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(in.c_d, cc.data(), sizeof(double) * cc.size(), cudaMemcpyHostToDevice));
+    CK(cudaMalloc(&cm->R_d, sizeof(double) * R.size()));
+    CK(cudaMalloc(&cm->c_d, sizeof(double) * cc.size()));
+    CK(cudaMemcpy(cm->R_d, R.data(), sizeof(double) * R.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(cm->c_d, cc.data(), sizeof(double) * cc.size(), cudaMemcpyHostToDevice));
+    in.map = cm;
   }
+  for (int k = 0; k < in.ny; ++k) {
+    in.y_edge.push_back((in.itf.comp[k] << 30) | (in.itf.ej[k] * sh.pitch + in.itf.ei[k]));
+    in.h_cell.push_back(in.itf.hj[k] * sh.pitch + in.itf.hi[k]);
+  }
+  CK(cudaMalloc(&in.state_d[0], sizeof(float) * in.n));
+  CK(cudaMalloc(&in.state_d[1], sizeof(float) * in.n));
+  CK(cudaMalloc(&in.y_edge_d, sizeof(int) * in.ny));
+  CK(cudaMalloc(&in.h_cell_d, sizeof(int) * in.ny));
+  CK(cudaMemset(in.state_d[0], 0, sizeof(float) * in.n));
+  CK(cudaMemset(in.state_d[1], 0, sizeof(float) * in.n));
+  CK(cudaMemcpy(in.y_edge_d, in.y_edge.data(), sizeof(int) * in.ny, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(in.h_cell_d, in.h_cell.data(), sizeof(int) * in.ny, cudaMemcpyHostToDevice));
   // Mark the covered cells and zero every field on and inside the region.
   CK(cudaStreamSynchronize(ctx->stream));
@@ -1072,7 +1098,7 @@ int rom_embed(fdtd_ctx* ctx, const rom_model* m, int sim, int i0, int j0, int* i
     }
   }
   ctx->insts.push_back(std::move(in));
-  rc = upload_instances(ctx);
+  int rc = upload_instances(ctx);
   if (rc) return rc;
   if (inst_out) *inst_out = (int)ctx->insts.size() - 1;
   return FDTD_OK;
@@ -1084,8 +1110,8 @@ int fdtd_get_rom_map(const fdtd_ctx* ctx, int inst, int* n, int* ny, double* P, 
   const Instance& in = ctx->insts[inst];
   if (n) *n = in.n;
   if (ny) *ny = in.ny;
-  if (P) std::memcpy(P, in.P.a.data(), sizeof(double) * in.P.a.size());
-  if (Q) std::memcpy(Q, in.Q.a.data(), sizeof(double) * in.Q.a.size());
+  if (P) std::memcpy(P, in.map->P.a.data(), sizeof(double) * in.map->P.a.size());
+  if (Q) std::memcpy(Q, in.map->Q.a.data(), sizeof(double) * in.map->Q.a.size());
   return FDTD_OK;
 }
 

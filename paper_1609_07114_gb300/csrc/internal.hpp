@@ -19,6 +19,7 @@ int set_global_error(int code, const std::string& msg);
 
 // A reduced model of one fine region (Sec. III, Eqs. (11)-(12)), FP64.
 struct rom_model {
+  long long id = 0;                    // unique per build (keys shared couplings)
   int a = 0, b = 0, r = 0;
   double dx = 0, dy = 0, dt = 0;
   int rule = FDTD_RULE_DUAL;

@@ -19,6 +19,7 @@
 // solving the remaining 5-point system on Hz,
 //   S_H = psi0 D_mu/dt + (1 - psi0^2)/4 K^T A11^{-1} K,  A11 = psi0 D_eps/dt + D_sigma/2,
 // with a banded Cholesky factorisation (bandwidth = fine cells per row).
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -266,6 +267,8 @@ extern "C" int rom_build(const rom_desc* d, rom_model** out, rom_build_report* r
   const auto t0 = std::chrono::steady_clock::now();
   rom_model* m = new (std::nothrow) rom_model();
   if (!m) return set_global_error(FDTD_ENOMEM, "rom_build: out of host memory");
+  static std::atomic<long long> next_id{1};
+  m->id = next_id++;
   try {
     const double dxf = d->dx / d->r, dyf = d->dy / d->r;
     FineSys f = assemble(nxf, nyf, dxf, dyf, d->eps_r, d->sigma);
