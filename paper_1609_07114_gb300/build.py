@@ -71,7 +71,10 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if errors:
         raise RuntimeError("build failed:\n" + "\n".join(errors))
     tmp = LIB + ".tmp"
-    link = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
+    vs = os.path.join(BUILD, "exports.map")   # export only the C ABI
+    with open(vs, "w") as f:
+        f.write("{ global: fdtd_*; rom_*; local: *; };\n")
+    link = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart", "-Xlinker", f"--version-script={vs}"]
     r = subprocess.run(link, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n" + r.stdout.decode(errors="replace"))
