@@ -223,6 +223,28 @@ int fdtd_get_step(const fdtd_ctx* ctx, long long* n);
  * use).  Synchronises the context's stream. */
 int fdtd_energy(fdtd_ctx* ctx, double* out);
 
+/* fdtd_energy without any device allocation.  No counterpart in the paper:
+ * this is a convenience for callers that must not allocate GPU memory at
+ * this point -- for example code that runs while another framework's caching
+ * allocator has reserved the free device memory, code that must not pay the
+ * implicit synchronisation of cudaMalloc/cudaFree inside a time-critical
+ * loop, or code that is about to record work into a CUDA graph.  The
+ * per-block partial sums go to a fixed array in the library's device memory
+ * (FDTD_ENERGY_STATIC_MAX doubles, 256 KB on every GPU that loads the
+ * library, kept until the process exits) instead of a buffer owned by the
+ * context; the result is the same as fdtd_energy's.
+ *   - Capacity: the context's stencil tiles + embedded models + simulations
+ *     must not exceed FDTD_ENERGY_STATIC_MAX; larger contexts get
+ *     FDTD_EINVAL (use fdtd_energy).
+ *   - The first call on a device looks up the array's device address once
+ *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   - All calls in the process share the one array: calls whose GPU work
+ *     overlaps (different contexts on different streams) race.  Every entry
+ *     used is written before it is read, so nothing needs clearing.
+ *   - out: host double[nsim].  Synchronises the context's stream. */
+#define FDTD_ENERGY_STATIC_MAX 32768
+int fdtd_energy_noalloc(fdtd_ctx* ctx, double* out);
+
 /* ------------------------------------------------------------ measurement */
 
 /* When on, fdtd_run launches every step directly (no CUDA graph) and records

@@ -96,6 +96,7 @@ def lib() -> C.CDLL:
         "fdtd_set_rom_state": (i, [vp, i, _fp]),
         "fdtd_get_step": (i, [vp, C.POINTER(ll)]),
         "fdtd_energy": (i, [vp, _dp]),
+        "fdtd_energy_noalloc": (i, [vp, _dp]),
         "fdtd_set_timing": (i, [vp, i]),
         "fdtd_get_kernel_times": (i, [vp, _dp, C.POINTER(ll), _dp, C.POINTER(ll)]),
         "fdtd_last_error": (C.c_char_p, [vp]),
@@ -312,6 +313,13 @@ class FdtdContext:
         """Storage function W of every simulation (``fdtd_energy``)."""
         out = np.zeros(len(self.shapes))
         self._ck(lib().fdtd_energy(self._h, out.ctypes.data_as(_dp)))
+        return out
+
+    def energy_noalloc(self):
+        """Same result as ``energy`` without any device allocation
+        (``fdtd_energy_noalloc``: partial sums in a fixed library array)."""
+        out = np.zeros(len(self.shapes))
+        self._ck(lib().fdtd_energy_noalloc(self._h, out.ctypes.data_as(_dp)))
         return out
 
     def set_timing(self, on: bool):

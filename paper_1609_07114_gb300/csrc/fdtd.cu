@@ -799,6 +799,8 @@ int march(fdtd_ctx* ctx, long long nsteps, int nprobe) {
 
 }  // namespace
 
+namespace {
+
 // Tile plan of the stencil kernel.  A CTA covers kCtaCols columns; the tile
 // height th (same for every simulation) is chosen so that the tiles fill
 // whole waves of resident CTAs: minimise ceil(T / slots) * (th + 1) (the +1
@@ -844,6 +846,30 @@ void plan_tiles(fdtd_ctx* ctx) {
         ctx->tiles.push_back({s, tx * kCtaCols, ty * best, std::min(sh.ny, (ty + 1) * best)});
   }
 }
+
+// Fixed device array used by fdtd_energy_noalloc for its partial sums.  In
+// host code its name is only a stand-in: the device address is looked up
+// once per device with cudaGetSymbolAddress (with that device current) and
+// cached.
+__device__ __align__(256) double g_energy_static[FDTD_ENERGY_STATIC_MAX];
+
+int static_energy_scratch(fdtd_ctx* ctx, double** ptr) {
+  static std::mutex mu;
+  static std::vector<void*> addr;   // per device ordinal
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(mu);
+  if ((int)addr.size() <= dev) addr.resize(dev + 1, nullptr);
+  if (!addr[dev]) {
+    void* p = nullptr;
+    CK(cudaGetSymbolAddress(&p, g_energy_static));
+    addr[dev] = p;
+  }
+  *ptr = static_cast<double*>(addr[dev]);
+  return FDTD_OK;
+}
+
+}  // namespace
 
 // ============================================================== C ABI
 
@@ -1223,6 +1249,32 @@ int fdtd_energy(fdtd_ctx* ctx, double* out) {
   const int nsim = (int)ctx->sims.size();
   CK(ctx->energy_scratch.reserve((size_t)ntiles + ninst + nsim));
   double* tp = ctx->energy_scratch.p;
+  double* ip = tp + ntiles;
+  double* op = ip + ninst;
+  energy_cells_kernel<<<ntiles, 256, 0, ctx->stream>>>(ctx->sims_d, ctx->tiles_d, ctx->cur, ctx->dt,
+                                                       ctx->dx, ctx->dy, tp);
+  if (ninst > 0)
+    energy_rom_kernel<<<ninst, 256, 0, ctx->stream>>>(ctx->sims_d, ctx->insts_d, ctx->einst_d, ctx->cur,
+                                                      ctx->dt, ip);
+  energy_sum_kernel<<<nsim, 256, 0, ctx->stream>>>(tp, ctx->tile_base_d, ip, ctx->insts_d, ninst, op);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(out, op, sizeof(double) * nsim, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return FDTD_OK;
+}
+
+int fdtd_energy_noalloc(fdtd_ctx* ctx, double* out) {
+  if (!ctx || !out) return fail(ctx, FDTD_EINVAL, "fdtd_energy_noalloc: bad argument");
+  const int ntiles = (int)ctx->tiles.size(), ninst = (int)ctx->insts.size();
+  const int nsim = (int)ctx->sims.size();
+  const long long need = (long long)ntiles + ninst + nsim;
+  if (need > FDTD_ENERGY_STATIC_MAX)
+    return fail(ctx, FDTD_EINVAL, "fdtd_energy_noalloc: context needs " + std::to_string(need) +
+                                      " partial sums, above the static capacity of " +
+                                      std::to_string(FDTD_ENERGY_STATIC_MAX) + " (use fdtd_energy)");
+  double* tp = nullptr;
+  const int rc = static_energy_scratch(ctx, &tp);
+  if (rc) return rc;
   double* ip = tp + ntiles;
   double* op = ip + ninst;
   energy_cells_kernel<<<ntiles, 256, 0, ctx->stream>>>(ctx->sims_d, ctx->tiles_d, ctx->cur, ctx->dt,
