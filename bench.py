@@ -174,6 +174,89 @@ def run_reference(args):
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
 
 
+def run_batched(args):
+    """Batched vs plain: 256 simulations (64 each of 128^2, 256^2, 512^2,
+    1024^2) sharing four reduced models, advanced together in one launch per
+    step, against the same simulations run one context and one fdtd_run at a
+    time."""
+    import numpy as np
+    import torch
+    import paper_1609_07114_gb300 as pg
+    from paper_1609_07114_gb300 import build as pbuild
+    import workloads
+    pbuild.build()
+    K, W, T = args.steps, args.warmup, args.tsteps
+    w = workloads.batched_256((W + K) * T)
+    models = [pg.rom_build(md["a"], md["b"], md["r"], w["dx"], w["dy"], w["dt"], md["eps_r"],
+                           md["sigma"], md["q"], f0=md["f0"]) for md in w["models"]]
+    sims = w["sims"]
+
+    def make_ctx(group):
+        ctx = pg.FdtdContext(w["dx"], w["dy"], w["dt"], [(s["eps_r"], s["sigma"]) for s in group])
+        for k, s in enumerate(group):
+            for (mi, i0, j0) in s["place"]:
+                ctx.rom_embed(models[mi], k, i0, j0)
+        waves = [torch.tensor(s["source"]["wave"].astype(np.float32), device="cuda") for s in group]
+        probes = [(k, s["probe"][0], s["probe"][1]) for k, s in enumerate(group)]
+        return ctx, waves, probes
+
+    def step(ctx, group, waves, probes, k0, n, out):
+        src = [dict(s["source"], sim=k, wave=waves[k][k0:k0 + n]) for k, s in enumerate(group)]
+        ctx.fdtd_run(n, src, probes, out)
+
+    cells = sum(s["nx"] * s["ny"] for s in sims)
+    ctx, waves, probes = make_ctx(sims)
+    out = torch.zeros((T, len(probes)), dtype=torch.float32, device="cuda")
+    for k in range(W):
+        step(ctx, sims, waves, probes, k * T, T, out)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    with ClockSampler() as clk:
+        e0.record(stream)
+        for k in range(W, W + K):
+            step(ctx, sims, waves, probes, k * T, T, out)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    el_b = e0.elapsed_time(e1) / 1e3
+    batched = cells * T * K / el_b / 1e9
+    ctx.set_timing(True)
+    step(ctx, sims, waves, probes, 0, T, out)
+    yee_ms, n_yee, post_ms, n_post = ctx.kernel_times()
+    ctx.close()
+    # plain: one context and one fdtd_run at a time, Tp steps each
+    Tp = max(T // 5, 32)
+    el_p = 0.0
+    outp = torch.zeros((Tp, 1), dtype=torch.float32, device="cuda")
+    for s in sims:
+        c1, wv, pr = make_ctx([s])
+        step(c1, [s], wv, pr, 0, Tp, outp)                  # warm (graph capture)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        step(c1, [s], wv, pr, Tp, Tp, outp)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        el_p += e0.elapsed_time(e1) / 1e3
+        c1.close()
+    plain = cells * Tp / el_p / 1e9
+    hbm, kind = peaks()
+    achieved = BYTES_PER_CELL_STEP * cells / (yee_ms / n_yee / 1e3) / 1e9
+    print(json.dumps({
+        "metric": "batched " + METRIC, "value": batched, "unit": UNIT, "n_gpus": 1, "steps": K,
+        "warmup": W, "ms_per_step": el_b / K * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "batched_256: 64 each of 128^2, 256^2, 512^2, 1024^2 coarse grids, "
+                               "4 shared ROMs r=3 q=40/80/160/320, one launch per step",
+                   "time_steps_per_step": T, "cells": cells,
+                   "plain_value": plain, "plain_time_steps_per_sim": Tp,
+                   "batched_over_plain": batched / plain},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "traffic": None, "peak_kind": kind,
+                     "kernel": "yee_step_kernel", "kernel_avg_ms": yee_ms / n_yee,
+                     "rom_post_avg_ms": post_ms / max(n_post, 1)},
+        "gpu_launches": K * (2 * T + T // 16), "clocks": clk.summary()}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -184,11 +267,17 @@ def main():
     ap.add_argument("--cpu-sample-steps", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--grid", type=int, default=4096, help="coarse grid size (4096 = the benchmark)")
+    ap.add_argument("--workload", default="grid", choices=["grid", "batched"])
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.workload == "batched":
+        if args.tsteps == 2000:
+            args.tsteps = 500          # 10 timed steps = the batch's 5000 time steps
+        run_batched(args)
         return
 
     import numpy as np

@@ -167,3 +167,54 @@ def lattice_lossless(n=256, nsteps=1_000_000, seed=None, lossless=True):
     return dict(name=f"lattice_{n}", nx=n, ny=n, dx=dx, dy=dy, dt=dt,
                 eps_r=np.ones((n, n)), sigma=np.zeros((n, n)) if lossless else 0.01 * g.random((n, n)),
                 roms=roms, sources=[src], probes=[(n // 4, n // 4), (3 * n // 4, n // 4)], nsteps=nsteps)
+
+
+def batched_256(nsteps: int = 5000, per_size: int = 64, sizes=(128, 256, 512, 1024), seed=None):
+    """Batch of independent simulations of uneven sizes sharing four reduced
+    models (r = 3; regions of 8, 12, 16 and 24 coarse cells, orders 40, 80,
+    160 and 320; vacuum fine interior with a centred lossy block).  Each
+    simulation: eps_r ~ U[1,4], sigma ~ U[0,0.02] per cell, the four regions
+    at seeded positions, one quadrant each, with a vacuum ring of coarse cells
+    around every region (so that all simulations share one coupled map per
+    model), one Jy point source at a seeded position with fc ~ U[10, 30] GHz,
+    and one Hz probe.  dt = 0.9 x the fine-mesh CFL limit for every one."""
+    g = rng_for(3, seed)
+    dx = dy = 1e-3
+    r = 3
+    types = [(8, 40), (12, 80), (16, 160), (24, 320)]
+    models = []
+    for a, q in types:
+        nf = a * r
+        lo, hi = nf // 3, nf - nf // 3
+        ef, sf = rect_fine(a, a, r, (lo, lo), (hi, hi), 3.0, 0.05)
+        models.append(dict(a=a, b=a, r=r, eps_r=ef, sigma=sf, q=q, f0=20e9))
+    dt = 0.9 * fine_cfl(dx, dy, r)
+    sims = []
+    for n in sizes:
+        for _ in range(per_size):
+            eps = g.uniform(1.0, 4.0, size=(n, n))
+            sig = g.uniform(0.0, 0.02, size=(n, n))
+            occ = np.zeros((n, n), dtype=bool)
+            place = []
+            h = n // 2
+            for k, (a, q) in enumerate(types):
+                qx, qy = (k % 2) * h, (k // 2) * h
+                i0 = qx + int(g.integers(3, h - a - 3))
+                j0 = qy + int(g.integers(3, h - a - 3))
+                eps[j0 - 1:j0 + a + 1, i0 - 1:i0 + a + 1] = 1.0
+                sig[j0 - 1:j0 + a + 1, i0 - 1:i0 + a + 1] = 0.0
+                occ[j0 - 2:j0 + a + 2, i0 - 2:i0 + a + 2] = True
+                place.append((k, i0, j0))
+            while True:
+                si, sj = int(g.integers(2, n - 2)), int(g.integers(2, n - 2))
+                if not occ[sj, si]:
+                    break
+            while True:
+                pi, pj = int(g.integers(1, n - 1)), int(g.integers(1, n - 1))
+                if not occ[pj, pi]:
+                    break
+            fc = float(g.uniform(10e9, 30e9))
+            sims.append(dict(nx=n, ny=n, eps_r=eps, sigma=sig, place=place,
+                             source=dict(comp=1, i=si, j=sj, len=1, wave=diff_gaussian(nsteps, dt, fc)),
+                             probe=(pi, pj)))
+    return dict(name="batched_256", dx=dx, dy=dy, dt=dt, models=models, sims=sims, nsteps=nsteps)
