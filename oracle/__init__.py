@@ -20,6 +20,8 @@ notation of the paper, so that it can be checked against the paper by eye:
                  and the discrete storage function (Sec. V, Appendix A)
 * ``problem``    builds a whole problem (grid + reduced models) from a
                  workload record
+* ``adjoint``    exact transpose of the time loop (gradients of the probe
+                 energy with respect to cell materials and source samples)
 
 Readings of places where the paper is silent or garbled are listed in each
 module header.  Parity unpinned: the accuracy of a reduced model relative to
