@@ -198,6 +198,26 @@ int fdtd_run(fdtd_ctx* ctx, long long nsteps, const fdtd_source* src, int nsrc,
 int fdtd_run_host(fdtd_ctx* ctx, long long nsteps, const fdtd_source* src, int nsrc,
                   const fdtd_probe* probes, int nprobe, float* probe_out_host);
 
+/* Gradient of the probe energy J = sum_n sum_p (Hz^{n+1/2}(p))^2 over the
+ * next nsteps steps, by the exact discrete adjoint of the time loop
+ * (transposed Eqs. (3), (5) and (23), run backwards).  Not in the paper; the
+ * reverse sweep recomputes the forward pass segment by segment from
+ * checkpoints taken every ckpt_every steps (the E fields of one segment are
+ * held in device memory).  Outputs (device, caller-owned, overwritten):
+ *   dJ_deps   FP32, per simulation [ny][nx] concatenated: dJ/d eps_r of each
+ *             coarse cell (0 for cells covered by a model; the coarse half
+ *             cells of interface edges include their effect through A1, A2
+ *             of Eq. (19));
+ *   dJ_dsigma FP32, same layout: dJ/d sigma (S/m);
+ *   dJ_dsrc   FP32 [nsrc][nsteps]: dJ/dJ^n for each source sample;
+ * any of them may be NULL.  J_out: host double (may be NULL).  The context
+ * ends in the state reached by the forward pass (as after fdtd_run).
+ * Ring-cell gradients assume a nonsingular coupling (dual rule, or the paper
+ * rule with a full-order model).  Synchronises. */
+int fdtd_grad(fdtd_ctx* ctx, long long nsteps, const fdtd_source* src, int nsrc,
+              const fdtd_probe* probes, int nprobe, int ckpt_every, float* dJ_deps,
+              float* dJ_dsigma, float* dJ_dsrc, double* J_out);
+
 /* ------------------------------------------------------------------ state */
 
 /* Host copies of the current fields of one simulation (E^n, Hz^{n-1/2}). */

@@ -96,6 +96,8 @@ def lib() -> C.CDLL:
         "fdtd_set_rom_state": (i, [vp, i, _fp]),
         "fdtd_get_step": (i, [vp, C.POINTER(ll)]),
         "fdtd_energy": (i, [vp, _dp]),
+        "fdtd_grad": (i, [vp, ll, C.POINTER(fdtd_source), i, C.POINTER(fdtd_probe), i, i,
+                          vp, vp, vp, _dp]),
         "fdtd_energy_noalloc": (i, [vp, _dp]),
         "fdtd_set_timing": (i, [vp, i]),
         "fdtd_get_kernel_times": (i, [vp, _dp, C.POINTER(ll), _dp, C.POINTER(ll)]),
@@ -308,6 +310,29 @@ class FdtdContext:
         n = C.c_longlong()
         self._ck(lib().fdtd_get_step(self._h, C.byref(n)))
         return n.value
+
+    def fdtd_grad(self, nsteps, sources=(), probes=(), ckpt_every=500, need_src=True):
+        """Gradient of J = sum of probe Hz^2 over the next nsteps steps (``fdtd_grad``).
+        Returns (J, dJ/deps_r per simulation [ny, nx], dJ/dsigma likewise,
+        dJ/dJ^n [nsrc, nsteps]) as CUDA float32 tensors (J a float)."""
+        import torch
+        src, _ = self._sources(sources, host=False)
+        pr = self._probes(probes)
+        ncell = sum(ny * nx for ny, nx in self.shapes)
+        geps = torch.zeros(ncell, dtype=torch.float32, device="cuda")
+        gsig = torch.zeros(ncell, dtype=torch.float32, device="cuda")
+        gsrc = torch.zeros((max(len(sources), 1), nsteps), dtype=torch.float32, device="cuda")
+        J = C.c_double()
+        self._ck(lib().fdtd_grad(self._h, nsteps, src, len(sources), pr, len(probes), ckpt_every,
+                                 C.c_void_p(geps.data_ptr()), C.c_void_p(gsig.data_ptr()),
+                                 C.c_void_p(gsrc.data_ptr()) if need_src else C.c_void_p(),
+                                 C.byref(J)))
+        out_e, out_s, off = [], [], 0
+        for ny, nx in self.shapes:
+            out_e.append(geps[off:off + ny * nx].view(ny, nx))
+            out_s.append(gsig[off:off + ny * nx].view(ny, nx))
+            off += ny * nx
+        return J.value, out_e, out_s, gsrc[:len(sources)]
 
     def energy(self):
         """Storage function W of every simulation (``fdtd_energy``)."""

@@ -1,0 +1,565 @@
+// Discrete adjoint of the time loop (fdtd_grad).  Included by fdtd.cu (one
+// translation unit: it launches the forward kernels for the recomputation).
+//
+// J = sum_n sum_p (Hz^{n+1/2}(p))^2.  Step n of the forward pass (fdtd.cu) is
+//   H'  = H + chx (Ex_{j+1} - Ex_j) - chy (Ey_{i+1} - Ey_i)          (Eq. (5))
+//   E'  = ca E + cb rd (dH') - cb J^n     on updated edges           (Eq. (3))
+//   s'  = P s + Q h(H'),   E'(interface) = s'[:n_y]                  (Eq. (23))
+// with the FP32 P, Q the forward uses.  Its transpose, backwards in n, with
+// g = dJ/d(state after step n):
+//   pre : g_s[:n_y] += g_E(interface); g_H'(h cells) += Q^T g_s; g_s <- P^T g_s;
+//         g_H'(probes) += 2 o^n; dJ/dJ^n = -cb g_E on source edges;
+//         half-cell material terms of the coupling (see below)
+//   h   : g_H' += curl^T(cb g_E);  material gradients of the cell's edges
+//   e   : g_E <- ca g_E (updated edges) + (H update)^T g_H'
+// Edge materials are cell means, so a cell gets half of each edge's
+//   dJ/deps_edge   = cb g_E (E^n - E^{n+1}) / dt,
+//   dJ/dsigma_edge = -cb g_E (E^n + E^{n+1}) / 2.
+// The coarse half cell of interface edge k enters the coupling of Eq. (19):
+// with c_k = A1^{-1} e_k = Q[:, k] / (Dl G^T)_k and t = Q^T g_s,
+//   dJ/deps_b,k   += (Dl Dl')_k / dt t_k / (Dl G^T)_k (y_k^n - y_k^{n+1})
+//   dJ/dsigma_b,k -= (Dl Dl')_k / 2  t_k / (Dl G^T)_k (y_k^n + y_k^{n+1}).
+// The forward pass is recomputed segment by segment from checkpoints; the E
+// fields of a segment are kept as frames, Hz ping-pongs.
+
+namespace {
+
+struct AdjSimDev {
+  float* gex[2];
+  float* gey[2];
+  float* ghz[2];
+  const float* exF;    // E frames of the segment: frame t at exF + t * fstride
+  const float* eyF;
+  float* geps;         // FP32 per-cell accumulators of the segment (pitched)
+  float* gsig;
+  const float2* mat;
+  long long fstride;
+  int nx, ny, pitch, pad;
+  float chx, chy, rdx, rdy;
+  float inv_dt, pad2;
+};
+
+struct AdjInstDev {
+  const float* M;        // [P | Q] FP32, n x ld (the forward's)
+  float* gs[2];          // adjoint of [y; x~]
+  const float* sF;       // state frames: frame t at sF + t * n
+  const int* y_edge;
+  const int* h_cell;
+  const float* lh_dt;    // (Dl Dl')_k / dt / (Dl G^T)_k
+  const float* lh_2;     // (Dl Dl')_k / 2 / (Dl G^T)_k
+  double* geps_b;        // per interface edge accumulators
+  double* gsig_b;
+  int n, ny, ld, sim;
+};
+
+struct AdjWork {         // one CTA of adj_pre: columns [c0, c1) of one instance
+  int inst, c0, c1, pad;
+};
+
+struct AdjRun {
+  const float* probe_out;   // [nsteps][nprobe] of the forward pass
+  const int* probe_sim;
+  const int* probe_cell;
+  const SrcEdge* src_edges;
+  float* dsrc;              // [nsrc][nsteps]
+  long long nsteps;
+  int nprobe, nedges;
+};
+
+__device__ __forceinline__ void cb_ca(float2 m1, float2 m2, float& ca, float& cb) {
+  edge_coef(m1, m2, ca, cb);
+}
+
+// ROM transpose, probe and source terms of reverse step n (segment index t).
+__global__ void __launch_bounds__(128)
+adj_pre_kernel(const AdjSimDev* __restrict__ sims, const AdjInstDev* __restrict__ insts,
+               const AdjWork* __restrict__ work, int nwork, const AdjRun* __restrict__ ar,
+               int par, int t, long long n) {
+  extern __shared__ float gsh[];
+  const int b = blockIdx.x;
+  if (b < nwork) {
+    const AdjWork w = work[b];
+    const AdjInstDev ai = insts[w.inst];
+    const AdjSimDev sd = sims[ai.sim];
+    const float* __restrict__ gsa = par ? ai.gs[1] : ai.gs[0];
+    float* __restrict__ gsb = par ? ai.gs[0] : ai.gs[1];
+    const float* __restrict__ gexa = par ? sd.gex[1] : sd.gex[0];
+    const float* __restrict__ geya = par ? sd.gey[1] : sd.gey[0];
+    float* __restrict__ ghza = par ? sd.ghz[1] : sd.ghz[0];
+    for (int k = threadIdx.x; k < ai.n; k += blockDim.x) {
+      float g = gsa[k];
+      if (k < ai.ny) {
+        const int code = ai.y_edge[k];
+        g += (code >> 30) ? geya[code & 0x3fffffff] : gexa[code & 0x3fffffff];
+      }
+      gsh[k] = g;
+    }
+    __syncthreads();
+    for (int c = w.c0 + threadIdx.x; c < w.c1; c += blockDim.x) {
+      float acc = 0.f;
+      for (int r = 0; r < ai.n; ++r) acc = fmaf(ai.M[(size_t)r * ai.ld + c], gsh[r], acc);
+      if (c < ai.n) {
+        gsb[c] = acc;
+      } else {
+        const int k = c - ai.n;
+        atomicAdd(ghza + ai.h_cell[k], acc);
+        const float y0 = ai.sF[(size_t)t * ai.n + k];
+        const float y1 = ai.sF[(size_t)(t + 1) * ai.n + k];
+        ai.geps_b[k] += (double)ai.lh_dt[k] * acc * ((double)y0 - y1);
+        ai.gsig_b[k] -= (double)ai.lh_2[k] * acc * ((double)y0 + y1);
+      }
+    }
+    return;
+  }
+  const int idx = (b - nwork) * blockDim.x + threadIdx.x;
+  if (idx < ar->nprobe) {
+    const AdjSimDev* sd = sims + ar->probe_sim[idx];
+    float* ghza = par ? sd->ghz[1] : sd->ghz[0];
+    atomicAdd(ghza + ar->probe_cell[idx], 2.f * ar->probe_out[n * ar->nprobe + idx]);
+  } else if (idx - ar->nprobe < ar->nedges) {
+    const SrcEdge se = ar->src_edges[idx - ar->nprobe];
+    const AdjSimDev* sd = sims + se.sim;
+    const size_t off = (size_t)se.j * sd->pitch + se.i;
+    const float2 m2 = sd->mat[off];
+    const float2 m1 = se.comp == 0 ? sd->mat[off - sd->pitch] : sd->mat[off - 1];
+    float ca, cb;
+    cb_ca(m1, m2, ca, cb);
+    const float* ga = se.comp == 0 ? (par ? sd->gex[1] : sd->gex[0]) : (par ? sd->gey[1] : sd->gey[0]);
+    atomicAdd(ar->dsrc + (size_t)se.src * ar->nsteps + n, -cb * ga[off]);
+  }
+}
+
+// g_H' = g_H + curl^T(cb g_E) per coarse cell, and the cell's material terms.
+__global__ void __launch_bounds__(256)
+adj_h_kernel(const AdjSimDev* __restrict__ sims, const TileWork* __restrict__ tiles, int par, int t) {
+  const TileWork tw = tiles[blockIdx.x];
+  const AdjSimDev sd = sims[tw.sim];
+  const int nx = sd.nx, ny = sd.ny, P = sd.pitch;
+  const float* __restrict__ gex = par ? sd.gex[1] : sd.gex[0];
+  const float* __restrict__ gey = par ? sd.gey[1] : sd.gey[0];
+  const float* __restrict__ gha = par ? sd.ghz[1] : sd.ghz[0];
+  float* __restrict__ ghb = par ? sd.ghz[0] : sd.ghz[1];
+  const float* __restrict__ ex0 = sd.exF + (size_t)t * sd.fstride;
+  const float* __restrict__ ex1 = ex0 + sd.fstride;
+  const float* __restrict__ ey0 = sd.eyF + (size_t)t * sd.fstride;
+  const float* __restrict__ ey1 = ey0 + sd.fstride;
+  const float2* __restrict__ mat = sd.mat;
+  const int w = min(kCtaCols, nx - tw.x0);
+  for (int k = threadIdx.x; k < w * (tw.y1 - tw.y0); k += blockDim.x) {
+    const int i = tw.x0 + k % w, j = tw.y0 + k / w;
+    const size_t off = (size_t)j * P + i;
+    const float2 m = mat[off];
+    if (m.x < 0.f) {
+      ghb[off] = 0.f;
+      continue;
+    }
+    float g = gha[off], qe = 0.f, qs = 0.f, ca, cb;
+    // Ex(i, j): cells (i, j-1), (i, j); Hz(i, j) enters with +cb rdy
+    if (j >= 1) {
+      const float2 mo = mat[off - P];
+      if (mo.x >= 0.f) {
+        cb_ca(mo, m, ca, cb);
+        const float mu = cb * gex[off];
+        g += sd.rdy * mu;
+        qe += mu * (ex0[off] - ex1[off]);
+        qs += mu * (ex0[off] + ex1[off]);
+      }
+    }
+    // Ex(i, j+1): cells (i, j), (i, j+1); Hz(i, j) enters with -cb rdy
+    if (j + 1 <= ny - 1) {
+      const float2 mo = mat[off + P];
+      if (mo.x >= 0.f) {
+        cb_ca(m, mo, ca, cb);
+        const float mu = cb * gex[off + P];
+        g -= sd.rdy * mu;
+        qe += mu * (ex0[off + P] - ex1[off + P]);
+        qs += mu * (ex0[off + P] + ex1[off + P]);
+      }
+    }
+    // Ey(i, j): cells (i-1, j), (i, j); Hz(i, j) enters with -cb rdx
+    if (i >= 1) {
+      const float2 mo = mat[off - 1];
+      if (mo.x >= 0.f) {
+        cb_ca(mo, m, ca, cb);
+        const float mu = cb * gey[off];
+        g -= sd.rdx * mu;
+        qe += mu * (ey0[off] - ey1[off]);
+        qs += mu * (ey0[off] + ey1[off]);
+      }
+    }
+    // Ey(i+1, j): cells (i, j), (i+1, j); Hz(i, j) enters with +cb rdx
+    if (i + 1 <= nx - 1) {
+      const float2 mo = mat[off + 1];
+      if (mo.x >= 0.f) {
+        cb_ca(m, mo, ca, cb);
+        const float mu = cb * gey[off + 1];
+        g += sd.rdx * mu;
+        qe += mu * (ey0[off + 1] - ey1[off + 1]);
+        qs += mu * (ey0[off + 1] + ey1[off + 1]);
+      }
+    }
+    ghb[off] = g;
+    sd.geps[off] += 0.5f * sd.inv_dt * qe;   // times eps0 when flushed
+    sd.gsig[off] -= 0.25f * qs;
+  }
+}
+
+// g_E <- ca g_E (updated edges) + (H update)^T g_H' (updated and interface edges).
+__global__ void __launch_bounds__(256)
+adj_e_kernel(const AdjSimDev* __restrict__ sims, const TileWork* __restrict__ tiles, int par) {
+  const TileWork tw = tiles[blockIdx.x];
+  const AdjSimDev sd = sims[tw.sim];
+  const int nx = sd.nx, P = sd.pitch;
+  const float* __restrict__ gexa = par ? sd.gex[1] : sd.gex[0];
+  const float* __restrict__ geya = par ? sd.gey[1] : sd.gey[0];
+  float* __restrict__ gexb = par ? sd.gex[0] : sd.gex[1];
+  float* __restrict__ geyb = par ? sd.gey[0] : sd.gey[1];
+  const float* __restrict__ gh = par ? sd.ghz[0] : sd.ghz[1];   // g_H' just written
+  const float2* __restrict__ mat = sd.mat;
+  const int w = min(kCtaCols, nx - tw.x0);
+  for (int k = threadIdx.x; k < w * (tw.y1 - tw.y0); k += blockDim.x) {
+    const int i = tw.x0 + k % w, j = tw.y0 + k / w;
+    const size_t off = (size_t)j * P + i;
+    const float2 m = mat[off];
+    float ca, cb;
+    // Ex(i, j), 1 <= j <= ny-1: H(i, j-1) has +chx Ex, H(i, j) has -chx Ex
+    float vx = 0.f;
+    if (j >= 1) {
+      const float2 mo = mat[off - P];
+      const bool live_lo = mo.x >= 0.f, live_hi = m.x >= 0.f;
+      if (live_lo || live_hi) {
+        vx = sd.chx * ((live_lo ? gh[off - P] : 0.f) - (live_hi ? gh[off] : 0.f));
+        if (live_lo && live_hi) {
+          cb_ca(mo, m, ca, cb);
+          vx += ca * gexa[off];
+        }
+      }
+    }
+    gexb[off] = vx;
+    // Ey(i, j), 1 <= i <= nx-1: H(i, j) has +chy Ey, H(i-1, j) has -chy Ey
+    float vy = 0.f;
+    if (i >= 1) {
+      const float2 mo = mat[off - 1];
+      const bool live_l = mo.x >= 0.f, live_r = m.x >= 0.f;
+      if (live_l || live_r) {
+        vy = sd.chy * ((live_r ? gh[off] : 0.f) - (live_l ? gh[off - 1] : 0.f));
+        if (live_l && live_r) {
+          cb_ca(mo, m, ca, cb);
+          vy += ca * geya[off];
+        }
+      }
+    }
+    geyb[off] = vy;
+  }
+}
+
+// Moves a segment's FP32 accumulators into the FP64 totals and clears them.
+__global__ void adj_flush_kernel(float* __restrict__ g32, double* __restrict__ g64, size_t n) {
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
+    g64[k] += g32[k];
+    g32[k] = 0.f;
+  }
+}
+
+// Dense per-simulation outputs from the pitched FP64 totals.
+__global__ void adj_out_kernel(const double* __restrict__ ge, const double* __restrict__ gs, int nx,
+                               int ny, int pitch, const float2* __restrict__ mat, float* __restrict__ oe,
+                               float* __restrict__ os) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nx * ny; k += gridDim.x * blockDim.x) {
+    const int i = k % nx, j = k / nx;
+    const size_t off = (size_t)j * pitch + i;
+    const bool live = mat[off].x >= 0.f;
+    if (oe) oe[k] = live ? (float)(ge[off] * kEps0d) : 0.f;
+    if (os) os[k] = live ? (float)gs[off] : 0.f;
+  }
+}
+
+// Adds the half-cell (coupling) terms of one model to the cells just outside.
+__global__ void adj_ring_kernel(double* __restrict__ ge, double* __restrict__ gs, const int* __restrict__ h_cell,
+                                const double* __restrict__ geps_b, const double* __restrict__ gsig_b, int ny) {
+  for (int k = threadIdx.x; k < ny; k += blockDim.x) {
+    atomicAdd(ge + h_cell[k], geps_b[k]);
+    atomicAdd(gs + h_cell[k], gsig_b[k]);
+  }
+}
+
+__global__ void sum_sq_kernel(const float* __restrict__ x, size_t n, double* __restrict__ out) {
+  __shared__ double red[32];
+  double acc = 0.0;
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x)
+    acc += (double)x[k] * x[k];
+  acc = block_sum(acc, red);
+  if (threadIdx.x == 0) atomicAdd(out, acc);
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ host side
+
+namespace {
+
+// Device allocations of one fdtd_grad call, released together.
+struct GradArena {
+  std::vector<void*> ptrs;
+  ~GradArena() {
+    for (void* p : ptrs) cudaFree(p);
+  }
+  template <class T>
+  cudaError_t alloc(T** p, size_t count) {
+    *p = nullptr;
+    cudaError_t e = cudaMalloc((void**)p, std::max<size_t>(count, 1) * sizeof(T));
+    if (e == cudaSuccess) {
+      ptrs.push_back(*p);
+      e = cudaMemset(*p, 0, std::max<size_t>(count, 1) * sizeof(T));
+    }
+    return e;
+  }
+};
+
+int run_grad(fdtd_ctx* ctx, long long nsteps, const fdtd_source* src, int nsrc,
+             const fdtd_probe* probes, int nprobe, int C, float* dJ_deps, float* dJ_dsig,
+             float* dJ_dsrc, double* J_out) {
+  if (nsteps < 1 || C < 1 || nsrc < 0 || nprobe < 0 || (nsrc && !src) || (nprobe && !probes))
+    return fail(ctx, FDTD_EINVAL, "fdtd_grad: bad argument");
+  for (int s = 0; s < nsrc; ++s)
+    if (!src[s].wave) return fail(ctx, FDTD_EINVAL, "fdtd_grad: null waveform");
+  if (C > nsteps) C = (int)nsteps;
+  const int nsim = (int)ctx->sims.size(), ninst = (int)ctx->insts.size();
+  const long long S = (nsteps + C - 1) / C;
+  cudaStream_t st = ctx->stream;
+  GradArena A;
+  // --- forward pass with checkpoints
+  float* probe_d = nullptr;
+  CK(A.alloc(&probe_d, (size_t)nsteps * std::max(nprobe, 1)));
+  std::vector<const float*> wv(std::max(nsrc, 1));
+  for (int s = 0; s < nsrc; ++s) wv[s] = src[s].wave;
+  int rc = prepare_run(ctx, nsteps, src, nsrc, wv.data(), probes, nprobe, probe_d);
+  if (rc) return rc;
+  std::vector<size_t> sim_off(nsim + 1, 0), inst_off(ninst + 1, 0);
+  for (int s = 0; s < nsim; ++s)
+    sim_off[s + 1] = sim_off[s] + (size_t)(ctx->sims[s].ny + 1) * ctx->sims[s].pitch;
+  for (int k = 0; k < ninst; ++k) inst_off[k + 1] = inst_off[k] + ctx->insts[k].n;
+  const size_t per_ckpt = 3 * sim_off[nsim] + inst_off[ninst];
+  float* ckpt = nullptr;
+  CK(A.alloc(&ckpt, per_ckpt * S));
+  auto ck_field = [&](long long k, int s, int f) { return ckpt + per_ckpt * k + 3 * sim_off[s] + (size_t)f * (sim_off[s + 1] - sim_off[s]); };
+  auto ck_inst = [&](long long k, int i) { return ckpt + per_ckpt * k + 3 * sim_off[nsim] + inst_off[i]; };
+  for (long long k = 0; k < S; ++k) {
+    const int c = ctx->cur;
+    for (int s = 0; s < nsim; ++s) {
+      const SimHost& sh = ctx->sims[s];
+      const size_t bytes = sizeof(float) * (sim_off[s + 1] - sim_off[s]);
+      CK(cudaMemcpyAsync(ck_field(k, s, 0), sh.ex[c], bytes, cudaMemcpyDeviceToDevice, st));
+      CK(cudaMemcpyAsync(ck_field(k, s, 1), sh.ey[c], bytes, cudaMemcpyDeviceToDevice, st));
+      CK(cudaMemcpyAsync(ck_field(k, s, 2), sh.hz[c], bytes, cudaMemcpyDeviceToDevice, st));
+    }
+    for (int i = 0; i < ninst; ++i)
+      CK(cudaMemcpyAsync(ck_inst(k, i), ctx->insts[i].state_d[c], sizeof(float) * ctx->insts[i].n,
+                         cudaMemcpyDeviceToDevice, st));
+    const long long base = k * C;
+    CK(cudaMemcpyAsync(&ctx->run_d->base, &base, sizeof(long long), cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));   // base is a host stack value
+    rc = march(ctx, std::min<long long>(C, nsteps - k * C), nprobe);
+    if (rc) return rc;
+  }
+  double* Jd = nullptr;
+  CK(A.alloc(&Jd, 1));
+  if (nprobe > 0) sum_sq_kernel<<<256, 256, 0, st>>>(probe_d, (size_t)nsteps * nprobe, Jd);
+  // --- adjoint state, frames and tables
+  std::vector<AdjSimDev> asd(nsim);
+  std::vector<double*> g64e(nsim), g64s(nsim);
+  std::vector<float*> g32e(nsim), g32s(nsim);
+  std::vector<float*> exF(nsim), eyF(nsim), hA(nsim), hB(nsim);
+  for (int s = 0; s < nsim; ++s) {
+    const SimHost& sh = ctx->sims[s];
+    const size_t fs = sim_off[s + 1] - sim_off[s];
+    AdjSimDev& a = asd[s];
+    for (int p = 0; p < 2; ++p) {
+      CK(A.alloc(&a.gex[p], fs));
+      CK(A.alloc(&a.gey[p], fs));
+      CK(A.alloc(&a.ghz[p], fs));
+    }
+    CK(A.alloc(&exF[s], fs * (C + 1)));
+    CK(A.alloc(&eyF[s], fs * (C + 1)));
+    CK(A.alloc(&hA[s], fs));
+    CK(A.alloc(&hB[s], fs));
+    CK(A.alloc(&g32e[s], fs));
+    CK(A.alloc(&g32s[s], fs));
+    CK(A.alloc(&g64e[s], fs));
+    CK(A.alloc(&g64s[s], fs));
+    a.exF = exF[s], a.eyF = eyF[s], a.fstride = (long long)fs;
+    a.geps = g32e[s], a.gsig = g32s[s];
+    a.mat = sh.mat_d;
+    a.nx = sh.nx, a.ny = sh.ny, a.pitch = sh.pitch;
+    a.chx = (float)(ctx->dt / (kMu0 * ctx->dy));
+    a.chy = (float)(ctx->dt / (kMu0 * ctx->dx));
+    a.rdy = (float)(1.0 / ctx->dy);
+    a.rdx = (float)(1.0 / ctx->dx);
+    a.inv_dt = (float)(1.0 / ctx->dt);
+  }
+  std::vector<AdjInstDev> aid(ninst);
+  std::vector<float*> sF(ninst);
+  std::vector<AdjWork> aw;
+  size_t pre_smem = 0;
+  for (int k = 0; k < ninst; ++k) {
+    const Instance& in = ctx->insts[k];
+    AdjInstDev& a = aid[k];
+    a.M = in.map->M_d;
+    CK(A.alloc(&a.gs[0], in.n));
+    CK(A.alloc(&a.gs[1], in.n));
+    CK(A.alloc(&sF[k], (size_t)in.n * (C + 1)));
+    a.sF = sF[k];
+    a.y_edge = in.y_edge_d;
+    a.h_cell = in.h_cell_d;
+    std::vector<float> l1(in.ny), l2(in.ny);
+    const double lh = 0.5 * ctx->dx * ctx->dy;   // (Dl Dl')_k on every side
+    for (int e = 0; e < in.ny; ++e) {
+      l1[e] = (float)(lh / ctx->dt / in.itf.dlg[e]);
+      l2[e] = (float)(lh / 2 / in.itf.dlg[e]);
+    }
+    float* lp = nullptr;
+    CK(A.alloc(&lp, 2 * (size_t)in.ny));
+    CK(cudaMemcpy(lp, l1.data(), sizeof(float) * in.ny, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(lp + in.ny, l2.data(), sizeof(float) * in.ny, cudaMemcpyHostToDevice));
+    a.lh_dt = lp, a.lh_2 = lp + in.ny;
+    CK(A.alloc(&a.geps_b, in.ny));
+    CK(A.alloc(&a.gsig_b, in.ny));
+    a.n = in.n, a.ny = in.ny, a.ld = in.map->ld, a.sim = in.sim;
+    for (int c0 = 0; c0 < in.n + in.ny; c0 += 128) aw.push_back({k, c0, std::min(in.n + in.ny, c0 + 128), 0});
+    pre_smem = std::max(pre_smem, sizeof(float) * (size_t)in.n);
+  }
+  if (pre_smem > 48 * 1024) {
+    if (pre_smem > 200 * 1024) return fail(ctx, FDTD_EINVAL, "fdtd_grad: reduced model too large");
+    CK(cudaFuncSetAttribute(adj_pre_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pre_smem));
+  }
+  AdjSimDev* asd_d = nullptr;
+  AdjInstDev* aid_d = nullptr;
+  AdjWork* aw_d = nullptr;
+  AdjRun* ar_d = nullptr;
+  CK(A.alloc(&asd_d, nsim));
+  CK(A.alloc(&aid_d, std::max(ninst, 1)));
+  CK(A.alloc(&aw_d, std::max<size_t>(aw.size(), 1)));
+  CK(A.alloc(&ar_d, 1));
+  CK(cudaMemcpy(asd_d, asd.data(), sizeof(AdjSimDev) * nsim, cudaMemcpyHostToDevice));
+  if (ninst) CK(cudaMemcpy(aid_d, aid.data(), sizeof(AdjInstDev) * ninst, cudaMemcpyHostToDevice));
+  if (!aw.empty()) CK(cudaMemcpy(aw_d, aw.data(), sizeof(AdjWork) * aw.size(), cudaMemcpyHostToDevice));
+  float* dsrc = dJ_dsrc;
+  if (!dsrc) CK(A.alloc(&dsrc, (size_t)std::max(nsrc, 1) * nsteps));
+  else CK(cudaMemsetAsync(dsrc, 0, sizeof(float) * (size_t)nsrc * nsteps, st));
+  int nedges = 0;
+  {
+    RunDev rd;
+    CK(cudaMemcpy(&rd, ctx->run_d, sizeof(RunDev), cudaMemcpyDeviceToHost));
+    int2 last{0, 0};
+    if (!ctx->tiles.empty())
+      CK(cudaMemcpy(&last, ctx->src_range.p + ctx->tiles.size() - 1, sizeof(int2), cudaMemcpyDeviceToHost));
+    nedges = last.y;
+    AdjRun ar{probe_d, ctx->probe_sim.p, ctx->probe_cell.p, ctx->src_edges.p, dsrc, nsteps, nprobe, nedges};
+    CK(cudaMemcpy(ar_d, &ar, sizeof(AdjRun), cudaMemcpyHostToDevice));
+  }
+  // per-step tables of the recomputation (frame t -> t+1), the same for every segment
+  std::vector<SimDev> simtab((size_t)C * nsim);
+  std::vector<RomInstDev> insttab((size_t)C * std::max(ninst, 1));
+  {
+    std::vector<SimDev> base(nsim);
+    CK(cudaMemcpy(base.data(), ctx->sims_d, sizeof(SimDev) * nsim, cudaMemcpyDeviceToHost));
+    std::vector<RomInstDev> ib(ninst);
+    if (ninst) CK(cudaMemcpy(ib.data(), ctx->insts_d, sizeof(RomInstDev) * ninst, cudaMemcpyDeviceToHost));
+    for (int t = 0; t < C; ++t) {
+      for (int s = 0; s < nsim; ++s) {
+        SimDev d = base[s];
+        const size_t fs = sim_off[s + 1] - sim_off[s];
+        d.ex[0] = exF[s] + fs * t, d.ex[1] = exF[s] + fs * (t + 1);
+        d.ey[0] = eyF[s] + fs * t, d.ey[1] = eyF[s] + fs * (t + 1);
+        d.hz[0] = (t & 1) ? hB[s] : hA[s];
+        d.hz[1] = (t & 1) ? hA[s] : hB[s];
+        simtab[(size_t)t * nsim + s] = d;
+      }
+      for (int k = 0; k < ninst; ++k) {
+        RomInstDev d = ib[k];
+        d.state[0] = sF[k] + (size_t)ctx->insts[k].n * t;
+        d.state[1] = sF[k] + (size_t)ctx->insts[k].n * (t + 1);
+        insttab[(size_t)t * ninst + k] = d;
+      }
+    }
+  }
+  SimDev* simtab_d = nullptr;
+  RomInstDev* insttab_d = nullptr;
+  RunDev* run2_d = nullptr;
+  CK(A.alloc(&simtab_d, simtab.size()));
+  CK(A.alloc(&insttab_d, insttab.size()));
+  CK(A.alloc(&run2_d, 1));
+  CK(cudaMemcpy(simtab_d, simtab.data(), sizeof(SimDev) * simtab.size(), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(insttab_d, insttab.data(), sizeof(RomInstDev) * insttab.size(), cudaMemcpyHostToDevice));
+  {
+    RunDev rd;
+    CK(cudaMemcpy(&rd, ctx->run_d, sizeof(RunDev), cudaMemcpyDeviceToHost));
+    rd.nprobe = 0;
+    rd.probe_out = nullptr;
+    CK(cudaMemcpy(run2_d, &rd, sizeof(RunDev), cudaMemcpyHostToDevice));
+  }
+  const unsigned ntiles = (unsigned)ctx->tiles.size();
+  const int npre_extra = (nprobe + nedges + 127) / 128;
+  int par = 0;
+  for (long long k = S - 1; k >= 0; --k) {
+    const int L = (int)std::min<long long>(C, nsteps - k * C);
+    for (int s = 0; s < nsim; ++s) {
+      const size_t bytes = sizeof(float) * (sim_off[s + 1] - sim_off[s]);
+      CK(cudaMemcpyAsync(exF[s], ck_field(k, s, 0), bytes, cudaMemcpyDeviceToDevice, st));
+      CK(cudaMemcpyAsync(eyF[s], ck_field(k, s, 1), bytes, cudaMemcpyDeviceToDevice, st));
+      CK(cudaMemcpyAsync(hA[s], ck_field(k, s, 2), bytes, cudaMemcpyDeviceToDevice, st));
+    }
+    for (int i = 0; i < ninst; ++i)
+      CK(cudaMemcpyAsync(sF[i], ck_inst(k, i), sizeof(float) * ctx->insts[i].n, cudaMemcpyDeviceToDevice, st));
+    const long long base = k * C;
+    CK(cudaMemcpyAsync(&run2_d->base, &base, sizeof(long long), cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));
+    for (int t = 0; t < L; ++t) {
+      if (ctx->vec == 2)
+        yee_step_kernel<2><<<ntiles, kCtaCols / 2, 0, st>>>(simtab_d + (size_t)t * nsim, ctx->tiles_d, run2_d, 0, t);
+      else
+        yee_step_kernel<4><<<ntiles, kCtaCols / 4, 0, st>>>(simtab_d + (size_t)t * nsim, ctx->tiles_d, run2_d, 0, t);
+      if (ctx->nromwork > 0)
+        rom_post_kernel<<<ctx->nromwork, kRomRowsPerCta * 32, ctx->post_smem, st>>>(
+            simtab_d + (size_t)t * nsim, insttab_d + (size_t)t * ninst, ctx->romwork_d, ctx->nromwork,
+            run2_d, 0, t);
+    }
+    for (int t = L - 1; t >= 0; --t) {
+      const long long n = k * C + t;
+      const int nb = (int)aw.size() + npre_extra;
+      if (nb > 0)
+        adj_pre_kernel<<<nb, 128, pre_smem, st>>>(asd_d, aid_d, aw_d, (int)aw.size(), ar_d, par, t, n);
+      adj_h_kernel<<<ntiles, 256, 0, st>>>(asd_d, ctx->tiles_d, par, t);
+      adj_e_kernel<<<ntiles, 256, 0, st>>>(asd_d, ctx->tiles_d, par);
+      par ^= 1;
+    }
+    CK(cudaGetLastError());
+    for (int s = 0; s < nsim; ++s) {
+      const size_t fs = sim_off[s + 1] - sim_off[s];
+      adj_flush_kernel<<<256, 256, 0, st>>>(g32e[s], g64e[s], fs);
+      adj_flush_kernel<<<256, 256, 0, st>>>(g32s[s], g64s[s], fs);
+    }
+  }
+  // half-cell terms of the coupling, then dense outputs
+  for (int k = 0; k < ninst; ++k) {
+    const Instance& in = ctx->insts[k];
+    adj_ring_kernel<<<1, 128, 0, st>>>(g64e[in.sim], g64s[in.sim], in.h_cell_d, aid[k].geps_b,
+                                        aid[k].gsig_b, in.ny);
+  }
+  size_t out_off = 0;
+  for (int s = 0; s < nsim; ++s) {
+    const SimHost& sh = ctx->sims[s];
+    adj_out_kernel<<<256, 256, 0, st>>>(g64e[s], g64s[s], sh.nx, sh.ny, sh.pitch, sh.mat_d,
+                                        dJ_deps ? dJ_deps + out_off : nullptr,
+                                        dJ_dsig ? dJ_dsig + out_off : nullptr);
+    out_off += (size_t)sh.nx * sh.ny;
+  }
+  CK(cudaGetLastError());
+  double J = 0.0;
+  CK(cudaMemcpyAsync(&J, Jd, sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (J_out) *J_out = J;
+  return FDTD_OK;
+}
+
+}  // namespace

@@ -24,6 +24,7 @@ using namespace fdtdrom;
 
 namespace {
 __device__ constexpr double kMu0d = 1.25663706212e-6;   // CODATA 2018
+__device__ constexpr double kEps0d = 8.8541878128e-12;
 }
 
 // ============================================================== device code
@@ -871,6 +872,8 @@ int static_energy_scratch(fdtd_ctx* ctx, double** ptr) {
 
 }  // namespace
 
+#include "adjoint.cuh"
+
 // ============================================================== C ABI
 
 extern "C" {
@@ -1287,6 +1290,14 @@ int fdtd_energy_noalloc(fdtd_ctx* ctx, double* out) {
   CK(cudaMemcpyAsync(out, op, sizeof(double) * nsim, cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   return FDTD_OK;
+}
+
+int fdtd_grad(fdtd_ctx* ctx, long long nsteps, const fdtd_source* src, int nsrc,
+              const fdtd_probe* probes, int nprobe, int ckpt_every, float* dJ_deps,
+              float* dJ_dsigma, float* dJ_dsrc, double* J_out) {
+  if (!ctx) return fail(ctx, FDTD_EINVAL, "fdtd_grad: null context");
+  if (ctx->timing) return fail(ctx, FDTD_EINVAL, "fdtd_grad: switch timing off first");
+  return run_grad(ctx, nsteps, src, nsrc, probes, nprobe, ckpt_every, dJ_deps, dJ_dsigma, dJ_dsrc, J_out);
 }
 
 int fdtd_set_timing(fdtd_ctx* ctx, int on) {
