@@ -58,17 +58,27 @@ def peaks():
 def profile_traffic():
     """DRAM bytes per stencil launch from the committed ncu summary, if it
     was taken on the current kernel source."""
-    src = os.path.join(ROOT, "paper_1609_07114_gb300", "csrc", "fdtd.cu")
     summ = os.path.join(ROOT, "profiles", "yee_step_grid4096.md")
-    if not (os.path.exists(src) and os.path.exists(summ)):
+    if not os.path.exists(summ):
         return None
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    sha = stencil_source_sha()
     txt = open(summ).read()
     m_sha = re.search(r"kernel source sha256\[:16\]:\s*([0-9a-f]+)", txt)
     m_b = re.search(r"dram bytes per full-size launch:\s*([0-9.eE+]+)", txt)
     if m_sha and m_b and m_sha.group(1) == sha:
         return float(m_b.group(1))
     return None
+
+
+def stencil_source_sha():
+    """Hash of the stencil kernel's source: kernels.cuh plus the part of
+    fdtd.cu from the stencil kernel up to the reduced-model kernel."""
+    d = os.path.join(ROOT, "paper_1609_07114_gb300", "csrc")
+    cu = open(os.path.join(d, "fdtd.cu")).read()
+    a = cu.index("// Fused coarse H and E half steps")
+    b = cu.index("// Eq. (23) for every embedded model")
+    h = hashlib.sha256(open(os.path.join(d, "kernels.cuh"), "rb").read() + cu[a:b].encode())
+    return h.hexdigest()[:16]
 
 
 class ClockSampler:
