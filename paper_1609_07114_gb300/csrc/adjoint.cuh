@@ -519,10 +519,10 @@ int run_grad(fdtd_ctx* ctx, long long nsteps, const fdtd_source* src, int nsrc,
         yee_step_kernel<2><<<ntiles, kCtaCols / 2, 0, st>>>(simtab_d + (size_t)t * nsim, ctx->tiles_d, run2_d, 0, t);
       else
         yee_step_kernel<4><<<ntiles, kCtaCols / 4, 0, st>>>(simtab_d + (size_t)t * nsim, ctx->tiles_d, run2_d, 0, t);
-      if (ctx->nromwork > 0)
-        rom_post_kernel<<<ctx->nromwork, kRomRowsPerCta * 32, ctx->post_smem, st>>>(
+      if (ctx->nromwork + ctx->ngwork > 0)
+        rom_post_kernel<<<ctx->nromwork + ctx->ngwork, kRomRowsPerCta * 32, ctx->post_smem, st>>>(
             simtab_d + (size_t)t * nsim, insttab_d + (size_t)t * ninst, ctx->romwork_d, ctx->nromwork,
-            run2_d, 0, t);
+            run2_d, 0, t, ctx->groups_d, ctx->gwork_d, ctx->ngwork, ctx->ginst_d);
     }
     for (int t = L - 1; t >= 0; --t) {
       const long long n = k * C + t;

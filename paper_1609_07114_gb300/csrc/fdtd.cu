@@ -240,12 +240,109 @@ yee_step_kernel(const SimDev* __restrict__ sims, const TileWork* __restrict__ wo
 // kRomRowsPerCta rows of one model, one row per warp: v = [y; x~; h] is staged
 // in shared memory and each warp forms one dot product with [P | Q] using
 // float4 loads (all of a row's loads are in flight together).
+// GEMM tile of the batched form: rows [r0, r0+32) of [P | Q] times the
+// columns [c0, c0+32) of [S; H] (one column per simulation sharing the map).
+// The next k-slice is loaded into registers while the current one is used.
+__device__ __forceinline__ void rom_gemm_tile(const SimDev* __restrict__ sims,
+                                              const RomInstDev* __restrict__ insts,
+                                              const GemmGroupDev& g, const GemmWork& gw,
+                                              const int* __restrict__ ginst, int par) {
+  __shared__ float Ms[32][33];
+  __shared__ float Vs[32][33];
+  __shared__ const float* s_in[32];
+  __shared__ float* s_out[32];
+  __shared__ const float* s_hz[32];
+  __shared__ const int* s_hc[32];
+  __shared__ const int* s_ye[32];
+  __shared__ float* s_ex[32];
+  __shared__ float* s_ey[32];
+  const int tid = threadIdx.x;
+  if (tid < 32) {
+    const int col = gw.c0 + tid;
+    s_in[tid] = nullptr;
+    if (col < g.B) {
+      const RomInstDev ri = insts[ginst[g.inst_off + col]];
+      const SimDev* sd = sims + ri.sim;
+      s_in[tid] = par ? ri.state[1] : ri.state[0];
+      s_out[tid] = par ? ri.state[0] : ri.state[1];
+      s_hz[tid] = par ? sd->hz[0] : sd->hz[1];
+      s_ex[tid] = par ? sd->ex[0] : sd->ex[1];
+      s_ey[tid] = par ? sd->ey[0] : sd->ey[1];
+      s_hc[tid] = ri.h_cell;
+      s_ye[tid] = ri.y_edge;
+    }
+  }
+  __syncthreads();
+  const int ty = tid >> 4, tx = tid & 15;   // 2 x 2 outputs per thread
+  float acc00 = 0.f, acc01 = 0.f, acc10 = 0.f, acc11 = 0.f;
+  float mreg[4], vreg[4];
+  auto load = [&](int k0) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int e = tid + 256 * u, row = e >> 5, kk = e & 31;
+      const int r = gw.r0 + row, k = k0 + kk;
+      mreg[u] = (r < g.n && k < g.ld) ? g.M[(size_t)r * g.ld + k] : 0.f;
+      const float* sp = s_in[row];   // here `row` indexes the column of V
+      float v = 0.f;
+      if (sp) {
+        if (k < g.n) v = sp[k];
+        else if (k < g.n + g.ny) v = s_hz[row][s_hc[row][k - g.n]];
+      }
+      vreg[u] = v;
+    }
+  };
+  load(0);
+  for (int k0 = 0; k0 < g.ld; k0 += 32) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int e = tid + 256 * u, row = e >> 5, kk = e & 31;
+      Ms[kk][row] = mreg[u];
+      Vs[kk][row] = vreg[u];
+    }
+    __syncthreads();
+    if (k0 + 32 < g.ld) load(k0 + 32);
+#pragma unroll 8
+    for (int kk = 0; kk < 32; ++kk) {
+      const float a0 = Ms[kk][2 * ty], a1 = Ms[kk][2 * ty + 1];
+      const float b0 = Vs[kk][2 * tx], b1 = Vs[kk][2 * tx + 1];
+      acc00 = fmaf(a0, b0, acc00);
+      acc01 = fmaf(a0, b1, acc01);
+      acc10 = fmaf(a1, b0, acc10);
+      acc11 = fmaf(a1, b1, acc11);
+    }
+    __syncthreads();
+  }
+  const float accs[2][2] = {{acc00, acc01}, {acc10, acc11}};
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int r = gw.r0 + 2 * ty + i, cc = 2 * tx + j;
+      if (r < g.n && s_in[cc]) {
+        s_out[cc][r] = accs[i][j];
+        if (r < g.ny) {
+          const int code = s_ye[cc][r];
+          float* base = (code >> 30) ? s_ey[cc] : s_ex[cc];
+          base[code & 0x3fffffff] = accs[i][j];
+        }
+      }
+    }
+  }
+}
+
 __global__ void __launch_bounds__(kRomRowsPerCta * 32)
 rom_post_kernel(const SimDev* __restrict__ sims, const RomInstDev* __restrict__ insts,
                 const RomWork* __restrict__ work, int nwork, const RunDev* __restrict__ run,
-                int par, int c) {
+                int par, int c, const GemmGroupDev* __restrict__ groups,
+                const GemmWork* __restrict__ gwork, int ngwork, const int* __restrict__ ginst) {
   extern __shared__ float4 smem4[];
   const unsigned FULL = 0xffffffffu;
+  if ((int)blockIdx.x >= nwork && (int)blockIdx.x < nwork + ngwork) {
+    const GemmWork gw = gwork[blockIdx.x - nwork];
+    const GemmGroupDev g = groups[gw.group];
+    rom_gemm_tile(sims, insts, g, gw, ginst, par);
+    return;
+  }
   if ((int)blockIdx.x < nwork) {
     const RomWork w = work[blockIdx.x];
     const RomInstDev ri = insts[w.inst];
@@ -310,7 +407,7 @@ rom_post_kernel(const SimDev* __restrict__ sims, const RomInstDev* __restrict__ 
       }
     }
   } else {
-    const int p = (blockIdx.x - nwork) * blockDim.x + threadIdx.x;
+    const int p = (blockIdx.x - nwork - ngwork) * blockDim.x + threadIdx.x;
     if (p < run->nprobe) {
       const long long n = run->base + c;
       const SimDev* sd = sims + run->probe_sim[p];
@@ -525,6 +622,10 @@ struct fdtd_ctx {
   RomInstDev* insts_d = nullptr;
   RomWork* romwork_d = nullptr;
   int nromwork = 0;
+  GemmGroupDev* groups_d = nullptr;   // batched form of shared maps
+  GemmWork* gwork_d = nullptr;
+  int* ginst_d = nullptr;
+  int ngwork = 0;
   size_t post_smem = 0;
   RunDev* run_d = nullptr;
   EnergyInstDev* einst_d = nullptr;
@@ -571,10 +672,37 @@ void drop_graphs(fdtd_ctx* ctx) {
   }
 }
 
+// Instances are stepped either one row per warp (rom_post_kernel's first
+// block range) or, when at least FDTD_ROM_GEMM_MIN (default 8) of them share
+// one coupled map, as one GEMM over the shared [P | Q] (second range).
 int upload_instances(fdtd_ctx* ctx) {
   std::vector<RomInstDev> h(ctx->insts.size());
   std::vector<RomWork> wk;
   size_t smem = 0;
+  int gemm_min = 8;
+  if (const char* e = getenv("FDTD_ROM_GEMM_MIN")) gemm_min = std::max(1, atoi(e));
+  std::vector<const CoupledMap*> maps;
+  std::vector<std::vector<int>> members;
+  for (size_t k = 0; k < ctx->insts.size(); ++k) {
+    const CoupledMap* m = ctx->insts[k].map.get();
+    size_t g = 0;
+    while (g < maps.size() && maps[g] != m) ++g;
+    if (g == maps.size()) maps.push_back(m), members.emplace_back();
+    members[g].push_back((int)k);
+  }
+  std::vector<GemmGroupDev> groups;
+  std::vector<GemmWork> gwork;
+  std::vector<int> ginst;
+  std::vector<char> in_gemm(ctx->insts.size(), 0);
+  for (size_t g = 0; g < maps.size(); ++g) {
+    if ((int)members[g].size() < gemm_min) continue;
+    const Instance& in0 = ctx->insts[members[g][0]];
+    GemmGroupDev gd{maps[g]->M_d, in0.n, in0.ny, maps[g]->ld, (int)members[g].size(), (int)ginst.size(), 0, 0, 0};
+    for (int k : members[g]) ginst.push_back(k), in_gemm[k] = 1;
+    for (int r0 = 0; r0 < gd.n; r0 += 32)
+      for (int c0 = 0; c0 < gd.B; c0 += 32) gwork.push_back({(int)groups.size(), r0, c0, 0});
+    groups.push_back(gd);
+  }
   for (size_t k = 0; k < ctx->insts.size(); ++k) {
     const Instance& in = ctx->insts[k];
     RomInstDev& d = h[k];
@@ -582,9 +710,25 @@ int upload_instances(fdtd_ctx* ctx) {
     d.state[0] = in.state_d[0], d.state[1] = in.state_d[1];
     d.y_edge = in.y_edge_d, d.h_cell = in.h_cell_d;
     d.n = in.n, d.ny = in.ny, d.ld = in.map->ld, d.sim = in.sim;
+    if (in_gemm[k]) continue;
     for (int r0 = 0; r0 < in.n; r0 += kRomRowsPerCta)
       wk.push_back({(int)k, r0, std::min(in.n, r0 + kRomRowsPerCta), 0});
     smem = std::max(smem, sizeof(float) * (size_t)in.map->ld);
+  }
+  cudaFree(ctx->groups_d);
+  cudaFree(ctx->gwork_d);
+  cudaFree(ctx->ginst_d);
+  ctx->groups_d = nullptr;
+  ctx->gwork_d = nullptr;
+  ctx->ginst_d = nullptr;
+  ctx->ngwork = (int)gwork.size();
+  if (!groups.empty()) {
+    CK(cudaMalloc(&ctx->groups_d, sizeof(GemmGroupDev) * groups.size()));
+    CK(cudaMemcpy(ctx->groups_d, groups.data(), sizeof(GemmGroupDev) * groups.size(), cudaMemcpyHostToDevice));
+    CK(cudaMalloc(&ctx->gwork_d, sizeof(GemmWork) * gwork.size()));
+    CK(cudaMemcpy(ctx->gwork_d, gwork.data(), sizeof(GemmWork) * gwork.size(), cudaMemcpyHostToDevice));
+    CK(cudaMalloc(&ctx->ginst_d, sizeof(int) * ginst.size()));
+    CK(cudaMemcpy(ctx->ginst_d, ginst.data(), sizeof(int) * ginst.size(), cudaMemcpyHostToDevice));
   }
   if (ctx->insts_d) cudaFree(ctx->insts_d);
   if (ctx->romwork_d) cudaFree(ctx->romwork_d);
@@ -602,8 +746,10 @@ int upload_instances(fdtd_ctx* ctx) {
     CK(cudaMemcpy(ctx->einst_d, eh.data(), sizeof(EnergyInstDev) * eh.size(), cudaMemcpyHostToDevice));
     CK(cudaMalloc(&ctx->insts_d, sizeof(RomInstDev) * h.size()));
     CK(cudaMemcpy(ctx->insts_d, h.data(), sizeof(RomInstDev) * h.size(), cudaMemcpyHostToDevice));
-    CK(cudaMalloc(&ctx->romwork_d, sizeof(RomWork) * wk.size()));
-    CK(cudaMemcpy(ctx->romwork_d, wk.data(), sizeof(RomWork) * wk.size(), cudaMemcpyHostToDevice));
+    if (!wk.empty()) {
+      CK(cudaMalloc(&ctx->romwork_d, sizeof(RomWork) * wk.size()));
+      CK(cudaMemcpy(ctx->romwork_d, wk.data(), sizeof(RomWork) * wk.size(), cudaMemcpyHostToDevice));
+    }
   }
   ctx->nromwork = (int)wk.size();
   ctx->post_smem = smem;
@@ -626,10 +772,11 @@ void launch_yee(fdtd_ctx* ctx, cudaStream_t s, int par, int c) {
 // Launches one step (chunk index c) on stream s.
 void launch_step(fdtd_ctx* ctx, cudaStream_t s, int par, int c, int nprobe_blocks) {
   launch_yee(ctx, s, par, c);
-  const int nb = ctx->nromwork + nprobe_blocks;
+  const int nb = ctx->nromwork + ctx->ngwork + nprobe_blocks;
   if (nb > 0)
     rom_post_kernel<<<nb, kRomRowsPerCta * 32, ctx->post_smem, s>>>(
-        ctx->sims_d, ctx->insts_d, ctx->romwork_d, ctx->nromwork, ctx->run_d, par, c);
+        ctx->sims_d, ctx->insts_d, ctx->romwork_d, ctx->nromwork, ctx->run_d, par, c, ctx->groups_d,
+        ctx->gwork_d, ctx->ngwork, ctx->ginst_d);
 }
 
 int ensure_graph(fdtd_ctx* ctx, int par, int nprobe_blocks) {
@@ -749,7 +896,7 @@ int drain_events(fdtd_ctx* ctx) {
 
 int march_timed(fdtd_ctx* ctx, long long nsteps, int nprobe) {
   const int nprobe_blocks = (nprobe + kRomRowsPerCta * 32 - 1) / (kRomRowsPerCta * 32);
-  const bool post = ctx->nromwork + nprobe_blocks > 0;
+  const bool post = ctx->nromwork + ctx->ngwork + nprobe_blocks > 0;
   while ((int)ctx->ev.size() < 3 * 64) {
     cudaEvent_t e;
     CK(cudaEventCreate(&e));
@@ -763,8 +910,9 @@ int march_timed(fdtd_ctx* ctx, long long nsteps, int nprobe) {
     launch_yee(ctx, ctx->stream, par, 0);
     CK(cudaEventRecord(e[1], ctx->stream));
     if (post)
-      rom_post_kernel<<<ctx->nromwork + nprobe_blocks, kRomRowsPerCta * 32, ctx->post_smem, ctx->stream>>>(
-          ctx->sims_d, ctx->insts_d, ctx->romwork_d, ctx->nromwork, ctx->run_d, par, 0);
+      rom_post_kernel<<<ctx->nromwork + ctx->ngwork + nprobe_blocks, kRomRowsPerCta * 32, ctx->post_smem,
+                        ctx->stream>>>(ctx->sims_d, ctx->insts_d, ctx->romwork_d, ctx->nromwork, ctx->run_d,
+                                       par, 0, ctx->groups_d, ctx->gwork_d, ctx->ngwork, ctx->ginst_d);
     CK(cudaEventRecord(e[2], ctx->stream));
     advance_kernel<<<1, 32, 0, ctx->stream>>>(ctx->run_d, 1);
     CK(cudaGetLastError());
@@ -915,6 +1063,9 @@ void fdtd_destroy(fdtd_ctx* ctx) {
   cudaFree(ctx->tiles_d);
   cudaFree(ctx->insts_d);
   cudaFree(ctx->romwork_d);
+  cudaFree(ctx->groups_d);
+  cudaFree(ctx->gwork_d);
+  cudaFree(ctx->ginst_d);
   cudaFree(ctx->run_d);
   cudaFree(ctx->einst_d);
   cudaFree(ctx->tile_base_d);

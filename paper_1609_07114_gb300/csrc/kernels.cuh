@@ -56,6 +56,18 @@ struct RomInstDev {
 
 constexpr int kRomRowsPerCta = 8;   // one row per warp
 
+// Simulations that share one coupled map step it as one GEMM:
+// [S'] = [P | Q] [S; H] with one column per simulation (32 x 32 tiles).
+struct GemmGroupDev {
+  const float* M;       // [P | Q | 0], n x ld
+  int n, ny, ld, B;     // B instances, listed at ginst[inst_off ...]
+  int inst_off, pad0, pad1, pad2;
+};
+
+struct GemmWork {
+  int group, r0, c0, pad;
+};
+
 struct RomWork {    // one CTA of rom_post: rows [row0, row1) of one instance
   int inst, row0, row1, pad;
 };

@@ -70,13 +70,16 @@ def test_gradients_match_oracle_adjoint():
 
 
 def test_checkpoint_spacing_does_not_change_the_result():
+    """The recomputed forward states are bit-identical whatever the segment
+    length; only the grouping of the FP32 gradient sums (flushed to FP64 per
+    segment) and the order of atomic additions change, at FP32 rounding."""
     w = grad_case(seed=61, nsteps=150)
     a = gpu_grad([w], 150, 7)
     b = gpu_grad([w], 150, 150)
     assert a[0] == b[0]
-    np.testing.assert_array_equal(a[1][0], b[1][0])
-    np.testing.assert_array_equal(a[2][0], b[2][0])
-    np.testing.assert_array_equal(a[3], b[3])
+    assert rel_l2(a[1][0], b[1][0]) < 1e-5
+    assert rel_l2(a[2][0], b[2][0]) < 1e-5
+    assert rel_l2(a[3], b[3]) < 1e-5
 
 
 def test_batch_gradients_are_per_simulation():
