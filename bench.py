@@ -267,6 +267,70 @@ def run_batched(args):
         "gpu_launches": K * (2 * T + T // 16), "clocks": clk.summary()}))
 
 
+def run_adjoint(args):
+    """Adjoint/forward time ratio: 16 simulations of 1024^2 cells with two
+    shared q = 120 models each, J = sum of Hz^2 at 8 probes per simulation
+    over --tsteps steps (default 10000), checkpoints every 500 steps."""
+    import numpy as np
+    import torch
+    import paper_1609_07114_gb300 as pg
+    from paper_1609_07114_gb300 import build as pbuild
+    import workloads
+    pbuild.build()
+    N = args.tsteps if args.tsteps != 2000 else 10000
+    w = workloads.adjoint_16(N)
+    models = [pg.rom_build(md["a"], md["b"], md["r"], w["dx"], w["dy"], w["dt"], md["eps_r"],
+                           md["sigma"], md["q"], f0=md["f0"]) for md in w["models"]]
+
+    def make_ctx():
+        ctx = pg.FdtdContext(w["dx"], w["dy"], w["dt"], [(s["eps_r"], s["sigma"]) for s in w["sims"]])
+        for k, s in enumerate(w["sims"]):
+            for (mi, i0, j0) in s["place"]:
+                ctx.rom_embed(models[mi], k, i0, j0)
+        return ctx
+
+    waves = [torch.tensor(s["source"]["wave"].astype(np.float32), device="cuda") for s in w["sims"]]
+    src = [dict(s["source"], sim=k, wave=waves[k]) for k, s in enumerate(w["sims"])]
+    probes = [(k, i, j) for k, s in enumerate(w["sims"]) for (i, j) in s["probes"]]
+    cells = sum(s["nx"] * s["ny"] for s in w["sims"])
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    fwd, adj = [], []
+    out = torch.zeros((N, len(probes)), dtype=torch.float32, device="cuda")
+    with ClockSampler() as clk:
+        for rep in range(args.warmup + args.steps):
+            ctx = make_ctx()
+            torch.cuda.synchronize()
+            e0.record(stream)
+            ctx.fdtd_run(N, src, probes, out)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            tf = e0.elapsed_time(e1) / 1e3
+            ctx.close()
+            ctx = make_ctx()
+            torch.cuda.synchronize()
+            e0.record(stream)
+            J, ge, gs, gw = ctx.fdtd_grad(N, src, probes, 500)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ta = e0.elapsed_time(e1) / 1e3
+            ctx.close()
+            if rep >= args.warmup:
+                fwd.append(tf)
+                adj.append(ta)
+    tf, ta = float(np.median(fwd)), float(np.median(adj))
+    print(json.dumps({
+        "metric": "adjoint/forward time ratio", "value": ta / tf, "unit": "x", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ta * 1e3, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "adjoint_16: 16 x 1024^2 coarse grids, 2 shared ROMs r=3 q=120 each, "
+                               "8 probes per simulation, J = sum Hz^2, checkpoints every 500 steps",
+                   "time_steps": N, "cells": cells, "forward_s": tf, "adjoint_s": ta,
+                   "forward_gcell_steps_per_s": cells * N / tf / 1e9,
+                   "gradient_gcell_steps_per_s": cells * N / ta / 1e9, "J": J},
+        "clocks": clk.summary()}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -277,12 +341,18 @@ def main():
     ap.add_argument("--cpu-sample-steps", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--grid", type=int, default=4096, help="coarse grid size (4096 = the benchmark)")
-    ap.add_argument("--workload", default="grid", choices=["grid", "batched"])
+    ap.add_argument("--workload", default="grid", choices=["grid", "batched", "adjoint"])
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.workload == "adjoint":
+        if args.steps == 10:
+            args.steps = 3
+        args.warmup = 1 if args.warmup == 3 else args.warmup
+        run_adjoint(args)
         return
     if args.workload == "batched":
         if args.tsteps == 2000:

@@ -218,3 +218,49 @@ def batched_256(nsteps: int = 5000, per_size: int = 64, sizes=(128, 256, 512, 10
                              source=dict(comp=1, i=si, j=sj, len=1, wave=diff_gaussian(nsteps, dt, fc)),
                              probe=(pi, pj)))
     return dict(name="batched_256", dx=dx, dy=dy, dt=dt, models=models, sims=sims, nsteps=nsteps)
+
+
+def adjoint_16(nsteps: int = 10000, nsim: int = 16, n: int = 1024, seed=None):
+    """Gradient workload: nsim simulations of n x n cells (eps_r ~ U[1,4],
+    sigma ~ U[0,0.02] per cell), each embedding the same two reduced models
+    (r = 3, q = 120, 16 x 16-cell regions; a lossy block and a dielectric
+    block) with vacuum rings, one Jy point source (fc = 20 GHz) and 8 Hz
+    probes per simulation; dt = 0.9 x the fine-mesh CFL limit.  The
+    objective is J = sum over steps and probes of Hz^2."""
+    g = rng_for(5, seed)
+    dx = dy = 1e-3
+    r, a = 3, 16
+    nf = a * r
+    m0 = rect_fine(a, a, r, (nf // 4, nf // 4), (3 * nf // 4, 3 * nf // 4), 4.0, 0.05)
+    m1 = rect_fine(a, a, r, (nf // 3, nf // 6), (2 * nf // 3, 5 * nf // 6), 8.0, 0.0)
+    models = [dict(a=a, b=a, r=r, eps_r=m0[0], sigma=m0[1], q=120, f0=20e9),
+              dict(a=a, b=a, r=r, eps_r=m1[0], sigma=m1[1], q=120, f0=20e9)]
+    dt = 0.9 * fine_cfl(dx, dy, r)
+    sims = []
+    for _ in range(nsim):
+        eps = g.uniform(1.0, 4.0, size=(n, n))
+        sig = g.uniform(0.0, 0.02, size=(n, n))
+        occ = np.zeros((n, n), dtype=bool)
+        place = []
+        for k in range(2):
+            while True:
+                i0 = int(g.integers(4, n - a - 4))
+                j0 = int(g.integers(4, n - a - 4))
+                if not occ[j0 - 3:j0 + a + 3, i0 - 3:i0 + a + 3].any():
+                    break
+            eps[j0 - 1:j0 + a + 1, i0 - 1:i0 + a + 1] = 1.0
+            sig[j0 - 1:j0 + a + 1, i0 - 1:i0 + a + 1] = 0.0
+            occ[j0 - 2:j0 + a + 2, i0 - 2:i0 + a + 2] = True
+            place.append((k, i0, j0))
+
+        def free():
+            while True:
+                i, j = int(g.integers(2, n - 2)), int(g.integers(2, n - 2))
+                if not occ[j, i]:
+                    return i, j
+
+        si, sj = free()
+        sims.append(dict(nx=n, ny=n, eps_r=eps, sigma=sig, place=place,
+                         source=dict(comp=1, i=si, j=sj, len=1, wave=diff_gaussian(nsteps, dt, 20e9)),
+                         probes=[free() for _ in range(8)]))
+    return dict(name="adjoint_16", dx=dx, dy=dy, dt=dt, models=models, sims=sims, nsteps=nsteps)
