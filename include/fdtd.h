@@ -194,7 +194,8 @@ int fdtd_run(fdtd_ctx* ctx, long long nsteps, const fdtd_source* src, int nsrc,
              const fdtd_probe* probes, int nprobe, float* probe_out);
 
 /* Same as fdtd_run with host buffers: copies the source waveforms to the
- * device, runs, copies the probe samples back, and synchronises. */
+ * device, runs, copies the probe samples back, and synchronises.  Returns
+ * FDTD_EUNSTABLE if a probe sample is not finite. */
 int fdtd_run_host(fdtd_ctx* ctx, long long nsteps, const fdtd_source* src, int nsrc,
                   const fdtd_probe* probes, int nprobe, float* probe_out_host);
 
@@ -232,6 +233,15 @@ int fdtd_set_rom_state(fdtd_ctx* ctx, int inst, const float* x);
 /* Number of steps taken since creation. */
 int fdtd_get_step(const fdtd_ctx* ctx, long long* n);
 
+/* Checkpoint / resume: the complete time-marching state (fields of every
+ * simulation, every model's [y; x~], the step counter) as one host buffer.
+ * fdtd_save_state with buf = NULL stores the required size in *size; with a
+ * buffer of *size bytes it fills it.  fdtd_load_state restores a buffer saved
+ * from a context with the same grids and embeddings (FDTD_EINVAL otherwise).
+ * Continuing after save + load gives bit-identical results. */
+int fdtd_save_state(fdtd_ctx* ctx, void* buf, size_t* size);
+int fdtd_load_state(fdtd_ctx* ctx, const void* buf, size_t size);
+
 /* Discrete storage function (Sec. V, Appendix A) of every simulation at the
  * current step, x = [E^n; Hz^{n-1/2}]:
  *   W = 1/2 E^T D_eps E + 1/2 H^T D_mu H - dt/2 E^T K H      (coarse system,
@@ -239,6 +249,7 @@ int fdtd_get_step(const fdtd_ctx* ctx, long long* n);
  *     + dt/2 x~^T R~ x~                                      (each model, Eq. (12)).
  * Lossless and source-free, W is constant; with losses it does not
  * increase.  FP32 state, FP64 accumulation.  out: host double[nsim].
+ * Returns FDTD_EUNSTABLE (after filling out) if some W is not finite.
  * Uses a device scratch buffer owned by the context (allocated on first
  * use).  Synchronises the context's stream. */
 int fdtd_energy(fdtd_ctx* ctx, double* out);

@@ -95,6 +95,8 @@ def lib() -> C.CDLL:
         "fdtd_get_rom_state": (i, [vp, i, _fp]),
         "fdtd_set_rom_state": (i, [vp, i, _fp]),
         "fdtd_get_step": (i, [vp, C.POINTER(ll)]),
+        "fdtd_save_state": (i, [vp, vp, C.POINTER(C.c_size_t)]),
+        "fdtd_load_state": (i, [vp, vp, C.c_size_t]),
         "fdtd_energy": (i, [vp, _dp]),
         "fdtd_grad": (i, [vp, ll, C.POINTER(fdtd_source), i, C.POINTER(fdtd_probe), i, i,
                           vp, vp, vp, _dp]),
@@ -305,6 +307,19 @@ class FdtdContext:
     def set_rom_state(self, inst, x):
         x = _f32(x)
         self._ck(lib().fdtd_set_rom_state(self._h, inst, x.ctypes.data_as(_fp)))
+
+    def save_state(self) -> bytes:
+        """``fdtd_save_state``: the whole marching state as bytes."""
+        n = C.c_size_t()
+        self._ck(lib().fdtd_save_state(self._h, None, C.byref(n)))
+        buf = C.create_string_buffer(n.value)
+        self._ck(lib().fdtd_save_state(self._h, buf, C.byref(n)))
+        return buf.raw
+
+    def load_state(self, data: bytes):
+        """``fdtd_load_state``."""
+        buf = C.create_string_buffer(data, len(data))
+        self._ck(lib().fdtd_load_state(self._h, buf, len(data)))
 
     def step_count(self):
         n = C.c_longlong()

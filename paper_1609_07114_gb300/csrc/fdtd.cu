@@ -1330,6 +1330,9 @@ int fdtd_run_host(fdtd_ctx* ctx, long long nsteps, const fdtd_source* src, int n
     CK(cudaMemcpyAsync(probe_out_host, ctx->host_probes.p, sizeof(float) * nsteps * nprobe,
                        cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
+  for (long long k = 0; k < nsteps * nprobe; ++k)
+    if (!std::isfinite(probe_out_host[k]))
+      return fail(ctx, FDTD_EUNSTABLE, "fdtd_run_host: non-finite probe sample at step " + std::to_string(k / nprobe));
   return FDTD_OK;
 }
 
@@ -1414,6 +1417,8 @@ int fdtd_energy(fdtd_ctx* ctx, double* out) {
   CK(cudaGetLastError());
   CK(cudaMemcpyAsync(out, op, sizeof(double) * nsim, cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
+  for (int k = 0; k < nsim; ++k)
+    if (!std::isfinite(out[k])) return fail(ctx, FDTD_EUNSTABLE, "non-finite storage function");
   return FDTD_OK;
 }
 
@@ -1440,6 +1445,8 @@ int fdtd_energy_noalloc(fdtd_ctx* ctx, double* out) {
   CK(cudaGetLastError());
   CK(cudaMemcpyAsync(out, op, sizeof(double) * nsim, cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
+  for (int k = 0; k < nsim; ++k)
+    if (!std::isfinite(out[k])) return fail(ctx, FDTD_EUNSTABLE, "non-finite storage function");
   return FDTD_OK;
 }
 
@@ -1473,6 +1480,71 @@ int fdtd_get_kernel_times(fdtd_ctx* ctx, double* yee_ms, long long* yee_launches
   if (yee_launches) *yee_launches = ctx->n_yee;
   if (post_ms) *post_ms = ctx->t_post;
   if (post_launches) *post_launches = ctx->n_post;
+  return FDTD_OK;
+}
+
+// State buffer: magic, step, cur-independent field copies (Ex, Ey, Hz per
+// simulation, pitched as on the device), every instance's [y; x~].
+static size_t state_bytes(const fdtd_ctx* ctx) {
+  size_t b = 4 * sizeof(long long);
+  for (const SimHost& sh : ctx->sims) b += 3 * sizeof(float) * (size_t)(sh.ny + 1) * sh.pitch;
+  for (const Instance& in : ctx->insts) b += sizeof(float) * (size_t)in.n;
+  return b;
+}
+
+int fdtd_save_state(fdtd_ctx* ctx, void* buf, size_t* size) {
+  if (!ctx || !size) return fail(ctx, FDTD_EINVAL, "fdtd_save_state: bad argument");
+  const size_t need = state_bytes(ctx);
+  if (!buf) {
+    *size = need;
+    return FDTD_OK;
+  }
+  if (*size < need) return fail(ctx, FDTD_EINVAL, "fdtd_save_state: buffer too small");
+  CK(cudaStreamSynchronize(ctx->stream));
+  char* p = static_cast<char*>(buf);
+  const long long hdr[4] = {0x46445444524f4d31LL, ctx->step, (long long)ctx->sims.size(), (long long)ctx->insts.size()};
+  std::memcpy(p, hdr, sizeof(hdr));
+  p += sizeof(hdr);
+  const int c = ctx->cur;
+  for (const SimHost& sh : ctx->sims) {
+    const size_t bytes = sizeof(float) * (size_t)(sh.ny + 1) * sh.pitch;
+    for (float* a : {sh.ex[c], sh.ey[c], sh.hz[c]}) {
+      CK(cudaMemcpy(p, a, bytes, cudaMemcpyDeviceToHost));
+      p += bytes;
+    }
+  }
+  for (const Instance& in : ctx->insts) {
+    CK(cudaMemcpy(p, in.state_d[c], sizeof(float) * in.n, cudaMemcpyDeviceToHost));
+    p += sizeof(float) * in.n;
+  }
+  *size = need;
+  return FDTD_OK;
+}
+
+int fdtd_load_state(fdtd_ctx* ctx, const void* buf, size_t size) {
+  if (!ctx || !buf) return fail(ctx, FDTD_EINVAL, "fdtd_load_state: bad argument");
+  const size_t need = state_bytes(ctx);
+  long long hdr[4];
+  if (size != need) return fail(ctx, FDTD_EINVAL, "fdtd_load_state: size does not match this context");
+  std::memcpy(hdr, buf, sizeof(hdr));
+  if (hdr[0] != 0x46445444524f4d31LL || hdr[2] != (long long)ctx->sims.size() ||
+      hdr[3] != (long long)ctx->insts.size())
+    return fail(ctx, FDTD_EINVAL, "fdtd_load_state: buffer was saved from another layout");
+  CK(cudaStreamSynchronize(ctx->stream));
+  const char* p = static_cast<const char*>(buf) + sizeof(hdr);
+  const int c = ctx->cur;
+  for (const SimHost& sh : ctx->sims) {
+    const size_t bytes = sizeof(float) * (size_t)(sh.ny + 1) * sh.pitch;
+    for (float* a : {sh.ex[c], sh.ey[c], sh.hz[c]}) {
+      CK(cudaMemcpy(a, p, bytes, cudaMemcpyHostToDevice));
+      p += bytes;
+    }
+  }
+  for (const Instance& in : ctx->insts) {
+    CK(cudaMemcpy(in.state_d[c], p, sizeof(float) * in.n, cudaMemcpyHostToDevice));
+    p += sizeof(float) * in.n;
+  }
+  ctx->step = hdr[1];
   return FDTD_OK;
 }
 

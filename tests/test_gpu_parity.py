@@ -285,3 +285,46 @@ def test_batched_layout_parity():
         assert rel_l2(g[:, col:col + npr], o) < TOL
         check_fields(ctx, s, st)
         col += npr
+
+
+def test_save_load_resume_is_bit_identical():
+    """Checkpoint / resume: N steps = k steps + save + (fresh context) load +
+    N - k steps, bit for bit."""
+    w = workloads.random_grid(70, 150, 120, 2, 5, 3, 30, 300, n_probes=4)
+    ctx1, _ = gpu_context([w])
+    g1 = gpu_run(ctx1, [w], 300)
+    ctx2, _ = gpu_context([w])
+    wa = dict(w, sources=[dict(s, wave=s["wave"][:110]) for s in w["sources"]])
+    ga = gpu_run(ctx2, [wa], 110)
+    blob = ctx2.save_state()
+    ctx3, _ = gpu_context([w])
+    ctx3.load_state(blob)
+    assert ctx3.step_count() == 110
+    wb = dict(w, sources=[dict(s, wave=s["wave"][110:]) for s in w["sources"]])
+    gb = gpu_run(ctx3, [wb], 190)
+    np.testing.assert_array_equal(g1, np.concatenate([ga, gb]))
+    with pytest.raises(pg.FdtdError):
+        ctx3.load_state(blob[:-4])
+
+
+def test_non_finite_state_is_reported():
+    """Non-finite values reaching a probe make the host entry point return
+    FDTD_EUNSTABLE (and fdtd_energy too); a model that is not passive at the
+    run's dt is refused at embedding (FDTD_ENOTPASSIVE)."""
+    w = workloads.random_grid(71, 60, 60, 1, 4, 2, 0, 50, dt_factor=1.9, n_probes=2)
+    rd = w["roms"][0]
+    m = pg.rom_build(rd["a"], rd["b"], rd["r"], w["dx"], w["dy"], w["dt"], rd["eps_r"], rd["sigma"], 0,
+                     gamma=0.0)
+    ctx = pg.FdtdContext(w["dx"], w["dy"], w["dt"], [(w["eps_r"], w["sigma"])])
+    with pytest.raises(pg.FdtdError) as ei:
+        ctx.rom_embed(m, 0, rd["i0"], rd["j0"])
+    assert ei.value.code == -4
+    Ex, Ey, Hz = ctx.get_fields(0)
+    Hz[30, 30] = np.nan
+    ctx.set_fields(0, Ex, Ey, Hz)
+    with pytest.raises(pg.FdtdError) as ei:
+        ctx.fdtd_run_host(5, [], [(0, 31, 30)])
+    assert ei.value.code == -6
+    with pytest.raises(pg.FdtdError) as ei:
+        ctx.energy()
+    assert ei.value.code == -6
