@@ -528,6 +528,8 @@ __global__ void advance_kernel(RunDev* run, int by) {
 
 }  // namespace
 
+#include "tb.cuh"
+
 // ============================================================== host side
 
 namespace fdtdrom {
@@ -640,6 +642,19 @@ struct fdtd_ctx {
   long long step = 0;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   int graph_nprobe_blocks[2] = {-1, -1};
+  // two-steps-per-launch path (tb.cuh)
+  bool tb = false;
+  std::vector<TbTile> tb_tiles;       // ordinary tiles then one per model
+  std::vector<int> tb_base;           // per simulation: first ordinary tile
+  std::vector<int4> tb_zones;
+  TbTile* tb_tiles_d = nullptr;
+  size_t tb_tiles_cap = 0;
+  int4* tb_zones_d = nullptr;
+  TbRun* tb_run_d = nullptr;
+  DevBuf<SrcEdge> tb_src;
+  DevBuf<int> tb_prb;
+  cudaGraphExec_t tb_graph[2] = {nullptr, nullptr};
+  int tb_graph_nprobe[2] = {-1, -1};
   // measurement mode (fdtd_set_timing)
   bool timing = false;
   std::vector<cudaEvent_t> ev;
@@ -669,7 +684,74 @@ void drop_graphs(fdtd_ctx* ctx) {
     if (ctx->graph[p]) cudaGraphExecDestroy(ctx->graph[p]);
     ctx->graph[p] = nullptr;
     ctx->graph_nprobe_blocks[p] = -1;
+    if (ctx->tb_graph[p]) cudaGraphExecDestroy(ctx->tb_graph[p]);
+    ctx->tb_graph[p] = nullptr;
+    ctx->tb_graph_nprobe[p] = -1;
   }
+}
+
+// Plan of the two-steps-per-launch path: ordinary kTbW x kTbH tiles, one
+// tile per model whose output is the model's zone, and the zone lists.  The
+// path is used only when every model fits the in-CTA model step and no model
+// lies within reach (two steps plus the zone margin) of another's tile.
+// FDTD_TB=0 disables it.
+int plan_tb(fdtd_ctx* ctx) {
+  ctx->tb = false;
+  ctx->tb_tiles.clear();
+  ctx->tb_zones.clear();
+  if (const char* e = getenv("FDTD_TB"))
+    if (atoi(e) == 0) return FDTD_OK;
+  const int M = kTbZoneMargin;
+  std::vector<int4> zone(ctx->insts.size());
+  for (size_t k = 0; k < ctx->insts.size(); ++k) {
+    const Instance& in = ctx->insts[k];
+    const SimHost& sh = ctx->sims[in.sim];
+    if (in.map->ld > kTbMaxRomN) return FDTD_OK;
+    int4 z{std::max(in.i0 - M, 0), std::max(in.j0 - M, 0), std::min(in.i0 + in.a + M, sh.nx),
+           std::min(in.j0 + in.b + M, sh.ny)};
+    if ((z.z - (z.x & ~3)) + 4 + 2 > kTbSW - 2 || z.w - z.y > kTbH) return FDTD_OK;
+    zone[k] = z;
+  }
+  for (size_t k = 0; k < ctx->insts.size(); ++k)
+    for (size_t m = 0; m < ctx->insts.size(); ++m) {
+      if (k == m || ctx->insts[k].sim != ctx->insts[m].sim) continue;
+      const Instance& o = ctx->insts[m];
+      const int4 w{zone[k].x - M, zone[k].y - M, zone[k].z + M, zone[k].w + M};   // tile's reach
+      if (!(o.i0 + o.a + 1 <= w.x || o.i0 - 1 >= w.z || o.j0 + o.b + 1 <= w.y || o.j0 - 1 >= w.w))
+        return FDTD_OK;
+    }
+  ctx->tb_base.assign(ctx->sims.size(), 0);
+  for (int s = 0; s < (int)ctx->sims.size(); ++s) {
+    const SimHost& sh = ctx->sims[s];
+    ctx->tb_base[s] = (int)ctx->tb_tiles.size();
+    for (int y0 = 0; y0 < sh.ny; y0 += kTbH)
+      for (int x0 = 0; x0 < sh.nx; x0 += kTbW) {
+        TbTile t{s, x0, std::min(x0 + kTbW, sh.nx), y0, std::min(y0 + kTbH, sh.ny), -1, 0, 0, 0, 0, 0, 0};
+        t.zone_b = (int)ctx->tb_zones.size();
+        for (size_t k = 0; k < ctx->insts.size(); ++k) {
+          if (ctx->insts[k].sim != s) continue;
+          const int4 z = zone[k];
+          if (z.x < t.x1 && z.z > t.x0 && z.y < t.y1 && z.w > t.y0) ctx->tb_zones.push_back(z);
+        }
+        t.zone_e = (int)ctx->tb_zones.size();
+        ctx->tb_tiles.push_back(t);
+      }
+  }
+  for (size_t k = 0; k < ctx->insts.size(); ++k) {
+    const int4 z = zone[k];
+    ctx->tb_tiles.push_back({ctx->insts[k].sim, z.x, z.z, z.y, z.w, (int)k, 0, 0, 0, 0, 0, 0});
+  }
+  cudaFree(ctx->tb_zones_d);
+  ctx->tb_zones_d = nullptr;
+  if (!ctx->tb_zones.empty()) {
+    CK(cudaMalloc(&ctx->tb_zones_d, sizeof(int4) * ctx->tb_zones.size()));
+    CK(cudaMemcpy(ctx->tb_zones_d, ctx->tb_zones.data(), sizeof(int4) * ctx->tb_zones.size(), cudaMemcpyHostToDevice));
+  }
+  if (!ctx->tb_run_d) CK(cudaMalloc(&ctx->tb_run_d, sizeof(TbRun)));
+  const size_t smem = kTbSmemFields;
+  CK(cudaFuncSetAttribute(yee_tb2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  ctx->tb = true;
+  return FDTD_OK;
 }
 
 // Instances are stepped either one row per warp (rom_post_kernel's first
@@ -758,7 +840,7 @@ int upload_instances(fdtd_ctx* ctx) {
     CK(cudaFuncSetAttribute(rom_post_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   }
   drop_graphs(ctx);
-  return FDTD_OK;
+  return plan_tb(ctx);
 }
 
 void launch_yee(fdtd_ctx* ctx, cudaStream_t s, int par, int c) {
@@ -864,6 +946,64 @@ int prepare_run(fdtd_ctx* ctx, long long nsteps, const fdtd_source* src, int nsr
     CK(cudaMemcpyAsync(ctx->probe_sim.p, psim.data(), sizeof(int) * nprobe, cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(ctx->probe_cell.p, pcell.data(), sizeof(int) * nprobe, cudaMemcpyHostToDevice, st));
   }
+  if (ctx->tb) {   // per-tile source and probe lists of the two-step path
+    const int nt = (int)ctx->tb_tiles.size();
+    std::vector<std::vector<SrcEdge>> ts(nt);
+    std::vector<std::vector<int>> tp(nt);
+    const int first_rom_tile = nt - (int)ctx->insts.size();
+    for (const SrcEdge& e : edges) {
+      const SimHost& sh = ctx->sims[e.sim];
+      const int ncx = (sh.nx + kTbW - 1) / kTbW, ncy = (sh.ny + kTbH - 1) / kTbH;
+      for (int ty = std::max(0, (e.j - 1) / kTbH); ty <= std::min(ncy - 1, (e.j + 1) / kTbH); ++ty)
+        for (int tx = std::max(0, (e.i - 1) / kTbW); tx <= std::min(ncx - 1, (e.i + 1) / kTbW); ++tx) {
+          const int t = ctx->tb_base[e.sim] + ty * ncx + tx;
+          const TbTile& tt = ctx->tb_tiles[t];
+          if (e.i >= tt.x0 - 1 && e.i <= tt.x1 && e.j >= tt.y0 - 1 && e.j <= tt.y1) ts[t].push_back(e);
+        }
+      for (int t = first_rom_tile; t < nt; ++t) {
+        const TbTile& tt = ctx->tb_tiles[t];
+        if (tt.sim == e.sim && e.i >= tt.x0 - 1 && e.i <= tt.x1 && e.j >= tt.y0 - 1 && e.j <= tt.y1)
+          ts[t].push_back(e);
+      }
+    }
+    for (int p = 0; p < nprobe; ++p) {
+      const int sim = psim[p], i = probes[p].i, j = probes[p].j;
+      int owner = -1;
+      for (int t = first_rom_tile; t < nt; ++t) {
+        const TbTile& tt = ctx->tb_tiles[t];
+        if (tt.sim == sim && i >= tt.x0 && i < tt.x1 && j >= tt.y0 && j < tt.y1) owner = t;
+      }
+      if (owner < 0) {
+        const SimHost& sh = ctx->sims[sim];
+        owner = ctx->tb_base[sim] + (j / kTbH) * ((sh.nx + kTbW - 1) / kTbW) + i / kTbW;
+      }
+      tp[owner].push_back(p);
+    }
+    std::vector<SrcEdge> fs;
+    std::vector<int> fp;
+    for (int t = 0; t < nt; ++t) {
+      TbTile& tt = ctx->tb_tiles[t];
+      tt.src_b = (int)fs.size();
+      fs.insert(fs.end(), ts[t].begin(), ts[t].end());
+      tt.src_e = (int)fs.size();
+      tt.prb_b = (int)fp.size();
+      fp.insert(fp.end(), tp[t].begin(), tp[t].end());
+      tt.prb_e = (int)fp.size();
+    }
+    CK(ctx->tb_src.reserve(fs.size()));
+    CK(ctx->tb_prb.reserve(fp.size()));
+    if (!ctx->tb_tiles_d || ctx->tb_tiles_cap < ctx->tb_tiles.size()) {
+      cudaFree(ctx->tb_tiles_d);
+      ctx->tb_tiles_d = nullptr;
+      CK(cudaMalloc(&ctx->tb_tiles_d, sizeof(TbTile) * ctx->tb_tiles.size()));
+      ctx->tb_tiles_cap = ctx->tb_tiles.size();
+    }
+    CK(cudaMemcpyAsync(ctx->tb_tiles_d, ctx->tb_tiles.data(), sizeof(TbTile) * nt, cudaMemcpyHostToDevice, st));
+    if (!fs.empty()) CK(cudaMemcpyAsync(ctx->tb_src.p, fs.data(), sizeof(SrcEdge) * fs.size(), cudaMemcpyHostToDevice, st));
+    if (!fp.empty()) CK(cudaMemcpyAsync(ctx->tb_prb.p, fp.data(), sizeof(int) * fp.size(), cudaMemcpyHostToDevice, st));
+    TbRun tr{ctx->tb_zones_d, ctx->tb_src.p, ctx->tb_prb.p};
+    CK(cudaMemcpyAsync(ctx->tb_run_d, &tr, sizeof(TbRun), cudaMemcpyHostToDevice, st));
+  }
   RunDev rd{};
   rd.base = 0;
   rd.nsteps = nsteps;
@@ -879,6 +1019,8 @@ int prepare_run(fdtd_ctx* ctx, long long nsteps, const fdtd_source* src, int nsr
   CK(cudaMemcpyAsync(ctx->run_d, &rd, sizeof(RunDev), cudaMemcpyHostToDevice, st));
   return FDTD_OK;
 }
+
+void launch_tb(fdtd_ctx* ctx, cudaStream_t s, int par, int c);
 
 // Sums the elapsed times of the recorded event triples (yee, post).
 int drain_events(fdtd_ctx* ctx) {
@@ -902,7 +1044,26 @@ int march_timed(fdtd_ctx* ctx, long long nsteps, int nprobe) {
     CK(cudaEventCreate(&e));
     ctx->ev.push_back(e);
   }
-  for (long long t = 0; t < nsteps; ++t) {
+  long long t = 0;
+  if (ctx->tb) {   // pairs of steps in one stencil launch; n_yee counts steps
+    for (; t + 2 <= nsteps; t += 2) {
+      const int par = ctx->cur ^ (int)(t & 1);
+      cudaEvent_t* e = &ctx->ev[ctx->ev_used];
+      CK(cudaEventRecord(e[0], ctx->stream));
+      launch_tb(ctx, ctx->stream, par, 0);
+      CK(cudaEventRecord(e[1], ctx->stream));
+      CK(cudaEventRecord(e[2], ctx->stream));
+      advance_kernel<<<1, 32, 0, ctx->stream>>>(ctx->run_d, 2);
+      CK(cudaGetLastError());
+      ctx->n_yee += 2;
+      ctx->ev_used += 3;
+      if (ctx->ev_used == (int)ctx->ev.size()) {
+        int rc = drain_events(ctx);
+        if (rc) return rc;
+      }
+    }
+  }
+  for (; t < nsteps; ++t) {
     const int par = ctx->cur ^ (int)(t & 1);
     cudaEvent_t* e = &ctx->ev[ctx->ev_used];
     CK(cudaEventRecord(e[0], ctx->stream));
@@ -929,8 +1090,53 @@ int march_timed(fdtd_ctx* ctx, long long nsteps, int nprobe) {
   return FDTD_OK;
 }
 
+void launch_tb(fdtd_ctx* ctx, cudaStream_t s, int par, int c) {
+  yee_tb2_kernel<<<(unsigned)ctx->tb_tiles.size(), kTbThreads, kTbSmemFields, s>>>(
+      ctx->sims_d, ctx->tb_tiles_d, ctx->insts_d, ctx->run_d, ctx->tb_run_d, par, c);
+}
+
+int ensure_tb_graph(fdtd_ctx* ctx, int par, int nprobe) {
+  if (ctx->tb_graph[par] && ctx->tb_graph_nprobe[par] == nprobe) return FDTD_OK;
+  if (ctx->tb_graph[par]) cudaGraphExecDestroy(ctx->tb_graph[par]);
+  ctx->tb_graph[par] = nullptr;
+  cudaGraph_t g = nullptr;
+  CK(cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal));
+  for (int c = 0; c < kChunk / 2; ++c) launch_tb(ctx, ctx->capture_stream, par ^ (c & 1), c);
+  advance_kernel<<<1, 32, 0, ctx->capture_stream>>>(ctx->run_d, kChunk);
+  CK(cudaStreamEndCapture(ctx->capture_stream, &g));
+  cudaError_t e = cudaGraphInstantiate(&ctx->tb_graph[par], g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return fail(ctx, FDTD_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+  ctx->tb_graph_nprobe[par] = nprobe;
+  return FDTD_OK;
+}
+
+// Two steps per launch: graph replays of kChunk steps, then pairs, then (odd
+// counts) one step of the one-step kernels.
+int march_tb(fdtd_ctx* ctx, long long nsteps, int nprobe) {
+  const int nprobe_blocks = (nprobe + kRomRowsPerCta * 32 - 1) / (kRomRowsPerCta * 32);
+  long long done = 0;
+  if (nsteps >= kChunk) {
+    int rc = ensure_tb_graph(ctx, ctx->cur, nprobe);
+    if (rc) return rc;
+    for (; done + kChunk <= nsteps; done += kChunk) CK(cudaGraphLaunch(ctx->tb_graph[ctx->cur], ctx->stream));
+  }
+  const int rem = (int)(nsteps - done);
+  int par = ctx->cur;
+  for (int c = 0; c < rem / 2; ++c, par ^= 1) launch_tb(ctx, ctx->stream, par, c);
+  if (rem & 1) {
+    launch_step(ctx, ctx->stream, par, 2 * (rem / 2), nprobe_blocks);
+    par ^= 1;
+  }
+  CK(cudaGetLastError());
+  ctx->cur = par;
+  ctx->step += nsteps;
+  return FDTD_OK;
+}
+
 int march(fdtd_ctx* ctx, long long nsteps, int nprobe) {
   if (ctx->timing) return march_timed(ctx, nsteps, nprobe);
+  if (ctx->tb) return march_tb(ctx, nsteps, nprobe);
   const int nprobe_blocks = (nprobe + kRomRowsPerCta * 32 - 1) / (kRomRowsPerCta * 32);
   long long done = 0;
   if (nsteps >= kChunk) {
@@ -1066,6 +1272,11 @@ void fdtd_destroy(fdtd_ctx* ctx) {
   cudaFree(ctx->groups_d);
   cudaFree(ctx->gwork_d);
   cudaFree(ctx->ginst_d);
+  cudaFree(ctx->tb_tiles_d);
+  cudaFree(ctx->tb_zones_d);
+  cudaFree(ctx->tb_run_d);
+  ctx->tb_src.release();
+  ctx->tb_prb.release();
   cudaFree(ctx->run_d);
   cudaFree(ctx->einst_d);
   cudaFree(ctx->tile_base_d);
@@ -1157,6 +1368,7 @@ int fdtd_create(const fdtd_grid_desc* g, void* cuda_stream, fdtd_ctx** out) {
     sd.rdx = (float)(1.0 / g->dx);
   }
   plan_tiles(ctx);
+  if (plan_tb(ctx) != FDTD_OK) return bail(FDTD_ECUDA);
   if (cudaMalloc(&ctx->sims_d, sizeof(SimDev) * sdev.size()) != cudaSuccess ||
       cudaMalloc(&ctx->tiles_d, sizeof(TileWork) * ctx->tiles.size()) != cudaSuccess ||
       cudaMalloc(&ctx->run_d, sizeof(RunDev)) != cudaSuccess) {

@@ -1,0 +1,234 @@
+// Two time steps per launch (temporal blocking).  Included by fdtd.cu.
+//
+// A CTA stages a window of E^n, Hz^{n-1/2} and the cell materials of its
+// output rectangle O = [X0, X1) x [Y0, Y1) in shared memory (cp.async, zero
+// fill outside the arrays), then, in shared memory:
+//   A.H  Hz^{n+1/2} on [X0-2, X1] x [Y0-2, Y1]                   (Eq. (5))
+//   A.E  E^{n+1} on the edges of [X0-1, X1] x [Y0-1, Y1] + J^n    (Eq. (3))
+//   (model tiles) [y; x~]^{n+1} = P [y; x~]^n + Q h^{n+1/2}      (Eq. (23))
+//   B.H  Hz^{n+3/2} on [X0-1, X1-1] x [Y0-1, Y1-1]
+//   B.E  E^{n+2} on the edges of O + J^{n+1}
+//   (model tiles) [y; x~]^{n+2}
+// and writes E^{n+2}, Hz^{n+3/2} of O.  Every cell depends only on values
+// within two cells of it over two steps, so the window is O plus two cells
+// (the interface values y^{n+1} of a model excepted).  Each model therefore
+// gets a tile of its own whose O is its "zone" (the region grown by 3 cells)
+// and which evaluates the model map between the sub-steps; ordinary tiles
+// compute through zones with the plain update but do not write zone cells.
+// Per step the DRAM traffic is about half that of the one-step kernel.
+
+namespace {
+
+constexpr int kTbW = 128;            // output columns of an ordinary tile (multiple of 4)
+constexpr int kTbH = 32;             // output rows
+constexpr int kTbSW = kTbW + 8;      // window columns [X0-4, X0+kTbW+4)
+constexpr int kTbSH = kTbH + 4;      // window rows    [Y0-2, Y0+kTbH+2)
+constexpr int kTbThreads = 256;
+constexpr int kTbZoneMargin = 3;     // zone = region grown by this many cells
+constexpr int kTbMaxRomN = 640;      // n + n_y limit for the in-CTA model step
+constexpr size_t kTbSmemFields = sizeof(float) * (size_t)kTbSH * kTbSW * 5;
+
+struct TbTile {
+  int sim;
+  int x0, x1, y0, y1;     // output rectangle O
+  int rom;                // model instance owned (-1: ordinary tile)
+  int zone_b, zone_e;     // ordinary tile: zones [b, e) in TbRun::zones to skip
+  int src_b, src_e;       // source edges within the tile's E window
+  int prb_b, prb_e;       // probes owned by the tile
+};
+
+struct TbRun {
+  const int4* zones;        // x0, y0, x1, y1 of every zone
+  const SrcEdge* src;       // per-tile source edges (TbTile ranges)
+  const int* prb_idx;       // probe indices (TbTile ranges)
+};
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool valid) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  const int sz = valid ? 16 : 0;
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(sz));
+}
+
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\n" ::);
+  asm volatile("cp.async.wait_group 0;\n" ::);
+}
+
+// In-CTA model step: v = [s; h; 0] (ri.ld floats, 16-B aligned) staged in
+// shared memory; rows split over warps.  The products and their order are
+// those of rom_post_kernel's row-per-warp path, so both paths give the same
+// bits.
+__device__ void tb_rom_step(const RomInstDev& ri, const float* v, float* sout) {
+  const unsigned FULL = 0xffffffffu;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const float4* v4 = reinterpret_cast<const float4*>(v);
+  const int l4 = ri.ld >> 2;
+  for (int r = warp; r < ri.n; r += nw) {
+    const float4* __restrict__ Mr = reinterpret_cast<const float4*>(ri.M + (size_t)r * ri.ld);
+    float acc = 0.f;
+    for (int k = lane; k < l4; k += 32) {
+      const float4 m = Mr[k];
+      const float4 x = v4[k];
+      acc = fmaf(m.x, x.x, acc);
+      acc = fmaf(m.y, x.y, acc);
+      acc = fmaf(m.z, x.z, acc);
+      acc = fmaf(m.w, x.w, acc);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
+    if (lane == 0) sout[r] = acc;
+  }
+}
+
+__global__ void __launch_bounds__(kTbThreads, 2)
+yee_tb2_kernel(const SimDev* __restrict__ sims, const TbTile* __restrict__ tiles,
+               const RomInstDev* __restrict__ insts, const RunDev* __restrict__ run,
+               const TbRun* __restrict__ tb, int par, int c) {
+  extern __shared__ float4 tb_smem4[];
+  float* sEx = reinterpret_cast<float*>(tb_smem4);
+  float* sEy = sEx + kTbSH * kTbSW;
+  float* sHz = sEy + kTbSH * kTbSW;
+  float2* sM = reinterpret_cast<float2*>(sHz + kTbSH * kTbSW);
+  const TbTile tt = tiles[blockIdx.x];
+  const SimDev sd = sims[tt.sim];
+  const int nx = sd.nx, ny = sd.ny, P = sd.pitch;
+  const float* __restrict__ ex = par ? sd.ex[1] : sd.ex[0];
+  const float* __restrict__ ey = par ? sd.ey[1] : sd.ey[0];
+  const float* __restrict__ hz = par ? sd.hz[1] : sd.hz[0];
+  float* __restrict__ exo = par ? sd.ex[0] : sd.ex[1];
+  float* __restrict__ eyo = par ? sd.ey[0] : sd.ey[1];
+  float* __restrict__ hzo = par ? sd.hz[0] : sd.hz[1];
+  const int X0 = tt.x0, X1 = tt.x1, Y0 = tt.y0, Y1 = tt.y1;
+  const int wx = (X0 & ~3) - 4;   // window origin (16-B aligned column)
+  const int wy = Y0 - 2;
+  const int tid = threadIdx.x;
+  // ---- stage the window
+  {
+    constexpr int q4 = kTbSW / 4;
+    for (int e = tid; e < kTbSH * q4; e += kTbThreads) {
+      const int r = e / q4, q = e % q4;
+      const int j = wy + r, i = wx + 4 * q;
+      const bool ok = (j >= 0) && (j <= ny) && (i >= 0) && (i + 3 < P);
+      const size_t off = ok ? (size_t)j * P + i : 0;
+      cp_async16(sEx + r * kTbSW + 4 * q, ex + off, ok);
+      cp_async16(sEy + r * kTbSW + 4 * q, ey + off, ok);
+      cp_async16(sHz + r * kTbSW + 4 * q, hz + off, ok);
+      cp_async16(sM + r * kTbSW + 4 * q, sd.mat + off, ok);
+      cp_async16(sM + r * kTbSW + 4 * q + 2, sd.mat + off + 2, ok);
+    }
+    cp_async_wait_all();
+    __syncthreads();
+  }
+  auto S = [&](int i, int j) { return (j - wy) * kTbSW + (i - wx); };
+  auto live = [&](int i, int j) { return i >= 0 && i < nx && j >= 0 && j < ny && sM[S(i, j)].x >= 0.f; };
+  auto h_update = [&](int ia, int ib, int ja, int jb) {   // inclusive ranges
+    const int w = ib - ia + 1;
+    for (int e = tid; e < w * (jb - ja + 1); e += kTbThreads) {
+      const int i = ia + e % w, j = ja + e / w;
+      const int s = S(i, j);
+      sHz[s] = live(i, j) ? sHz[s] + sd.chx * (sEx[s + kTbSW] - sEx[s]) - sd.chy * (sEy[s + 1] - sEy[s]) : 0.f;
+    }
+  };
+  auto e_update = [&](int ia, int ib, int ja, int jb) {   // Ex and Ey owned by cells in the range
+    const int w = ib - ia + 1;
+    for (int e = tid; e < w * (jb - ja + 1); e += kTbThreads) {
+      const int i = ia + e % w, j = ja + e / w;
+      const int s = S(i, j);
+      const bool me = live(i, j);
+      float ca, cb;
+      if (me && j >= 1 && live(i, j - 1)) {
+        edge_coef(sM[s - kTbSW], sM[s], ca, cb);
+        sEx[s] = ca * sEx[s] + cb * sd.rdy * (sHz[s] - sHz[s - kTbSW]);
+      }
+      if (me && i >= 1 && live(i - 1, j)) {
+        edge_coef(sM[s - 1], sM[s], ca, cb);
+        sEy[s] = ca * sEy[s] - cb * sd.rdx * (sHz[s] - sHz[s - 1]);
+      }
+    }
+  };
+  auto sources = [&](int ia, int ib, int ja, int jb, long long n) {
+    for (int e = tt.src_b + tid; e < tt.src_e; e += kTbThreads) {
+      const SrcEdge se = tb->src[e];
+      if (se.i < ia || se.i > ib || se.j < ja || se.j > jb) continue;
+      const int s = S(se.i, se.j);
+      float ca, cb;
+      edge_coef(se.comp == 0 ? sM[s - kTbSW] : sM[s - 1], sM[s], ca, cb);
+      (se.comp == 0 ? sEx : sEy)[s] -= cb * run->waves[se.src][n];
+    }
+  };
+  auto probes = [&](long long n) {
+    for (int e = tt.prb_b + tid; e < tt.prb_e; e += kTbThreads) {
+      const int p = tb->prb_idx[e];
+      const int cell = run->probe_cell[p];
+      run->probe_out[n * run->nprobe + p] = sHz[S(cell % P, cell / P)];
+    }
+  };
+  // model state staging (model tiles): s_state[b] = [s; h; 0], ri.ld floats
+  __shared__ __align__(16) float s_state[2][kTbMaxRomN];
+  RomInstDev ri{};
+  if (tt.rom >= 0) {
+    ri = insts[tt.rom];
+    const float* st = par ? ri.state[1] : ri.state[0];
+    for (int k = tid; k < ri.ld; k += kTbThreads) {
+      s_state[0][k] = k < ri.n ? st[k] : 0.f;
+      s_state[1][k] = 0.f;
+    }
+  }
+  auto rom_phase = [&](int from) {   // s_state[from] -> s_state[1-from], y into sEx/sEy
+    float* hv = s_state[from] + ri.n;
+    for (int k = tid; k < ri.ny; k += kTbThreads) {
+      const int cell = ri.h_cell[k];
+      hv[k] = sHz[S(cell % P, cell / P)];
+    }
+    __syncthreads();
+    tb_rom_step(ri, s_state[from], s_state[1 - from]);
+    __syncthreads();
+    for (int k = tid; k < ri.ny; k += kTbThreads) {
+      const int code = ri.y_edge[k];
+      const int off = code & 0x3fffffff;
+      (code >> 30 ? sEy : sEx)[S(off % P, off / P)] = s_state[1 - from][k];
+    }
+    __syncthreads();
+  };
+  const long long n0 = run->base + 2 * (long long)c;
+  // ---- step n
+  h_update(X0 - 2, X1, Y0 - 2, Y1);
+  __syncthreads();
+  probes(n0);
+  e_update(X0 - 1, X1, Y0 - 1, Y1);
+  __syncthreads();
+  sources(X0 - 1, X1, Y0 - 1, Y1, n0);
+  __syncthreads();
+  if (tt.rom >= 0) rom_phase(0);
+  // ---- step n+1
+  h_update(X0 - 1, X1 - 1, Y0 - 1, Y1 - 1);
+  __syncthreads();
+  probes(n0 + 1);
+  e_update(X0, X1 - 1, Y0, Y1 - 1);
+  __syncthreads();
+  sources(X0, X1 - 1, Y0, Y1 - 1, n0 + 1);
+  __syncthreads();
+  if (tt.rom >= 0) {
+    rom_phase(1);
+    float* so = par ? ri.state[0] : ri.state[1];
+    for (int k = tid; k < ri.n; k += kTbThreads) so[k] = s_state[0][k];
+  }
+  // ---- write O (ordinary tiles skip zone cells)
+  const int w = X1 - X0;
+  for (int e = tid; e < w * (Y1 - Y0); e += kTbThreads) {
+    const int i = X0 + e % w, j = Y0 + e / w;
+    bool own = true;
+    for (int z = tt.zone_b; z < tt.zone_e; ++z) {
+      const int4 zn = tb->zones[z];
+      if (i >= zn.x && i < zn.z && j >= zn.y && j < zn.w) own = false;
+    }
+    if (!own) continue;
+    const int s = S(i, j);
+    const size_t off = (size_t)j * P + i;
+    hzo[off] = sHz[s];
+    exo[off] = sEx[s];
+    eyo[off] = sEy[s];
+  }
+}
+
+}  // namespace
