@@ -120,30 +120,72 @@ yee_tb2_kernel(const SimDev* __restrict__ sims, const TbTile* __restrict__ tiles
     __syncthreads();
   }
   auto S = [&](int i, int j) { return (j - wy) * kTbSW + (i - wx); };
-  auto live = [&](int i, int j) { return i >= 0 && i < nx && j >= 0 && j < ny && sM[S(i, j)].x >= 0.f; };
-  auto h_update = [&](int ia, int ib, int ja, int jb) {   // inclusive ranges
-    const int w = ib - ia + 1;
-    for (int e = tid; e < w * (jb - ja + 1); e += kTbThreads) {
-      const int i = ia + e % w, j = ja + e / w;
-      const int s = S(i, j);
-      sHz[s] = live(i, j) ? sHz[s] + sd.chx * (sEx[s + kTbSW] - sEx[s]) - sd.chy * (sEy[s + 1] - sEy[s]) : 0.f;
+  // Cells outside the grid are marked dead (their edges are PEC or outside).
+  if (wx < 0 || wx + kTbSW > nx || wy < 0 || wy + kTbSH > ny) {
+    for (int e = tid; e < kTbSH * kTbSW; e += kTbThreads) {
+      const int i = wx + e % kTbSW, j = wy + e / kTbSW;
+      if (i < 0 || i >= nx || j < 0 || j >= ny) sM[e].x = -1.f;
+    }
+    __syncthreads();
+  }
+  // Both sub-steps update the whole window (H: rows 0..SH-2, E: rows 1..SH-1)
+  // in float4 units; values within 3 cells of the window edge use neighbours
+  // outside the window and are wrong, but no output depends on them (the
+  // outputs are 4 columns and 2 rows inside the window).
+  constexpr int q4 = kTbSW / 4;
+  auto h_update = [&]() {
+    for (int u = tid; u < (kTbSH - 1) * q4; u += kTbThreads) {
+      const int s = (u / q4) * kTbSW + 4 * (u % q4);
+      const float4 e0 = ld4(sEx + s), e1 = ld4(sEx + s + kTbSW), yv = ld4(sEy + s);
+      float4 h = ld4(sHz + s);
+      const float4 ma = ld4(reinterpret_cast<const float*>(sM + s));
+      const float4 mb = ld4(reinterpret_cast<const float*>(sM + s + 2));
+      const float yA[5] = {yv.x, yv.y, yv.z, yv.w, sEy[s + 4]};
+      const float mx[4] = {ma.x, ma.z, mb.x, mb.z};
+      float hn[4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t)
+        hn[t] = mx[t] >= 0.f ? comp(h, t) + sd.chx * (comp(e1, t) - comp(e0, t)) - sd.chy * (yA[t + 1] - yA[t]) : 0.f;
+      st4(sHz + s, make_float4(hn[0], hn[1], hn[2], hn[3]));
     }
   };
-  auto e_update = [&](int ia, int ib, int ja, int jb) {   // Ex and Ey owned by cells in the range
-    const int w = ib - ia + 1;
-    for (int e = tid; e < w * (jb - ja + 1); e += kTbThreads) {
-      const int i = ia + e % w, j = ja + e / w;
-      const int s = S(i, j);
-      const bool me = live(i, j);
-      float ca, cb;
-      if (me && j >= 1 && live(i, j - 1)) {
-        edge_coef(sM[s - kTbSW], sM[s], ca, cb);
-        sEx[s] = ca * sEx[s] + cb * sd.rdy * (sHz[s] - sHz[s - kTbSW]);
+  auto e_update = [&]() {
+    for (int u = tid; u < (kTbSH - 1) * q4; u += kTbThreads) {
+      const int s = (u / q4 + 1) * kTbSW + 4 * (u % q4);
+      const float4 h = ld4(sHz + s), hd = ld4(sHz + s - kTbSW);
+      const float hL = sHz[s - 1];
+      float4 xv = ld4(sEx + s), yv = ld4(sEy + s);
+      const float4 ma = ld4(reinterpret_cast<const float*>(sM + s));
+      const float4 mb = ld4(reinterpret_cast<const float*>(sM + s + 2));
+      const float4 da = ld4(reinterpret_cast<const float*>(sM + s - kTbSW));
+      const float4 db = ld4(reinterpret_cast<const float*>(sM + s - kTbSW + 2));
+      const float2 mL = sM[s - 1];
+      const float2 m[4] = {make_float2(ma.x, ma.y), make_float2(ma.z, ma.w), make_float2(mb.x, mb.y),
+                           make_float2(mb.z, mb.w)};
+      const float2 md[4] = {make_float2(da.x, da.y), make_float2(da.z, da.w), make_float2(db.x, db.y),
+                            make_float2(db.z, db.w)};
+      float xo[4], yo[4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        float v = comp(xv, t);
+        if (md[t].x >= 0.f && m[t].x >= 0.f) {
+          float ca, cb;
+          edge_coef(md[t], m[t], ca, cb);
+          v = ca * v + cb * sd.rdy * (comp(h, t) - comp(hd, t));
+        }
+        xo[t] = v;
+        const float2 ml = t == 0 ? mL : m[t - 1];
+        const float hl = t == 0 ? hL : comp(h, t - 1);
+        float w = comp(yv, t);
+        if (ml.x >= 0.f && m[t].x >= 0.f) {
+          float ca, cb;
+          edge_coef(ml, m[t], ca, cb);
+          w = ca * w - cb * sd.rdx * (comp(h, t) - hl);
+        }
+        yo[t] = w;
       }
-      if (me && i >= 1 && live(i - 1, j)) {
-        edge_coef(sM[s - 1], sM[s], ca, cb);
-        sEy[s] = ca * sEy[s] - cb * sd.rdx * (sHz[s] - sHz[s - 1]);
-      }
+      st4(sEx + s, make_float4(xo[0], xo[1], xo[2], xo[3]));
+      st4(sEy + s, make_float4(yo[0], yo[1], yo[2], yo[3]));
     }
   };
   auto sources = [&](int ia, int ib, int ja, int jb, long long n) {
@@ -192,19 +234,19 @@ yee_tb2_kernel(const SimDev* __restrict__ sims, const TbTile* __restrict__ tiles
   };
   const long long n0 = run->base + 2 * (long long)c;
   // ---- step n
-  h_update(X0 - 2, X1, Y0 - 2, Y1);
+  h_update();
   __syncthreads();
   probes(n0);
-  e_update(X0 - 1, X1, Y0 - 1, Y1);
+  e_update();
   __syncthreads();
   sources(X0 - 1, X1, Y0 - 1, Y1, n0);
   __syncthreads();
   if (tt.rom >= 0) rom_phase(0);
   // ---- step n+1
-  h_update(X0 - 1, X1 - 1, Y0 - 1, Y1 - 1);
+  h_update();
   __syncthreads();
   probes(n0 + 1);
-  e_update(X0, X1 - 1, Y0, Y1 - 1);
+  e_update();
   __syncthreads();
   sources(X0, X1 - 1, Y0, Y1 - 1, n0 + 1);
   __syncthreads();
@@ -214,20 +256,32 @@ yee_tb2_kernel(const SimDev* __restrict__ sims, const TbTile* __restrict__ tiles
     for (int k = tid; k < ri.n; k += kTbThreads) so[k] = s_state[0][k];
   }
   // ---- write O (ordinary tiles skip zone cells)
-  const int w = X1 - X0;
-  for (int e = tid; e < w * (Y1 - Y0); e += kTbThreads) {
-    const int i = X0 + e % w, j = Y0 + e / w;
-    bool own = true;
-    for (int z = tt.zone_b; z < tt.zone_e; ++z) {
-      const int4 zn = tb->zones[z];
-      if (i >= zn.x && i < zn.z && j >= zn.y && j < zn.w) own = false;
+  if (tt.rom < 0 && tt.zone_b == tt.zone_e && ((X1 - X0) & 3) == 0) {
+    const int w4 = (X1 - X0) >> 2;
+    for (int e = tid; e < w4 * (Y1 - Y0); e += kTbThreads) {
+      const int i = X0 + 4 * (e % w4), j = Y0 + e / w4;
+      const int s = S(i, j);
+      const size_t off = (size_t)j * P + i;
+      st4(hzo + off, ld4(sHz + s));
+      st4(exo + off, ld4(sEx + s));
+      st4(eyo + off, ld4(sEy + s));
     }
-    if (!own) continue;
-    const int s = S(i, j);
-    const size_t off = (size_t)j * P + i;
-    hzo[off] = sHz[s];
-    exo[off] = sEx[s];
-    eyo[off] = sEy[s];
+  } else {
+    const int w = X1 - X0;
+    for (int e = tid; e < w * (Y1 - Y0); e += kTbThreads) {
+      const int i = X0 + e % w, j = Y0 + e / w;
+      bool own = true;
+      for (int z = tt.zone_b; z < tt.zone_e; ++z) {
+        const int4 zn = tb->zones[z];
+        if (i >= zn.x && i < zn.z && j >= zn.y && j < zn.w) own = false;
+      }
+      if (!own) continue;
+      const int s = S(i, j);
+      const size_t off = (size_t)j * P + i;
+      hzo[off] = sHz[s];
+      exo[off] = sEx[s];
+      eyo[off] = sEy[s];
+    }
   }
 }
 
