@@ -694,13 +694,15 @@ void drop_graphs(fdtd_ctx* ctx) {
 // tile per model whose output is the model's zone, and the zone lists.  The
 // path is used only when every model fits the in-CTA model step and no model
 // lies within reach (two steps plus the zone margin) of another's tile.
-// FDTD_TB=0 disables it.
+// Opt-in (FDTD_TB=1): on GB300 it halves the DRAM bytes per step but is
+// issue-bound and slower than the one-step kernel (measured 118 vs 186
+// Gcell-steps/s at 4096^2).
 int plan_tb(fdtd_ctx* ctx) {
   ctx->tb = false;
   ctx->tb_tiles.clear();
   ctx->tb_zones.clear();
-  if (const char* e = getenv("FDTD_TB"))
-    if (atoi(e) == 0) return FDTD_OK;
+  const char* e = getenv("FDTD_TB");
+  if (!e || atoi(e) != 1) return FDTD_OK;
   const int M = kTbZoneMargin;
   std::vector<int4> zone(ctx->insts.size());
   for (size_t k = 0; k < ctx->insts.size(); ++k) {
