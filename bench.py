@@ -71,13 +71,16 @@ def profile_traffic():
 
 
 def stencil_source_sha():
-    """Hash of the stencil kernel's source: kernels.cuh plus the part of
-    fdtd.cu from the stencil kernel up to the reduced-model kernel."""
+    """Hash of the stencil kernel's source: the grid and tile structures of
+    kernels.cuh (up to the reduced-model structures) plus the part of fdtd.cu
+    from the stencil kernel up to the reduced-model kernel."""
     d = os.path.join(ROOT, "paper_1609_07114_gb300", "csrc")
     cu = open(os.path.join(d, "fdtd.cu")).read()
     a = cu.index("// Fused coarse H and E half steps")
     b = cu.index("// Eq. (23) for every embedded model")
-    h = hashlib.sha256(open(os.path.join(d, "kernels.cuh"), "rb").read() + cu[a:b].encode())
+    kh = open(os.path.join(d, "kernels.cuh")).read()
+    kh = kh[:kh.index("struct RomInstDev")]
+    h = hashlib.sha256(kh.encode() + cu[a:b].encode())
     return h.hexdigest()[:16]
 
 
@@ -331,6 +334,124 @@ def run_adjoint(args):
         "clocks": clk.summary()}))
 
 
+def run_lattice(args):
+    """Many heterogeneous models with CFL extension: an 8192^2 vacuum grid
+    with 1% lossy scatterers, 64 embedded models of three types (r = 5, q =
+    60/180/400) at dt = 2 x the fine-mesh CFL limit, four full-column line
+    sources, 16 probes.  One benchmark step = --tsteps time steps (default
+    1000, so ten timed steps are the configuration's 10000).  --lossless
+    runs the sigma = 0 variant; --energy-every E then also records the
+    storage function every E steps over --tsteps x (warmup + steps) steps and
+    reports its drift after the pulse has left the sources."""
+    import numpy as np
+    import torch
+    import paper_1609_07114_gb300 as pg
+    from paper_1609_07114_gb300 import build as pbuild
+    import workloads
+    pbuild.build()
+    K, W, T = args.steps, args.warmup, args.tsteps
+    total = (W + K) * T
+    w = workloads.lattice_8192(min(total, 20000), lossless=args.lossless)
+    ctx = pg.FdtdContext(w["dx"], w["dy"], w["dt"], [(w["eps_r"], w["sigma"])])
+    t0 = time.perf_counter()
+    built = {}
+    for rd in w["roms"]:
+        key = id(rd["eps_r"])
+        if key not in built:
+            built[key] = pg.rom_build(rd["a"], rd["b"], rd["r"], w["dx"], w["dy"], w["dt"], rd["eps_r"],
+                                      rd["sigma"], rd["q"], f0=rd["f0"])
+        ctx.rom_embed(built[key], 0, rd["i0"], rd["j0"])
+    rom_seconds = time.perf_counter() - t0
+    nwave = len(w["sources"][0]["wave"])
+    wave = torch.zeros(total + T, dtype=torch.float32, device="cuda")
+    wave[:nwave] = torch.tensor(w["sources"][0]["wave"].astype(np.float32), device="cuda")
+    probes = [(0, i, j) for (i, j) in w["probes"]]
+    out = torch.zeros((T, len(probes)), dtype=torch.float32, device="cuda")
+
+    def one_step(k):
+        src = [dict(s, sim=0, wave=wave[k * T:(k + 1) * T]) for s in w["sources"]]
+        ctx.fdtd_run(T, src, probes, out)
+
+    energy = []
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if args.energy_every:
+        E = args.energy_every
+        assert T % E == 0
+        src_all = [dict(s, sim=0, wave=wave) for s in w["sources"]]
+        t_run = 0.0
+        with ClockSampler() as clk:
+            for k in range(total // E):
+                src = [dict(s, wave=s["wave"][k * E:(k + 1) * E]) for s in src_all]
+                torch.cuda.synchronize()
+                e0.record(stream)
+                ctx.fdtd_run(E, src, probes, out[:E] if E <= T else None)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                t_run += e0.elapsed_time(e1) / 1e3
+                energy.append(float(ctx.energy()[0]))
+        el_s = t_run
+        nsteps_timed = total
+    else:
+        for k in range(W):
+            one_step(k)
+        torch.cuda.synchronize()
+        with ClockSampler() as clk:
+            e0.record(stream)
+            for k in range(W, W + K):
+                one_step(k)
+            e1.record(stream)
+            torch.cuda.synchronize()
+        el_s = e0.elapsed_time(e1) / 1e3
+        nsteps_timed = K * T
+    cells = w["nx"] * w["ny"]
+    value = cells * nsteps_timed / el_s / 1e9
+    ctx.set_timing(True)
+    for k in range(2):
+        one_step(k)
+    yee_ms, n_yee, post_ms, n_post = ctx.kernel_times()
+    ctx.set_timing(False)
+    f_nb = float(np.mean((w["eps_r"] != 1.0) | (w["sigma"] != 0.0)))
+    bpc = 24.0 + 8.0 * f_nb     # fields + the materials of non-background cells
+    hbm, kind = peaks()
+    achieved = bpc * cells / (yee_ms / n_yee / 1e3) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": K, "warmup": W,
+        "ms_per_step": el_s / max(nsteps_timed // T, 1) * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"lattice_8192: 8192^2 vacuum grid, {100 * f_nb:.2f}% "
+                               f"{'lossless' if args.lossless else 'lossy'} scatterer cells, 64 ROMs of 3 "
+                               "types (r=5, q=60/180/400) at dt=2x fine CFL, 4 full-column Jy line "
+                               "sources, 16 Hz probes",
+                   "time_steps_per_step": T, "nx": w["nx"], "ny": w["ny"], "roms": len(w["roms"]),
+                   "rom_q": sorted({m.q for m in built.values()}),
+                   "rom_clamped": [m.report.n_clamped for m in built.values()],
+                   "rom_build_s": round(rom_seconds, 3),
+                   "l2": "inputs larger than L2: 1.6 GB of fields per time step (L2 129 MB)"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "traffic": None, "peak_kind": kind,
+                     "kernel": "yee_step_kernel", "kernel_avg_ms": yee_ms / n_yee,
+                     "alg_bytes_per_cell_step": bpc, "rom_post_avg_ms": post_ms / max(n_post, 1)},
+        "gpu_launches": (nsteps_timed // T) * (2 * T + T // 16),
+        "clocks": clk.summary(),
+    }
+    if energy:
+        E = args.energy_every
+        wv = np.abs(w["sources"][0]["wave"])
+        n_quiet = int(np.nonzero(wv > 1e-12 * wv.max())[0][-1]) + 1   # sources silent from here on
+        k0 = min(len(energy) - 1, (n_quiet + E - 1) // E)
+        ref = energy[k0]
+        tail = np.array(energy[k0:])
+        x = np.arange(len(tail)) * E
+        slope = float(np.polyfit(x, tail / ref, 1)[0]) if len(tail) > 2 else 0.0
+        line["energy"] = {"every": E, "samples": len(energy), "from_step": k0 * E, "W_ref": ref,
+                          "max_rel_dev": float(np.abs(tail / ref - 1).max()),
+                          "final_rel_dev": float(tail[-1] / ref - 1),
+                          "slope_per_1e6_steps": slope * 1e6}
+    print(json.dumps(line))
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -341,7 +462,10 @@ def main():
     ap.add_argument("--cpu-sample-steps", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--grid", type=int, default=4096, help="coarse grid size (4096 = the benchmark)")
-    ap.add_argument("--workload", default="grid", choices=["grid", "batched", "adjoint"])
+    ap.add_argument("--workload", default="grid", choices=["grid", "batched", "adjoint", "lattice"])
+    ap.add_argument("--lossless", action="store_true", help="lattice: sigma = 0 everywhere")
+    ap.add_argument("--energy-every", type=int, default=0,
+                    help="lattice: record the storage function every E steps")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -353,6 +477,11 @@ def main():
             args.steps = 3
         args.warmup = 1 if args.warmup == 3 else args.warmup
         run_adjoint(args)
+        return
+    if args.workload == "lattice":
+        if args.tsteps == 2000:
+            args.tsteps = 1000         # 10 timed steps = the configuration's 10000 time steps
+        run_lattice(args)
         return
     if args.workload == "batched":
         if args.tsteps == 2000:

@@ -219,6 +219,28 @@ int fdtd_grad(fdtd_ctx* ctx, long long nsteps, const fdtd_source* src, int nsrc,
               const fdtd_probe* probes, int nprobe, int ckpt_every, float* dJ_deps,
               float* dJ_dsigma, float* dJ_dsrc, double* J_out);
 
+/* -------------------------------------------------------- frequency response */
+
+/* Running DFT monitors of Hz (the paper reports its results as frequency
+ * responses and reflected power, Sec. VI).  Sets nmon monitor cells
+ * (fdtd_probe: sim, coarse cell i, j) and nfreq frequencies (Hz, finite,
+ * >= 0) and sets the accumulators to acc_init ([nmon][nfreq][2] doubles
+ * {Re, Im} as returned by fdtd_dft_get; NULL = zeros).  From then on every
+ * time step n the context takes (fdtd_run, fdtd_run_host and the forward
+ * pass of fdtd_grad; n counted from creation, as fdtd_get_step) adds
+ *     X_m(f) += Hz^{n+1/2}(m) exp(-i 2 pi f (n + 1/2) dt) dt
+ * in FP64 (fused into the probe step on the device).  nmon = 0 removes the
+ * monitors.  Host arrays are copied.  FDTD_EINVAL for a monitor outside its
+ * grid, a bad frequency or more than 2^24 monitor-frequency pairs.
+ * Synchronises the context's stream.  While monitors are set the
+ * two-steps-per-launch path is not used. */
+int fdtd_dft_set(fdtd_ctx* ctx, const fdtd_probe* mons, int nmon, const double* freqs,
+                 int nfreq, const double* acc_init);
+/* Host copy of the accumulators: out[m][f] = {Re X_m(f), Im X_m(f)}
+ * (2 nmon nfreq doubles; nothing is written when no monitors are set).
+ * Synchronises the context's stream. */
+int fdtd_dft_get(fdtd_ctx* ctx, double* out);
+
 /* ------------------------------------------------------------------ state */
 
 /* Host copies of the current fields of one simulation (E^n, Hz^{n-1/2}). */

@@ -101,6 +101,8 @@ def lib() -> C.CDLL:
         "fdtd_grad": (i, [vp, ll, C.POINTER(fdtd_source), i, C.POINTER(fdtd_probe), i, i,
                           vp, vp, vp, _dp]),
         "fdtd_energy_noalloc": (i, [vp, _dp]),
+        "fdtd_dft_set": (i, [vp, C.POINTER(fdtd_probe), i, _dp, i, _dp]),
+        "fdtd_dft_get": (i, [vp, _dp]),
         "fdtd_set_timing": (i, [vp, i]),
         "fdtd_get_kernel_times": (i, [vp, _dp, C.POINTER(ll), _dp, C.POINTER(ll)]),
         "fdtd_last_error": (C.c_char_p, [vp]),
@@ -320,6 +322,30 @@ class FdtdContext:
         """``fdtd_load_state``."""
         buf = C.create_string_buffer(data, len(data))
         self._ck(lib().fdtd_load_state(self._h, buf, len(data)))
+
+    def dft_set(self, monitors, freqs, init=None):
+        """Running DFT monitors of Hz (``fdtd_dft_set``): monitors are
+        (sim, i, j) or (i, j); freqs in Hz; init an optional complex
+        [nmon, nfreq] array of starting sums (as returned by dft_get)."""
+        f = _f64(freqs)
+        nmon = len(monitors)
+        if init is not None:
+            a = np.asarray(init, dtype=np.complex128).reshape(nmon, f.size)
+            acc = np.ascontiguousarray(np.stack([a.real, a.imag], axis=-1))
+            self._dft_init = acc
+            ip = acc.ctypes.data_as(_dp)
+        else:
+            ip = None
+        self._ck(lib().fdtd_dft_set(self._h, self._probes(monitors), nmon, f.ctypes.data_as(_dp),
+                                    f.size if nmon else 0, ip))
+        self._dft_shape = (nmon, f.size if nmon else 0)
+
+    def dft_get(self):
+        """X[m, f] = sum_n Hz^{n+1/2}(m) exp(-i 2 pi f (n + 1/2) dt) dt (complex)."""
+        nmon, nf = getattr(self, "_dft_shape", (0, 0))
+        out = np.zeros((nmon, nf, 2))
+        self._ck(lib().fdtd_dft_get(self._h, out.ctypes.data_as(_dp)))
+        return out[..., 0] + 1j * out[..., 1]
 
     def step_count(self):
         n = C.c_longlong()

@@ -11,6 +11,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <memory>
 #include <mutex>
 #include <new>
@@ -75,23 +76,30 @@ struct RowIn {
   float2 mL;
 };
 
+// dense = the row's strip holds cells other than the background bg (its
+// materials are read; otherwise every cell of the strip row is bg).
 template <int V>
 __device__ __forceinline__ void load_row(RowIn<V>& r, const float* __restrict__ ex,
                                          const float* __restrict__ ey, const float* __restrict__ hz,
                                          const float2* __restrict__ mat, size_t row, int P, int cl,
-                                         int c0, int nx, int lane, bool halo) {
+                                         int c0, int nx, int lane, bool halo, bool dense, float2 bg) {
   using T = typename Vec<V>::T;
   r.exn = *reinterpret_cast<const T*>(ex + row + P + cl);
   r.eyv = *reinterpret_cast<const T*>(ey + row + cl);
   r.hzv = *reinterpret_cast<const T*>(hz + row + cl);
+  if (dense) {
 #pragma unroll
-  for (int h = 0; h < V / 2; ++h) r.m4[h] = ld4(reinterpret_cast<const float*>(mat + row + cl + 2 * h));
+    for (int h = 0; h < V / 2; ++h) r.m4[h] = ld4(reinterpret_cast<const float*>(mat + row + cl + 2 * h));
+  } else {
+#pragma unroll
+    for (int h = 0; h < V / 2; ++h) r.m4[h] = make_float4(bg.x, bg.y, bg.x, bg.y);
+  }
   r.eyR = (lane == 31 && c0 + 32 * V <= nx) ? ey[row + c0 + 32 * V] : 0.f;
   if (halo) {
     r.exLn = ex[row + P + c0 - 1];
     r.eyL = ey[row + c0 - 1];
     r.hzL = hz[row + c0 - 1];
-    r.mL = mat[row + c0 - 1];
+    r.mL = dense ? mat[row + c0 - 1] : bg;
   } else {
     r.exLn = r.eyL = r.hzL = 0.f;
     r.mL = make_float2(-1.f, 0.f);
@@ -132,11 +140,19 @@ yee_step_kernel(const SimDev* __restrict__ sims, const TileWork* __restrict__ wo
       mp[t] = make_float2(0.f, 0.f);
     }
     float exLc = halo ? ex[(size_t)j * P + c0 - 1] : 0.f;
+    // Sparse-material bits of rows j .. j1-1 of this strip: lane w holds word
+    // jb + w (tile heights are capped so that 32 words cover a tile).
+    const int jb = j >> 5;
+    const float2 bg = sd.mbg;
+    uint32_t fw = 0xffffffffu;
+    if (jb + lane <= ((sd.ny - 1) >> 5)) fw = sd.mbits[(size_t)(jb + lane) * sd.nstrip + (c0 >> 7)];
+    auto dense = [&](int jj) { return ((__shfl_sync(FULL, fw, (jj >> 5) - jb) >> (jj & 31)) & 1u) != 0u; };
     RowIn<V> cur, nxt;
-    load_row<V>(cur, ex, ey, hz, mat, (size_t)j * P, P, cl, c0, nx, lane, halo);
+    load_row<V>(cur, ex, ey, hz, mat, (size_t)j * P, P, cl, c0, nx, lane, halo, dense(j), bg);
     for (; j < j1; ++j) {
       const size_t row = (size_t)j * P;
-      if (j + 1 < j1) load_row<V>(nxt, ex, ey, hz, mat, row + P, P, cl, c0, nx, lane, halo);
+      const bool dn = dense(j + 1 < j1 ? j + 1 : j);
+      if (j + 1 < j1) load_row<V>(nxt, ex, ey, hz, mat, row + P, P, cl, c0, nx, lane, halo, dn, bg);
       float2 m[V];
 #pragma unroll
       for (int h = 0; h < V / 2; ++h) {
@@ -407,12 +423,35 @@ rom_post_kernel(const SimDev* __restrict__ sims, const RomInstDev* __restrict__ 
       }
     }
   } else {
-    const int p = (blockIdx.x - nwork - ngwork) * blockDim.x + threadIdx.x;
-    if (p < run->nprobe) {
-      const long long n = run->base + c;
-      const SimDev* sd = sims + run->probe_sim[p];
-      const float* hzn = par ? sd->hz[0] : sd->hz[1];
-      run->probe_out[n * run->nprobe + p] = hzn[run->probe_cell[p]];
+    // Probe blocks, then running-DFT blocks (one thread per monitor and
+    // frequency; each accumulator has one owner, steps are stream-ordered).
+    const int b = blockIdx.x - nwork - ngwork;
+    const int pb = (run->nprobe + blockDim.x - 1) / blockDim.x;
+    const long long n = run->base + c;
+    if (b < pb) {
+      const int p = b * blockDim.x + threadIdx.x;
+      if (p < run->nprobe) {
+        const SimDev* sd = sims + run->probe_sim[p];
+        const float* hzn = par ? sd->hz[0] : sd->hz[1];
+        run->probe_out[n * run->nprobe + p] = hzn[run->probe_cell[p]];
+      }
+    } else {
+      const int q = (b - pb) * blockDim.x + threadIdx.x;
+      if (q < run->ndft) {
+        const int m = q / run->nfreq, f = q - m * run->nfreq;
+        const SimDev* sd = sims + run->dft_sim[m];
+        const float* hzn = par ? sd->hz[0] : sd->hz[1];
+        const double v = hzn[run->dft_cell[m]];
+        // phase in cycles at t^{n+1/2}, reduced to [0, 1) before sin/cos
+        double x = run->dft_fdt[f] * ((double)(run->step0 + n) + 0.5);
+        x -= floor(x);
+        double sn, cs;
+        sincospi(2.0 * x, &sn, &cs);
+        double2 a = run->dft_acc[q];
+        a.x += v * cs;
+        a.y -= v * sn;
+        run->dft_acc[q] = a;
+      }
     }
   }
 }
@@ -558,8 +597,51 @@ struct SimHost {
   float* ey[2] = {nullptr, nullptr};
   float* hz[2] = {nullptr, nullptr};
   float2* mat_d = nullptr;
+  float2 mbg = {0.f, 0.f};                // background material (sparse-material bits)
+  int nstrip = 0;                         // 128-column strips per row
+  std::vector<uint32_t> mbits;
+  uint32_t* mbits_d = nullptr;
+  bool all_dense = false;
   int tile_base = 0, ncx = 0, ncy = 0, th = 0;   // tiles: ncx x ncy of kCtaCols x th cells
 };
+
+// Background of a simulation: the most frequent material among up to 4096
+// cells sampled on a regular stride (none when no value repeats, i.e. every
+// strip row is read densely).
+bool pick_background(const SimHost& sh, float2* bg) {
+  std::map<uint64_t, int> cnt;
+  const long long ncell = (long long)sh.nx * sh.ny;
+  const long long stride = std::max<long long>(1, ncell / 4096);
+  for (long long k = 0; k < ncell; k += stride) {
+    const float2 m = sh.mat[(size_t)(k / sh.nx) * sh.pitch + (k % sh.nx)];
+    uint64_t key;
+    std::memcpy(&key, &m, sizeof(key));
+    ++cnt[key];
+  }
+  uint64_t best = 0;
+  int bc = 0;
+  for (const auto& kv : cnt)
+    if (kv.second > bc) best = kv.first, bc = kv.second;
+  if (bc < 2) return false;
+  std::memcpy(bg, &best, sizeof(best));
+  return true;
+}
+
+// Recompute the sparse-material bits of rows [ja, jb).
+void update_mbits(SimHost& sh, int ja, int jb) {
+  const uint64_t* m = reinterpret_cast<const uint64_t*>(sh.mat.data());
+  uint64_t bgk;
+  std::memcpy(&bgk, &sh.mbg, sizeof(bgk));
+  for (int j = ja; j < jb; ++j)
+    for (int st = 0; st < sh.nstrip; ++st) {
+      bool dense = sh.all_dense;
+      const int i0 = std::max(st * 128 - 1, 0), i1 = std::min(st * 128 + 128, sh.nx);
+      for (int i = i0; i < i1 && !dense; ++i) dense = m[(size_t)j * sh.pitch + i] != bgk;
+      uint32_t& w = sh.mbits[(size_t)(j >> 5) * sh.nstrip + st];
+      const uint32_t bit = 1u << (j & 31);
+      w = dense ? (w | bit) : (w & ~bit);
+    }
+}
 
 // The run-time map of one (model, interface materials) pair.  Instances of
 // the same model whose outside half cells carry identical materials share it
@@ -638,6 +720,11 @@ struct fdtd_ctx {
   DevBuf<const float*> waves;
   DevBuf<int> probe_sim, probe_cell;
   DevBuf<float> host_waves, host_probes;
+  // running DFT monitors (fdtd_dft_set)
+  int dft_nmon = 0, dft_nfreq = 0;
+  DevBuf<int> dft_sim, dft_cell;
+  DevBuf<double> dft_fdt;
+  DevBuf<double2> dft_acc;
   int cur = 0;
   long long step = 0;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
@@ -1016,6 +1103,13 @@ int prepare_run(fdtd_ctx* ctx, long long nsteps, const fdtd_source* src, int nsr
   rd.probe_sim = ctx->probe_sim.p;
   rd.probe_cell = ctx->probe_cell.p;
   rd.nprobe = nprobe;
+  rd.ndft = ctx->dft_nmon * ctx->dft_nfreq;
+  rd.step0 = ctx->step;
+  rd.dft_fdt = ctx->dft_fdt.p;
+  rd.dft_sim = ctx->dft_sim.p;
+  rd.dft_cell = ctx->dft_cell.p;
+  rd.dft_acc = ctx->dft_acc.p;
+  rd.nfreq = ctx->dft_nfreq;
   // Pageable host sources: cudaMemcpyAsync returns once the data are staged,
   // so the host vectors may go out of scope; the copies stay stream-ordered.
   CK(cudaMemcpyAsync(ctx->run_d, &rd, sizeof(RunDev), cudaMemcpyHostToDevice, st));
@@ -1023,6 +1117,12 @@ int prepare_run(fdtd_ctx* ctx, long long nsteps, const fdtd_source* src, int nsr
 }
 
 void launch_tb(fdtd_ctx* ctx, cudaStream_t s, int par, int c);
+
+// Blocks of rom_post after the model rows: probes, then DFT monitors.
+int post_extra_blocks(const fdtd_ctx* ctx, int nprobe) {
+  constexpr int t = kRomRowsPerCta * 32;
+  return (nprobe + t - 1) / t + (ctx->dft_nmon * ctx->dft_nfreq + t - 1) / t;
+}
 
 // Sums the elapsed times of the recorded event triples (yee, post).
 int drain_events(fdtd_ctx* ctx) {
@@ -1039,7 +1139,7 @@ int drain_events(fdtd_ctx* ctx) {
 }
 
 int march_timed(fdtd_ctx* ctx, long long nsteps, int nprobe) {
-  const int nprobe_blocks = (nprobe + kRomRowsPerCta * 32 - 1) / (kRomRowsPerCta * 32);
+  const int nprobe_blocks = post_extra_blocks(ctx, nprobe);
   const bool post = ctx->nromwork + ctx->ngwork + nprobe_blocks > 0;
   while ((int)ctx->ev.size() < 3 * 64) {
     cudaEvent_t e;
@@ -1047,7 +1147,7 @@ int march_timed(fdtd_ctx* ctx, long long nsteps, int nprobe) {
     ctx->ev.push_back(e);
   }
   long long t = 0;
-  if (ctx->tb) {   // pairs of steps in one stencil launch; n_yee counts steps
+  if (ctx->tb && ctx->dft_nmon == 0) {   // pairs of steps in one stencil launch; n_yee counts steps
     for (; t + 2 <= nsteps; t += 2) {
       const int par = ctx->cur ^ (int)(t & 1);
       cudaEvent_t* e = &ctx->ev[ctx->ev_used];
@@ -1116,7 +1216,7 @@ int ensure_tb_graph(fdtd_ctx* ctx, int par, int nprobe) {
 // Two steps per launch: graph replays of kChunk steps, then pairs, then (odd
 // counts) one step of the one-step kernels.
 int march_tb(fdtd_ctx* ctx, long long nsteps, int nprobe) {
-  const int nprobe_blocks = (nprobe + kRomRowsPerCta * 32 - 1) / (kRomRowsPerCta * 32);
+  const int nprobe_blocks = post_extra_blocks(ctx, nprobe);
   long long done = 0;
   if (nsteps >= kChunk) {
     int rc = ensure_tb_graph(ctx, ctx->cur, nprobe);
@@ -1138,8 +1238,8 @@ int march_tb(fdtd_ctx* ctx, long long nsteps, int nprobe) {
 
 int march(fdtd_ctx* ctx, long long nsteps, int nprobe) {
   if (ctx->timing) return march_timed(ctx, nsteps, nprobe);
-  if (ctx->tb) return march_tb(ctx, nsteps, nprobe);
-  const int nprobe_blocks = (nprobe + kRomRowsPerCta * 32 - 1) / (kRomRowsPerCta * 32);
+  if (ctx->tb && ctx->dft_nmon == 0) return march_tb(ctx, nsteps, nprobe);
+  const int nprobe_blocks = post_extra_blocks(ctx, nprobe);
   long long done = 0;
   if (nsteps >= kChunk) {
     int rc = ensure_graph(ctx, ctx->cur, nprobe_blocks);
@@ -1183,7 +1283,7 @@ void plan_tiles(fdtd_ctx* ctx) {
   };
   int best = 32;
   if (const char* e = getenv("FDTD_TILE_ROWS")) {
-    best = std::max(4, atoi(e));
+    best = std::min(512, std::max(4, atoi(e)));   // <= 512: one warp's 32 bit words cover a tile
   } else {
     long long best_cost = -1;
     for (int th = 8; th <= 128; ++th) {
@@ -1259,6 +1359,7 @@ void fdtd_destroy(fdtd_ctx* ctx) {
       cudaFree(s.hz[p]);
     }
     cudaFree(s.mat_d);
+    cudaFree(s.mbits_d);
   }
   for (Instance& in : ctx->insts) {
     cudaFree(in.state_d[0]);
@@ -1355,14 +1456,24 @@ int fdtd_create(const fdtd_grid_desc* g, void* cuda_stream, fdtd_ctx** out) {
       cudaMemset(sh.ey[p], 0, bytes);
       cudaMemset(sh.hz[p], 0, bytes);
     }
-    if (cudaMalloc(&sh.mat_d, sizeof(float2) * sh.mat.size()) != cudaSuccess) {
+    sh.nstrip = sh.pitch / 128;
+    const char* md = getenv("FDTD_MAT_DENSE");
+    sh.all_dense = (md && atoi(md) == 1) || !pick_background(sh, &sh.mbg);
+    sh.mbits.assign((size_t)((d.ny + 31) / 32) * sh.nstrip, 0u);
+    update_mbits(sh, 0, d.ny);
+    if (cudaMalloc(&sh.mat_d, sizeof(float2) * sh.mat.size()) != cudaSuccess ||
+        cudaMalloc(&sh.mbits_d, sizeof(uint32_t) * sh.mbits.size()) != cudaSuccess) {
       ctx->err = "fdtd_create: device allocation failed";
       return bail(FDTD_ENOMEM);
     }
     cudaMemcpy(sh.mat_d, sh.mat.data(), sizeof(float2) * sh.mat.size(), cudaMemcpyHostToDevice);
+    cudaMemcpy(sh.mbits_d, sh.mbits.data(), sizeof(uint32_t) * sh.mbits.size(), cudaMemcpyHostToDevice);
     SimDev& sd = sdev[s];
     for (int p = 0; p < 2; ++p) sd.ex[p] = sh.ex[p], sd.ey[p] = sh.ey[p], sd.hz[p] = sh.hz[p];
     sd.mat = sh.mat_d;
+    sd.mbits = sh.mbits_d;
+    sd.mbg = sh.mbg;
+    sd.nstrip = sh.nstrip;
     sd.nx = d.nx, sd.ny = d.ny, sd.pitch = sh.pitch;
     sd.chx = (float)(g->dt / (kMu0 * g->dy));
     sd.chy = (float)(g->dt / (kMu0 * g->dx));
@@ -1481,7 +1592,9 @@ int rom_embed(fdtd_ctx* ctx, const rom_model* m, int sim, int i0, int j0, int* i
       sh.region[(size_t)j * sh.nx + i] = 1;
       sh.mat[(size_t)j * sh.pitch + i].x = -1.f;
     }
+  update_mbits(sh, j0, j0 + b);
   CK(cudaMemcpy(sh.mat_d, sh.mat.data(), sizeof(float2) * sh.mat.size(), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(sh.mbits_d, sh.mbits.data(), sizeof(uint32_t) * sh.mbits.size(), cudaMemcpyHostToDevice));
   for (int p = 0; p < 2; ++p) {
     for (int j = j0; j <= j0 + b; ++j) {
       CK(cudaMemset(sh.ex[p] + (size_t)j * sh.pitch + i0, 0, sizeof(float) * a));
@@ -1759,6 +1872,59 @@ int fdtd_load_state(fdtd_ctx* ctx, const void* buf, size_t size) {
     p += sizeof(float) * in.n;
   }
   ctx->step = hdr[1];
+  return FDTD_OK;
+}
+
+int fdtd_dft_set(fdtd_ctx* ctx, const fdtd_probe* mons, int nmon, const double* freqs, int nfreq,
+                 const double* acc_init) {
+  if (!ctx || nmon < 0 || nfreq < 0 || (nmon > 0 && (!mons || !freqs || nfreq < 1)))
+    return fail(ctx, FDTD_EINVAL, "fdtd_dft_set: bad argument");
+  if ((long long)nmon * nfreq > (1ll << 24))
+    return fail(ctx, FDTD_EINVAL, "fdtd_dft_set: more than 2^24 monitor-frequency pairs");
+  std::vector<int> sim(nmon), cell(nmon);
+  for (int m = 0; m < nmon; ++m) {
+    if (mons[m].sim < 0 || mons[m].sim >= (int)ctx->sims.size())
+      return fail(ctx, FDTD_EINVAL, "fdtd_dft_set: monitor sim out of range");
+    const SimHost& sh = ctx->sims[mons[m].sim];
+    if (mons[m].i < 0 || mons[m].i >= sh.nx || mons[m].j < 0 || mons[m].j >= sh.ny)
+      return fail(ctx, FDTD_EINVAL, "fdtd_dft_set: monitor outside the grid");
+    sim[m] = mons[m].sim;
+    cell[m] = mons[m].j * sh.pitch + mons[m].i;
+  }
+  std::vector<double> fdt(nfreq);
+  for (int f = 0; f < nfreq && nmon > 0; ++f) {
+    if (!std::isfinite(freqs[f]) || freqs[f] < 0)
+      return fail(ctx, FDTD_EINVAL, "fdtd_dft_set: frequencies must be finite and >= 0");
+    fdt[f] = freqs[f] * ctx->dt;
+  }
+  CK(cudaStreamSynchronize(ctx->stream));   // no run may be using the old tables
+  ctx->dft_nmon = 0;
+  ctx->dft_nfreq = 0;
+  if (nmon == 0) return FDTD_OK;
+  const size_t np = (size_t)nmon * nfreq;
+  CK(ctx->dft_sim.reserve(nmon));
+  CK(ctx->dft_cell.reserve(nmon));
+  CK(ctx->dft_fdt.reserve(nfreq));
+  CK(ctx->dft_acc.reserve(np));
+  CK(cudaMemcpy(ctx->dft_sim.p, sim.data(), sizeof(int) * nmon, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ctx->dft_cell.p, cell.data(), sizeof(int) * nmon, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ctx->dft_fdt.p, fdt.data(), sizeof(double) * nfreq, cudaMemcpyHostToDevice));
+  std::vector<double2> acc(np, make_double2(0.0, 0.0));
+  if (acc_init)
+    for (size_t k = 0; k < np; ++k) acc[k] = make_double2(acc_init[2 * k] / ctx->dt, acc_init[2 * k + 1] / ctx->dt);
+  CK(cudaMemcpy(ctx->dft_acc.p, acc.data(), sizeof(double2) * np, cudaMemcpyHostToDevice));
+  ctx->dft_nmon = nmon;
+  ctx->dft_nfreq = nfreq;
+  return FDTD_OK;
+}
+
+int fdtd_dft_get(fdtd_ctx* ctx, double* out) {
+  if (!ctx || (!out && ctx->dft_nmon > 0)) return fail(ctx, FDTD_EINVAL, "fdtd_dft_get: bad argument");
+  const size_t np = (size_t)ctx->dft_nmon * ctx->dft_nfreq;
+  if (np == 0) return FDTD_OK;
+  CK(cudaStreamSynchronize(ctx->stream));
+  CK(cudaMemcpy(out, ctx->dft_acc.p, sizeof(double2) * np, cudaMemcpyDeviceToHost));
+  for (size_t k = 0; k < 2 * np; ++k) out[k] *= ctx->dt;
   return FDTD_OK;
 }
 

@@ -13,6 +13,12 @@
 // as float2 {eps0 eps_r / dt, sigma/2}, the first component set to -1 for
 // cells covered by a reduced model.  An E edge is updated only if both its
 // cells are coarse cells and it is not on the PEC wall.
+//
+// Sparse materials: a simulation's most frequent cell material is its
+// background mbg.  One bit per (row, 128-column strip) says whether any cell
+// of the strip, or the cell just left of it, differs from mbg; the stencil
+// reads the materials of flagged strip rows only (a vacuum grid with sparse
+// scatterers moves 24 B per cell-step instead of 32).
 #pragma once
 
 #include <cstdint>
@@ -29,7 +35,9 @@ struct SimDev {
   float* ey[2];
   float* hz[2];
   const float2* mat;
-  int nx, ny, pitch, pad;
+  const uint32_t* mbits;  // [(ny + 31) / 32][nstrip]: bit (j & 31) of word (j / 32, strip)
+  float2 mbg;             // background material
+  int nx, ny, pitch, nstrip;
   float chx;   // dt / (mu0 dy):  Hz += chx (Ex_{j+1} - Ex_j)
   float chy;   // dt / (mu0 dx):  Hz -= chy (Ey_{i+1} - Ey_i)
   float rdy;   // 1/dy: Ex += cb (Hz_j - Hz_{j-1}) / dy
@@ -89,6 +97,17 @@ struct RunDev {
   const int* probe_sim;
   const int* probe_cell;     // j * pitch + i
   int nprobe;
+  int ndft;                  // DFT monitors x frequencies (0: none)
+  // Running DFT of Hz at monitor cells (frequency responses): the step
+  // index of the context at the run start, per frequency f dt (cycles per
+  // step), per monitor its simulation and cell, and FP64 accumulators
+  // sum_n Hz^{n+1/2} exp(-i 2 pi f (n + 1/2) dt), [monitor][frequency].
+  long long step0;
+  const double* dft_fdt;
+  const int* dft_sim;
+  const int* dft_cell;
+  double2* dft_acc;
+  int nfreq;
   int pad;
 };
 

@@ -169,6 +169,81 @@ def lattice_lossless(n=256, nsteps=1_000_000, seed=None, lossless=True):
                 roms=roms, sources=[src], probes=[(n // 4, n // 4), (3 * n // 4, n // 4)], nsteps=nsteps)
 
 
+def lattice_8192(nsteps: int = 10000, n: int = 8192, pitch: int = 1024, lossless: bool = False,
+                 fill: float = 0.01, n_line: int = 4, n_probes: int = 16, seed=None):
+    """Many heterogeneous reduced models with CFL extension: an n x n vacuum
+    grid (dx = 1 mm) with seeded lossy rectangular scatterers (sides U[4, 16]
+    cells, eps_r ~ U[2, 6], sigma ~ U[0, 0.05]) covering a fraction `fill` of
+    the cells, and one embedded region per pitch x pitch lattice cell (seeded
+    jitter of up to pitch/4), drawn from three fine-region types refined r = 5
+    (regions of 6, 12 and 20 coarse cells, ROM orders 60, 180, 400; each type
+    holds one seeded dielectric inclusion).  Scatterers keep two cells from
+    every region, so each region's ring of outside half cells is vacuum.
+    n_line Jy line sources, each a full column of Ey edges at a seeded x clear
+    of the regions (fc = 10 GHz differentiated Gaussian); n_probes Hz probes;
+    dt = 2 x the fine-mesh CFL limit (0.4 x the coarse one).  lossless: sigma
+    = 0 everywhere, including the inclusions."""
+    g = rng_for(6, seed)
+    dx = dy = 1e-3
+    r = 5
+    types = []
+    for a, q in [(6, 60), (12, 180), (20, 400)]:
+        nf = a * r
+        w = int(g.integers(nf // 4, nf // 2))
+        x0, y0 = int(g.integers(0, nf - w)), int(g.integers(0, nf - w))
+        ef, sf = rect_fine(a, a, r, (x0, y0), (x0 + w, y0 + w), g.uniform(2.0, 6.0),
+                           0.0 if lossless else g.uniform(0.0, 0.05))
+        types.append(dict(a=a, b=a, r=r, eps_r=ef, sigma=sf, q=q, f0=10e9))
+    m = n // pitch
+    occ = np.zeros((n, n), dtype=bool)   # regions plus a two-cell margin
+    roms = []
+    for ty in range(m):
+        for tx in range(m):
+            t = types[int(g.integers(0, 3))]
+            a = t["a"]
+            c = pitch // 2 - a // 2
+            i0 = tx * pitch + c + int(g.integers(-(pitch // 4), pitch // 4 + 1))
+            j0 = ty * pitch + c + int(g.integers(-(pitch // 4), pitch // 4 + 1))
+            occ[j0 - 3:j0 + a + 3, i0 - 3:i0 + a + 3] = True
+            roms.append(dict(t, i0=i0, j0=j0))
+    eps = np.ones((n, n))
+    sig = np.zeros((n, n))
+    cov = np.zeros((n, n), dtype=bool)
+    pre = np.zeros((n + 1, n + 1), dtype=np.int64)   # prefix sums of occ
+    pre[1:, 1:] = np.cumsum(np.cumsum(occ, axis=0), axis=1)
+    target = int(fill * n * n)
+    while cov.sum() < target:
+        k = int(min(256, max(4, (target - cov.sum()) // 100)))
+        w = g.integers(4, 17, size=k)
+        h = g.integers(4, 17, size=k)
+        x = g.integers(1, n - 17, size=k)
+        y = g.integers(1, n - 17, size=k)
+        e_in = g.uniform(2.0, 6.0, size=k)
+        s_in = np.zeros(k) if lossless else g.uniform(0.0, 0.05, size=k)
+        hit = pre[y + h, x + w] - pre[y, x + w] - pre[y + h, x] + pre[y, x]
+        for t in np.nonzero(hit == 0)[0]:
+            sl = (slice(y[t], y[t] + h[t]), slice(x[t], x[t] + w[t]))
+            eps[sl] = e_in[t]
+            sig[sl] = s_in[t]
+            cov[sl] = True
+    dt = 2.0 * fine_cfl(dx, dy, r)
+    blocked = occ.any(axis=0)
+    xs = []
+    while len(xs) < n_line:
+        x = int(g.integers(8, n - 8))
+        if not blocked[x - 2:x + 3].any() and all(abs(x - u) > 8 for u in xs):
+            xs.append(x)
+    wave = diff_gaussian(nsteps, dt, 10e9)
+    sources = [dict(comp=1, i=x, j=0, len=n, wave=wave) for x in xs]
+    probes = []
+    while len(probes) < n_probes:
+        i, j = int(g.integers(1, n - 1)), int(g.integers(1, n - 1))
+        if not occ[j, i]:
+            probes.append((i, j))
+    return dict(name=f"lattice_{n}", nx=n, ny=n, dx=dx, dy=dy, dt=dt, eps_r=eps, sigma=sig,
+                roms=roms, sources=sources, probes=probes, nsteps=nsteps, types=types)
+
+
 def batched_256(nsteps: int = 5000, per_size: int = 64, sizes=(128, 256, 512, 1024), seed=None):
     """Batch of independent simulations of uneven sizes sharing four reduced
     models (r = 3; regions of 8, 12, 16 and 24 coarse cells, orders 40, 80,
