@@ -141,3 +141,15 @@ def energy(grid: CoarseGrid, st: State, roms) -> float:
     for e in roms:
         W += 0.5 * grid.dt * float(e.x @ (e.rom.R(grid.dt) @ e.x))
     return W
+
+
+def fine_fields(e: Embedded, nxf: int, nyf: int):
+    """Fine-region fields rebuilt from a model's state (Sec. III: the
+    projection x_hat ~ V x~ with V = blkdiag(V1, V2)): Ex [nyf+1][nxf],
+    Ey [nyf][nxf+1], Hz [nyf][nxf], the fine state order (all Ex, all Ey, Hz,
+    each row-major).  Same time levels as the coarse fields: E^n, Hz^{n-1/2}."""
+    r = e.rom
+    xE = r.V1 @ e.x[:r.qE]
+    xH = r.V2 @ e.x[r.qE:]
+    nEx = nxf * (nyf + 1)
+    return (xE[:nEx].reshape(nyf + 1, nxf), xE[nEx:].reshape(nyf, nxf + 1), xH.reshape(nyf, nxf))

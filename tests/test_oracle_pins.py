@@ -429,3 +429,52 @@ def test_pins_catch_wrong_port_order(monkeypatch):
     monkeypatch.setattr(fine, "interpolation_T", bad)
     with pytest.raises(AssertionError):
         test_r1_full_order_is_plain_yee(couple.PAPER)
+
+
+# --------------------------------------------------------------------------- field reconstruction
+@pytest.mark.parametrize("rule", [couple.PAPER, couple.DUAL])
+def test_r1_reconstructed_fields_are_plain_yee_fields(rule):
+    """r = 1, V = I: the fields rebuilt from the model state are the plain
+    Yee scheme's Hz in the covered cells and its E on the region's inner
+    edges (pins the state layout of the reconstruction)."""
+    w = small_problem(r=1, lossy=True)
+    rd = w["roms"][0]
+    i0, j0, a, b = rd["i0"], rd["j0"], rd["a"], rd["b"]
+    grid, emb, built = problem.build(w, rule=rule, order=0)
+    eps = w["eps_r"].copy()
+    sig = w["sigma"].copy()
+    eps[j0:j0 + b, i0:i0 + a] = rd["eps_r"]
+    sig[j0:j0 + b, i0:i0 + a] = rd["sigma"]
+    plain = yee.CoarseGrid(w["nx"], w["ny"], w["dx"], w["dy"], w["dt"], eps, sig)
+    src = [dict(comp=1, i=2, j=3, len=2, wave=np.sin(np.arange(90) * 0.3))]
+    _, st1, _ = scheme.run(grid, emb, 90, src, [])
+    _, st2, _ = scheme.run(plain, [], 90, src, [])
+    Exf, Eyf, Hzf = scheme.fine_fields(emb[0], a, b)
+    scale = np.abs(st2.Hz).max()
+    assert np.abs(Hzf - st2.Hz[j0:j0 + b, i0:i0 + a]).max() < 1e-10 * scale
+    escale = np.abs(st2.Ex).max()
+    assert np.abs(Exf[1:-1, :] - st2.Ex[j0 + 1:j0 + b, i0:i0 + a]).max() < 1e-10 * escale
+    assert np.abs(Eyf[:, 1:-1] - st2.Ey[j0:j0 + b, i0 + 1:i0 + a]).max() < 1e-10 * escale
+    # the region's boundary edges are the interface values y
+    assert np.abs(Exf[0, :] - st2.Ex[j0, i0:i0 + a]).max() < 1e-10 * escale
+
+
+def test_reconstruction_error_shrinks_with_order():
+    """Information, not a bound from the paper: the rebuilt fine Hz of
+    reduced models approaches the direct subgridding field as q grows."""
+    w = small_problem(lossy=False)
+    rd = w["roms"][0]
+    a, b, r = rd["a"], rd["b"], rd["r"]
+    src = [dict(comp=1, i=2, j=3, len=1, wave=np.sin(np.arange(200) * 0.05) * np.exp(-((np.arange(200) - 60) / 25.0) ** 2))]
+    grid, emb, built = problem.build(w, rule=couple.DUAL, order=0)
+    reg = subgrid.FineRegion(grid, 0, built[0].fs, built[0].T, r, couple.DUAL)
+    subgrid.run(grid, [reg], 200, src, [])
+    ref = reg.H.reshape(r * b, r * a)
+    errs = []
+    for q in (42, 84, 0):
+        grid, emb, built = problem.build(w, rule=couple.DUAL, order=q)
+        scheme.run(grid, emb, 200, src, [])
+        Hzf = scheme.fine_fields(emb[0], r * a, r * b)[2]
+        errs.append(np.linalg.norm(Hzf - ref) / np.linalg.norm(ref))
+    assert errs[2] < 1e-9
+    assert errs[1] < 0.1 * errs[0]
