@@ -14,7 +14,7 @@ from __future__ import annotations
 import dataclasses
 import numpy as np
 
-from . import fine, sprim, passivity, couple, scheme
+from . import cpml, fine, sprim, passivity, couple, scheme
 from .yee import CoarseGrid, cfl_limit
 
 
@@ -53,8 +53,13 @@ def build_rom(rd, grid: CoarseGrid, k: int, rule=couple.DUAL, gamma=0.99, tol=1e
 
 def make_grid(w) -> CoarseGrid:
     regions = [(rd["i0"], rd["j0"], rd["a"], rd["b"]) for rd in w["roms"]]
-    return CoarseGrid(w["nx"], w["ny"], w["dx"], w["dy"], w["dt"], w["eps_r"], w["sigma"],
+    grid = CoarseGrid(w["nx"], w["ny"], w["dx"], w["dy"], w["dt"], w["eps_r"], w["sigma"],
                       regions)
+    if w.get("pml"):
+        p = w["pml"]
+        grid.pml = cpml.CPML(grid, p["n"], p["sides"], p.get("m", 3.0), p.get("sigma_max"),
+                             p.get("kappa_max", 1.0), p.get("alpha_max", 0.0))
+    return grid
 
 
 def build(w, rule=couple.DUAL, gamma=0.99, order=None):

@@ -77,14 +77,16 @@ def source_edges(src):
 
 def step(grid: CoarseGrid, st: State, roms, sources=(), n: int = 0, probes=None,
          out=None):
-    """One step n -> n+1 of the scheme (module header)."""
-    st.Hz = grid.h_update(st.Ex, st.Ey, st.Hz)
+    """One step n -> n+1 of the scheme (module header).  A grid carrying a
+    CPML (attribute ``pml``, oracle.cpml) takes its stretched updates."""
+    pml = getattr(grid, "pml", None)
+    st.Hz = pml.h_update(grid, st.Ex, st.Ey, st.Hz) if pml else grid.h_update(st.Ex, st.Ey, st.Hz)
     if probes is not None and len(probes):
         pi = np.array([p[0] for p in probes])
         pj = np.array([p[1] for p in probes])
         out[n] = st.Hz[pj, pi]
     y_old = [gather_y(grid, e.itf_index, st) for e in roms]
-    st.Ex, st.Ey = grid.e_update(st.Ex, st.Ey, st.Hz)
+    st.Ex, st.Ey = pml.e_update(grid, st.Ex, st.Ey, st.Hz) if pml else grid.e_update(st.Ex, st.Ey, st.Hz)
     for src in sources:
         for (c, i, j) in source_edges(src):
             grid.add_current(st.Ex, st.Ey, c, i, j, src["wave"][n])
