@@ -351,7 +351,8 @@ def run_lattice(args):
     pbuild.build()
     K, W, T = args.steps, args.warmup, args.tsteps
     total = (W + K) * T
-    w = workloads.lattice_8192(min(total, 20000), lossless=args.lossless)
+    n = args.lattice_n
+    w = workloads.lattice_8192(min(total, 20000), n=n, pitch=n // 8, lossless=args.lossless)
     ctx = pg.FdtdContext(w["dx"], w["dy"], w["dt"], [(w["eps_r"], w["sigma"])])
     t0 = time.perf_counter()
     built = {}
@@ -419,7 +420,7 @@ def run_lattice(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": K, "warmup": W,
         "ms_per_step": el_s / max(nsteps_timed // T, 1) * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"lattice_8192: 8192^2 vacuum grid, {100 * f_nb:.2f}% "
+        "config": {"workload": f"lattice_{n}: {n}^2 vacuum grid, {100 * f_nb:.2f}% "
                                f"{'lossless' if args.lossless else 'lossy'} scatterer cells, 64 ROMs of 3 "
                                "types (r=5, q=60/180/400) at dt=2x fine CFL, 4 full-column Jy line "
                                "sources, 16 Hz probes",
@@ -427,7 +428,7 @@ def run_lattice(args):
                    "rom_q": sorted({m.q for m in built.values()}),
                    "rom_clamped": [m.report.n_clamped for m in built.values()],
                    "rom_build_s": round(rom_seconds, 3),
-                   "l2": "inputs larger than L2: 1.6 GB of fields per time step (L2 129 MB)"},
+                   "l2": f"inputs larger than L2: {24 * n * n / 1e9:.2f} GB of fields per time step (L2 129 MB)"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": None, "peak_kind": kind,
                      "kernel": "yee_step_kernel", "kernel_avg_ms": yee_ms / n_yee,
@@ -464,6 +465,8 @@ def main():
     ap.add_argument("--grid", type=int, default=4096, help="coarse grid size (4096 = the benchmark)")
     ap.add_argument("--workload", default="grid", choices=["grid", "batched", "adjoint", "lattice"])
     ap.add_argument("--lossless", action="store_true", help="lattice: sigma = 0 everywhere")
+    ap.add_argument("--lattice-n", type=int, default=8192,
+                    help="lattice: grid size (8192 = the configuration; 64 models at pitch n/8)")
     ap.add_argument("--energy-every", type=int, default=0,
                     help="lattice: record the storage function every E steps")
     args = ap.parse_args()

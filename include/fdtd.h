@@ -139,6 +139,13 @@ int rom_get_info(const rom_model* model, int* qE, int* qH, int* n_u);
 int rom_get_blocks(const rom_model* model, double* R11, double* R22, double* Kt,
                    double* Sig, double* LE);
 
+/* Projection bases of a model (Sec. III: x_hat ~ V x~, V = blkdiag(V1, V2)),
+ * row-major FP64: V1 is nE x qE over the fine E unknowns, V2 nH x qH over the
+ * fine Hz unknowns, in the fine state order (all Ex [r b + 1][r a], then all
+ * Ey [r b][r a + 1], each row-major; Hz [r b][r a]).  Sizes through nE, nH;
+ * any pointer may be NULL (query the sizes first). */
+int rom_get_basis(const rom_model* model, int* nE, int* nH, double* V1, double* V2);
+
 /* Places a model into simulation `sim` with its lower-left coarse cell at
  * (i0, j0); the region is [i0, i0+a) x [j0, j0+b).  The region must keep
  * one coarse cell from the walls and from every other region.  Precomputes
@@ -219,6 +226,39 @@ int fdtd_grad(fdtd_ctx* ctx, long long nsteps, const fdtd_source* src, int nsrc,
               const fdtd_probe* probes, int nprobe, int ckpt_every, float* dJ_deps,
               float* dJ_dsigma, float* dJ_dsrc, double* J_out);
 
+/* ---------------------------------------------------------- open boundaries */
+
+/* Convolutional PML layers (complex-frequency-shifted CPML of Roden and
+ * Gedney) inside the PEC walls of one simulation; the paper terminates its
+ * open structures with PML layers of a few coarse cells (Sec. VI) without
+ * stating the formulation.  Every spatial difference of Eqs. (3), (5) in a
+ * layer becomes (1/kappa) d + psi with psi^n = b psi^{n-1} + a d^n,
+ * b = exp(-(sigma/kappa + alpha) dt/eps0),
+ * a = sigma (b - 1) / (sigma kappa + kappa^2 alpha); at depth rho in [0, 1]
+ * (0 at the layer's inner face, 1 at the wall) sigma = sigma_max rho^m,
+ * kappa = 1 + (kappa_max - 1) rho^m, alpha = alpha_max (1 - rho), each sampled
+ * where its difference is taken.  Outside the layers the update is unchanged. */
+enum { FDTD_PML_W = 1, FDTD_PML_E = 2, FDTD_PML_S = 4, FDTD_PML_N = 8 };
+typedef struct {
+  int sides;          /* FDTD_PML_* bits (x = 0, x = nx, y = 0, y = ny); 0 = none */
+  int ncells;         /* layer thickness in coarse cells (>= 1 when sides != 0) */
+  double m;           /* grading order, > 0 (3 is usual) */
+  double sigma_max;   /* S/m at the wall; <= 0 selects 0.8 (m + 1) / (eta0 h) */
+  double kappa_max;   /* >= 1 */
+  double alpha_max;   /* S/m, >= 0 */
+} fdtd_pml_desc;
+
+/* Sets (or with sides = 0 removes) the layers of simulation `sim` and
+ * zeroes the auxiliary fields of every simulation's layers.  Layers must
+ * leave at least two interior cells in each direction and keep two coarse
+ * cells from every embedded region (rom_embed checks the same later);
+ * sources may not drive an edge next to a layer cell.  The storage function
+ * (fdtd_energy) does not include the auxiliaries; fdtd_grad rejects a
+ * context with layers.  fdtd_save_state / fdtd_load_state carry the
+ * auxiliaries.  Host data is copied; synchronises the context's stream.
+ * FDTD_EINVAL on a bad descriptor or placement. */
+int fdtd_set_pml(fdtd_ctx* ctx, int sim, const fdtd_pml_desc* pml);
+
 /* -------------------------------------------------------- frequency response */
 
 /* Running DFT monitors of Hz (the paper reports its results as frequency
@@ -240,6 +280,18 @@ int fdtd_dft_set(fdtd_ctx* ctx, const fdtd_probe* mons, int nmon, const double* 
  * (2 nmon nfreq doubles; nothing is written when no monitors are set).
  * Synchronises the context's stream. */
 int fdtd_dft_get(fdtd_ctx* ctx, double* out);
+
+/* Fine-region fields of an embedded instance rebuilt from its state
+ * (x_hat ~ V x~, Sec. III; output only, not part of the time march).
+ * `model` must be the model the instance was embedded with (FDTD_EINVAL
+ * otherwise).  Writes Ex [r b + 1][r a], Ey [r b][r a + 1], Hz [r b][r a]
+ * (FP32, row-major, fine cell (0, 0) at the region's lower-left corner) to
+ * caller-owned DEVICE buffers, on the context's stream, at the time levels of
+ * the coarse fields (E^n, Hz^{n-1/2}).  The first call for a model keeps an
+ * FP32 copy of its bases on the device (4 (nE qE + nH qH) bytes) until
+ * fdtd_destroy. */
+int fdtd_fine_fields(fdtd_ctx* ctx, int inst, const rom_model* model, float* Ex, float* Ey,
+                     float* Hz);
 
 /* ------------------------------------------------------------------ state */
 

@@ -56,6 +56,14 @@ class rom_build_report(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class fdtd_pml_desc(C.Structure):
+    _fields_ = [("sides", C.c_int), ("ncells", C.c_int), ("m", C.c_double), ("sigma_max", C.c_double),
+                ("kappa_max", C.c_double), ("alpha_max", C.c_double)]
+
+
+FDTD_PML_W, FDTD_PML_E, FDTD_PML_S, FDTD_PML_N = 1, 2, 4, 8
+
+
 class fdtd_source(C.Structure):
     _fields_ = [("sim", C.c_int), ("comp", C.c_int), ("i", C.c_int), ("j", C.c_int),
                 ("len", C.c_int), ("wave", _fp)]
@@ -103,6 +111,9 @@ def lib() -> C.CDLL:
         "fdtd_energy_noalloc": (i, [vp, _dp]),
         "fdtd_dft_set": (i, [vp, C.POINTER(fdtd_probe), i, _dp, i, _dp]),
         "fdtd_dft_get": (i, [vp, _dp]),
+        "fdtd_fine_fields": (i, [vp, i, vp, vp, vp, vp]),
+        "fdtd_set_pml": (i, [vp, i, C.POINTER(fdtd_pml_desc)]),
+        "rom_get_basis": (i, [vp, C.POINTER(i), C.POINTER(i), _dp, _dp]),
         "fdtd_set_timing": (i, [vp, i]),
         "fdtd_get_kernel_times": (i, [vp, _dp, C.POINTER(ll), _dp, C.POINTER(ll)]),
         "fdtd_last_error": (C.c_char_p, [vp]),
@@ -164,6 +175,14 @@ class RomModel:
         ptr = lambda a: a.ctypes.data_as(_dp)
         _check(lib().rom_get_blocks(self._h, ptr(R11), ptr(R22), ptr(Kt), ptr(Sig), ptr(LE)))
         return R11, R22, Kt, Sig, LE
+
+    def basis(self):
+        """(V1, V2): the projection bases (``rom_get_basis``), FP64."""
+        nE, nH = C.c_int(), C.c_int()
+        _check(lib().rom_get_basis(self._h, C.byref(nE), C.byref(nH), None, None))
+        V1, V2 = np.zeros((nE.value, self.qE)), np.zeros((nH.value, self.qH))
+        _check(lib().rom_get_basis(self._h, None, None, V1.ctypes.data_as(_dp), V2.ctypes.data_as(_dp)))
+        return V1, V2
 
     def couple(self, ring_eps_r, ring_sigma):
         """Host-only run-time map (P, Q) of Eq. (23) for the given outside
@@ -322,6 +341,25 @@ class FdtdContext:
         """``fdtd_load_state``."""
         buf = C.create_string_buffer(data, len(data))
         self._ck(lib().fdtd_load_state(self._h, buf, len(data)))
+
+    def set_pml(self, sim, sides, ncells, m=3.0, sigma_max=0.0, kappa_max=1.0, alpha_max=0.0):
+        """Convolutional PML layers of simulation `sim` (``fdtd_set_pml``);
+        sides = FDTD_PML_* bits, 0 removes them; sigma_max <= 0 selects the
+        default 0.8 (m + 1) / (eta0 h)."""
+        d = fdtd_pml_desc(sides, ncells, m, sigma_max, kappa_max, alpha_max)
+        self._ck(lib().fdtd_set_pml(self._h, sim, C.byref(d)))
+
+    def fine_fields(self, inst, model):
+        """Fine-region (Ex, Ey, Hz) of instance `inst` rebuilt from its state
+        (``fdtd_fine_fields``), as CUDA float32 tensors."""
+        import torch
+        nxf, nyf = model.r * model.a, model.r * model.b
+        Ex = torch.empty((nyf + 1, nxf), dtype=torch.float32, device="cuda")
+        Ey = torch.empty((nyf, nxf + 1), dtype=torch.float32, device="cuda")
+        Hz = torch.empty((nyf, nxf), dtype=torch.float32, device="cuda")
+        self._ck(lib().fdtd_fine_fields(self._h, inst, model._h, C.c_void_p(Ex.data_ptr()),
+                                        C.c_void_p(Ey.data_ptr()), C.c_void_p(Hz.data_ptr())))
+        return Ex, Ey, Hz
 
     def dft_set(self, monitors, freqs, init=None):
         """Running DFT monitors of Hz (``fdtd_dft_set``): monitors are

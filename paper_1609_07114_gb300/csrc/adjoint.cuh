@@ -283,13 +283,13 @@ __global__ void adj_ring_kernel(double* __restrict__ ge, double* __restrict__ gs
   }
 }
 
+// One block, fixed summation order: J does not depend on scheduling.
 __global__ void sum_sq_kernel(const float* __restrict__ x, size_t n, double* __restrict__ out) {
   __shared__ double red[32];
   double acc = 0.0;
-  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x)
-    acc += (double)x[k] * x[k];
+  for (size_t k = threadIdx.x; k < n; k += blockDim.x) acc += (double)x[k] * x[k];
   acc = block_sum(acc, red);
-  if (threadIdx.x == 0) atomicAdd(out, acc);
+  if (threadIdx.x == 0) *out = acc;
 }
 
 }  // namespace
@@ -321,6 +321,7 @@ int run_grad(fdtd_ctx* ctx, long long nsteps, const fdtd_source* src, int nsrc,
              float* dJ_dsrc, double* J_out) {
   if (nsteps < 1 || C < 1 || nsrc < 0 || nprobe < 0 || (nsrc && !src) || (nprobe && !probes))
     return fail(ctx, FDTD_EINVAL, "fdtd_grad: bad argument");
+  if (!ctx->pml_cells.empty()) return fail(ctx, FDTD_EINVAL, "fdtd_grad: not available with PML layers");
   for (int s = 0; s < nsrc; ++s)
     if (!src[s].wave) return fail(ctx, FDTD_EINVAL, "fdtd_grad: null waveform");
   if (C > nsteps) C = (int)nsteps;
@@ -364,7 +365,7 @@ int run_grad(fdtd_ctx* ctx, long long nsteps, const fdtd_source* src, int nsrc,
   }
   double* Jd = nullptr;
   CK(A.alloc(&Jd, 1));
-  if (nprobe > 0) sum_sq_kernel<<<256, 256, 0, st>>>(probe_d, (size_t)nsteps * nprobe, Jd);
+  if (nprobe > 0) sum_sq_kernel<<<1, 1024, 0, st>>>(probe_d, (size_t)nsteps * nprobe, Jd);
   // --- adjoint state, frames and tables
   std::vector<AdjSimDev> asd(nsim);
   std::vector<double*> g64e(nsim), g64s(nsim);

@@ -106,11 +106,193 @@ __device__ __forceinline__ void load_row(RowIn<V>& r, const float* __restrict__ 
   }
 }
 
+// Values carried from row j-1 to row j by one lane.
+template <int V>
+struct RowCarry {
+  float exc[V];   // Ex(j) (read as the previous row's Ex(j+1))
+  float hzp[V];   // Hz^{n+1/2}(j-1)
+  float2 mp[V];   // mat(j-1)
+  float exLc;     // lane 0: Ex(c0 - 1, j)
+};
+
+// Constants of the sparse-material path: edge coefficients between two
+// background cells (the same operations as edge_coef on any other pair).
+struct BgCoef {
+  float ca, cy, cx;   // ca, cb / dy, cb / dx
+};
+
+// One row of the fused step for one lane (module header): Eq. (5) for Hz of
+// row j, then Eq. (3) for Ex and Ey of row j, stored if j >= j0.  Every
+// product and sum is an explicit correctly rounded operation, so the two
+// load paths that share this function give identical bits.
+template <int V>
+__device__ __forceinline__ void stencil_row(const SimDev& sd, const RowIn<V>& cur, RowCarry<V>& cy,
+                                            int j, int j0, int cl, int nx, int lane, bool halo,
+                                            bool dcur, bool dprev, const BgCoef& bc, size_t row,
+                                            float* __restrict__ hzo, float* __restrict__ exo,
+                                            float* __restrict__ eyo) {
+  using VT = Vec<V>;
+  const unsigned FULL = 0xffffffffu;
+  float2 m[V];
+#pragma unroll
+  for (int h = 0; h < V / 2; ++h) {
+    m[2 * h] = make_float2(cur.m4[h].x, cur.m4[h].y);
+    m[2 * h + 1] = make_float2(cur.m4[h].z, cur.m4[h].w);
+  }
+  float eyA[V + 1];
+#pragma unroll
+  for (int t = 0; t < V; ++t) eyA[t] = VT::get(cur.eyv, t);
+  eyA[V] = __shfl_down_sync(FULL, eyA[0], 1);
+  if (lane == 31) eyA[V] = cur.eyR;
+  // Eq. (5): Hz^{n+1/2} = Hz^{n-1/2} + dt/(mu0 dy)(Ex_{j+1} - Ex_j)
+  //                                  - dt/(mu0 dx)(Ey_{i+1} - Ey_i)
+  float hn[V];
+#pragma unroll
+  for (int t = 0; t < V; ++t) {
+    const bool live = (cl + t < nx) && (m[t].x >= 0.f);
+    hn[t] = live ? __fsub_rn(__fmaf_rn(sd.chx, __fsub_rn(VT::get(cur.exn, t), cy.exc[t]), VT::get(cur.hzv, t)),
+                             __fmul_rn(sd.chy, __fsub_rn(eyA[t + 1], eyA[t])))
+                 : 0.f;
+  }
+  // Left neighbour of column cl: lane - 1's last cell, or the halo column.
+  float hnL = __shfl_up_sync(FULL, hn[V - 1], 1);
+  float2 mL;
+  mL.x = __shfl_up_sync(FULL, m[V - 1].x, 1);
+  mL.y = __shfl_up_sync(FULL, m[V - 1].y, 1);
+  if (lane == 0) {
+    mL = cur.mL;
+    hnL = (halo && mL.x >= 0.f)
+              ? __fsub_rn(__fmaf_rn(sd.chx, __fsub_rn(cur.exLn, cy.exLc), cur.hzL),
+                          __fmul_rn(sd.chy, __fsub_rn(eyA[0], cur.eyL)))
+              : 0.f;
+  }
+  if (j >= j0) {
+    float exw[V], eyw[V];
+    // Eq. (3): Ex^{n+1} = ca Ex^n + cb (Hz_j - Hz_{j-1}) / dy on edge (i, j),
+    // between cells (i, j-1) and (i, j).  Rows j-1 and j both background:
+    // the coefficients are the constants (warp-uniform branch).
+    if (dcur || dprev) {
+#pragma unroll
+      for (int t = 0; t < V; ++t) {
+        float v = cy.exc[t];
+        if (j >= 1 && cl + t < nx && cy.mp[t].x >= 0.f && m[t].x >= 0.f) {
+          float ca, cb;
+          edge_coef(cy.mp[t], m[t], ca, cb);
+          v = __fmaf_rn(ca, v, __fmul_rn(__fmul_rn(cb, sd.rdy), __fsub_rn(hn[t], cy.hzp[t])));
+        }
+        exw[t] = v;
+      }
+    } else {
+#pragma unroll
+      for (int t = 0; t < V; ++t) {
+        float v = cy.exc[t];
+        if (j >= 1 && cl + t < nx) v = __fmaf_rn(bc.ca, v, __fmul_rn(bc.cy, __fsub_rn(hn[t], cy.hzp[t])));
+        exw[t] = v;
+      }
+    }
+    // Ey^{n+1} = ca Ey^n - cb (Hz_i - Hz_{i-1}) / dx on edge (i, j),
+    // between cells (i-1, j) and (i, j) (cell c0 - 1 is covered by the
+    // strip's bit).
+    if (dcur) {
+#pragma unroll
+      for (int t = 0; t < V; ++t) {
+        const int i = cl + t;
+        const float2 ml = t == 0 ? mL : m[t - 1];
+        const float hl = t == 0 ? hnL : hn[t - 1];
+        float v = eyA[t];
+        if (i >= 1 && i < nx && ml.x >= 0.f && m[t].x >= 0.f) {
+          float ca, cb;
+          edge_coef(ml, m[t], ca, cb);
+          v = __fmaf_rn(ca, v, -__fmul_rn(__fmul_rn(cb, sd.rdx), __fsub_rn(hn[t], hl)));
+        }
+        eyw[t] = v;
+      }
+    } else {
+#pragma unroll
+      for (int t = 0; t < V; ++t) {
+        const int i = cl + t;
+        const float hl = t == 0 ? hnL : hn[t - 1];
+        float v = eyA[t];
+        if (i >= 1 && i < nx) v = __fmaf_rn(bc.ca, v, -__fmul_rn(bc.cx, __fsub_rn(hn[t], hl)));
+        eyw[t] = v;
+      }
+    }
+    if constexpr (V == 4) {
+      st4(hzo + row + cl, make_float4(hn[0], hn[1], hn[2], hn[3]));
+      st4(exo + row + cl, make_float4(exw[0], exw[1], exw[2], exw[3]));
+      st4(eyo + row + cl, make_float4(eyw[0], eyw[1], eyw[2], eyw[3]));
+    } else {
+      *reinterpret_cast<float2*>(hzo + row + cl) = make_float2(hn[0], hn[1]);
+      *reinterpret_cast<float2*>(exo + row + cl) = make_float2(exw[0], exw[1]);
+      *reinterpret_cast<float2*>(eyo + row + cl) = make_float2(eyw[0], eyw[1]);
+    }
+  }
+#pragma unroll
+  for (int t = 0; t < V; ++t) {
+    cy.exc[t] = VT::get(cur.exn, t);
+    cy.hzp[t] = hn[t];
+    cy.mp[t] = m[t];
+  }
+  cy.exLc = cur.exLn;
+}
+
+// Start-of-strip state shared by both stencil kernels: the carried values
+// of row js = max(j0 - 1, 0), the strip's sparse-material bit words (lane w
+// holds word js/32 + w; tile heights are capped so that 32 words cover a
+// tile) and the background coefficients.
+template <int V>
+__device__ __forceinline__ void stencil_start(const SimDev& sd, const float* __restrict__ ex, int js,
+                                              int cl, int c0, int lane, bool halo, RowCarry<V>& cy,
+                                              uint32_t& fw, BgCoef& bc) {
+  const int P = sd.pitch;
+#pragma unroll
+  for (int t = 0; t < V; ++t) {
+    cy.exc[t] = ex[(size_t)js * P + cl + t];
+    cy.hzp[t] = 0.f;
+    cy.mp[t] = make_float2(0.f, 0.f);
+  }
+  cy.exLc = halo ? ex[(size_t)js * P + c0 - 1] : 0.f;
+  const int jb = js >> 5;
+  fw = 0xffffffffu;
+  if (jb + lane <= ((sd.ny - 1) >> 5)) fw = sd.mbits[(size_t)(jb + lane) * sd.nstrip + (c0 >> 7)];
+  float ca, cb;
+  edge_coef(sd.mbg, sd.mbg, ca, cb);
+  bc.ca = ca;
+  bc.cy = __fmul_rn(cb, sd.rdy);
+  bc.cx = __fmul_rn(cb, sd.rdx);
+}
+
+// Whether row jj of the strip holds any non-background cell (warp-collective).
+__device__ __forceinline__ bool strip_dense(uint32_t fw, int js, int jj) {
+  return ((__shfl_sync(0xffffffffu, fw, (jj >> 5) - (js >> 5)) >> (jj & 31)) & 1u) != 0u;
+}
+
+// Source currents on the CTA's edges, after its rows are written:
+// E^{n+1} -= cb J(t^{n+1/2}) (block-wide; every thread of the CTA calls it).
+__device__ __forceinline__ void stencil_sources(const RunDev* __restrict__ run, int c,
+                                                const float2* __restrict__ mat, int P,
+                                                float* __restrict__ exo, float* __restrict__ eyo) {
+  const int2 rg = run->src_range[blockIdx.x];
+  if (rg.y > rg.x) {
+    __syncthreads();
+    const long long n = run->base + c;
+    for (int e = rg.x + threadIdx.x; e < rg.y; e += blockDim.x) {
+      const SrcEdge se = run->src_edges[e];
+      const size_t off = (size_t)se.j * P + se.i;
+      const float2 m2 = mat[off];
+      const float2 m1 = se.comp == 0 ? mat[off - P] : mat[off - 1];
+      float ca, cb;
+      edge_coef(m1, m2, ca, cb);
+      float* dst = se.comp == 0 ? exo : eyo;
+      dst[off] = __fsub_rn(dst[off], __fmul_rn(cb, run->waves[se.src][n]));
+    }
+  }
+}
+
 template <int V>
 __global__ void __launch_bounds__(kCtaCols / V, V == 4 ? 4 : 3)
 yee_step_kernel(const SimDev* __restrict__ sims, const TileWork* __restrict__ work,
                 const RunDev* __restrict__ run, int par, int c) {
-  using VT = Vec<V>;
   constexpr int kStrip = 32 * V;
   const TileWork tw = work[blockIdx.x];
   const SimDev sd = sims[tw.sim];
@@ -125,146 +307,71 @@ yee_step_kernel(const SimDev* __restrict__ sims, const TileWork* __restrict__ wo
   float* __restrict__ eyo = par ? sd.ey[0] : sd.ey[1];
   float* __restrict__ hzo = par ? sd.hz[0] : sd.hz[1];
   const float2* __restrict__ mat = sd.mat;
-  const unsigned FULL = 0xffffffffu;
   if (c0 < nx) {
     const int cl = c0 + V * lane;
     const int j0 = tw.y0, j1 = tw.y1;
-    int j = j0 > 0 ? j0 - 1 : 0;
+    const int js = j0 > 0 ? j0 - 1 : 0;
     const bool halo = (lane == 0) && (c0 > 0);
-    float exc[V], hzp[V];
-    float2 mp[V];
-#pragma unroll
-    for (int t = 0; t < V; ++t) {
-      exc[t] = ex[(size_t)j * P + cl + t];
-      hzp[t] = 0.f;
-      mp[t] = make_float2(0.f, 0.f);
-    }
-    float exLc = halo ? ex[(size_t)j * P + c0 - 1] : 0.f;
-    // Sparse-material bits of rows j .. j1-1 of this strip: lane w holds word
-    // jb + w (tile heights are capped so that 32 words cover a tile).
-    const int jb = j >> 5;
-    const float2 bg = sd.mbg;
-    uint32_t fw = 0xffffffffu;
-    if (jb + lane <= ((sd.ny - 1) >> 5)) fw = sd.mbits[(size_t)(jb + lane) * sd.nstrip + (c0 >> 7)];
-    auto dense = [&](int jj) { return ((__shfl_sync(FULL, fw, (jj >> 5) - jb) >> (jj & 31)) & 1u) != 0u; };
+    RowCarry<V> cy;
+    uint32_t fw;
+    BgCoef bc;
+    stencil_start<V>(sd, ex, js, cl, c0, lane, halo, cy, fw, bc);
+    bool dcur = strip_dense(fw, js, js), dprev = true;   // row j's bit, row j-1's bit
     RowIn<V> cur, nxt;
-    load_row<V>(cur, ex, ey, hz, mat, (size_t)j * P, P, cl, c0, nx, lane, halo, dense(j), bg);
-    for (; j < j1; ++j) {
+    load_row<V>(cur, ex, ey, hz, mat, (size_t)js * P, P, cl, c0, nx, lane, halo, dcur, sd.mbg);
+    for (int j = js; j < j1; ++j) {
       const size_t row = (size_t)j * P;
-      const bool dn = dense(j + 1 < j1 ? j + 1 : j);
-      if (j + 1 < j1) load_row<V>(nxt, ex, ey, hz, mat, row + P, P, cl, c0, nx, lane, halo, dn, bg);
-      float2 m[V];
-#pragma unroll
-      for (int h = 0; h < V / 2; ++h) {
-        m[2 * h] = make_float2(cur.m4[h].x, cur.m4[h].y);
-        m[2 * h + 1] = make_float2(cur.m4[h].z, cur.m4[h].w);
-      }
-      float eyA[V + 1];
-#pragma unroll
-      for (int t = 0; t < V; ++t) eyA[t] = VT::get(cur.eyv, t);
-      eyA[V] = __shfl_down_sync(FULL, eyA[0], 1);
-      if (lane == 31) eyA[V] = cur.eyR;
-      // Eq. (5): Hz^{n+1/2} = Hz^{n-1/2} + dt/(mu0 dy)(Ex_{j+1} - Ex_j)
-      //                                  - dt/(mu0 dx)(Ey_{i+1} - Ey_i)
-      float hn[V];
-#pragma unroll
-      for (int t = 0; t < V; ++t) {
-        const bool live = (cl + t < nx) && (m[t].x >= 0.f);
-        hn[t] = live ? VT::get(cur.hzv, t) + sd.chx * (VT::get(cur.exn, t) - exc[t]) -
-                           sd.chy * (eyA[t + 1] - eyA[t])
-                     : 0.f;
-      }
-      // Left neighbour of column cl: lane - 1's last cell, or the halo column.
-      float hnL = __shfl_up_sync(FULL, hn[V - 1], 1);
-      float2 mL;
-      mL.x = __shfl_up_sync(FULL, m[V - 1].x, 1);
-      mL.y = __shfl_up_sync(FULL, m[V - 1].y, 1);
-      if (lane == 0) {
-        mL = cur.mL;
-        hnL = (halo && mL.x >= 0.f)
-                  ? cur.hzL + sd.chx * (cur.exLn - exLc) - sd.chy * (eyA[0] - cur.eyL)
-                  : 0.f;
-      }
-      if (j >= j0) {
-        float exw[V], eyw[V];
-        // Eq. (3): Ex^{n+1} = ca Ex^n + cb (Hz_j - Hz_{j-1}) / dy on edge (i, j),
-        // between cells (i, j-1) and (i, j).
-#pragma unroll
-        for (int t = 0; t < V; ++t) {
-          float v = exc[t];
-          if (j >= 1 && cl + t < nx && mp[t].x >= 0.f && m[t].x >= 0.f) {
-            float ca, cb;
-            edge_coef(mp[t], m[t], ca, cb);
-            v = ca * v + cb * sd.rdy * (hn[t] - hzp[t]);
-          }
-          exw[t] = v;
-        }
-        // Ey^{n+1} = ca Ey^n - cb (Hz_i - Hz_{i-1}) / dx on edge (i, j),
-        // between cells (i-1, j) and (i, j).
-#pragma unroll
-        for (int t = 0; t < V; ++t) {
-          const int i = cl + t;
-          const float2 ml = t == 0 ? mL : m[t - 1];
-          const float hl = t == 0 ? hnL : hn[t - 1];
-          float v = eyA[t];
-          if (i >= 1 && i < nx && ml.x >= 0.f && m[t].x >= 0.f) {
-            float ca, cb;
-            edge_coef(ml, m[t], ca, cb);
-            v = ca * v - cb * sd.rdx * (hn[t] - hl);
-          }
-          eyw[t] = v;
-        }
-        if constexpr (V == 4) {
-          st4(hzo + row + cl, make_float4(hn[0], hn[1], hn[2], hn[3]));
-          st4(exo + row + cl, make_float4(exw[0], exw[1], exw[2], exw[3]));
-          st4(eyo + row + cl, make_float4(eyw[0], eyw[1], eyw[2], eyw[3]));
-        } else {
-          *reinterpret_cast<float2*>(hzo + row + cl) = make_float2(hn[0], hn[1]);
-          *reinterpret_cast<float2*>(exo + row + cl) = make_float2(exw[0], exw[1]);
-          *reinterpret_cast<float2*>(eyo + row + cl) = make_float2(eyw[0], eyw[1]);
-        }
-      }
-#pragma unroll
-      for (int t = 0; t < V; ++t) {
-        exc[t] = VT::get(cur.exn, t);
-        hzp[t] = hn[t];
-        mp[t] = m[t];
-      }
-      exLc = cur.exLn;
+      const bool dn = strip_dense(fw, js, j + 1 < j1 ? j + 1 : j);
+      if (j + 1 < j1) load_row<V>(nxt, ex, ey, hz, mat, row + P, P, cl, c0, nx, lane, halo, dn, sd.mbg);
+      stencil_row<V>(sd, cur, cy, j, j0, cl, nx, lane, halo, dcur, dprev, bc, row, hzo, exo, eyo);
       cur = nxt;
+      dprev = dcur;
+      dcur = dn;
     }
   }
-  // Source currents on this tile's edges: E^{n+1} -= cb J(t^{n+1/2}).
-  const int2 rg = run->src_range[blockIdx.x];
-  if (rg.y > rg.x) {
-    __syncthreads();
-    const long long n = run->base + c;
-    for (int e = rg.x + threadIdx.x; e < rg.y; e += blockDim.x) {
-      const SrcEdge se = run->src_edges[e];
-      const size_t off = (size_t)se.j * P + se.i;
-      const float2 m2 = mat[off];
-      const float2 m1 = se.comp == 0 ? mat[off - P] : mat[off - 1];
-      float ca, cb;
-      edge_coef(m1, m2, ca, cb);
-      float* dst = se.comp == 0 ? exo : eyo;
-      dst[off] -= cb * run->waves[se.src][n];
-    }
-  }
+  stencil_sources(run, c, mat, P, exo, eyo);
 }
+
+#include "stencil_tma.cuh"
 
 // Eq. (23) for every embedded model, then the probes.  A CTA takes
 // kRomRowsPerCta rows of one model, one row per warp: v = [y; x~; h] is staged
 // in shared memory and each warp forms one dot product with [P | Q] using
 // float4 loads (all of a row's loads are in flight together).
-// GEMM tile of the batched form: rows [r0, r0+32) of [P | Q] times the
-// columns [c0, c0+32) of [S; H] (one column per simulation sharing the map).
-// The next k-slice is loaded into registers while the current one is used.
-__device__ __forceinline__ void rom_gemm_tile(const SimDev* __restrict__ sims,
+// Batched form: the simulations sharing one coupled map step it as one
+// GEMM [S'] = [P | Q] [S; H], one column per simulation.  A CTA takes
+// 8 RPW rows (RPW per warp) and up to 32 columns (one per lane).  Its rows
+// of [P | Q] (row-major, stride ld + 4) and the input panel [S; H] of its
+// columns (ld x 32, stride 33) are staged in shared memory by cp.async with
+// every copy in flight at once; lane l then accumulates its rows . column l
+// in order k = 0, 1, ... (one memory latency per launch).  RPW = 1 gives
+// more, smaller CTAs (a map shared by a few tens of simulations); RPW = 4
+// re-stages the panel less often (large batches).
+__host__ __device__ constexpr size_t gemm_smem_floats(int ld, int rpw) {
+  return (size_t)ld * 33 + (size_t)rpw * kRomRowsPerCta * (ld + 4);
+}
+
+// Asynchronous global -> shared copies (no register round trip, so every
+// copy of a staging loop is in flight at once).
+__device__ __forceinline__ void async_copy16(void* smem, const void* gmem) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"((unsigned)__cvta_generic_to_shared(smem)),
+               "l"(gmem)
+               : "memory");
+}
+__device__ __forceinline__ void async_copy4(void* smem, const void* gmem) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"((unsigned)__cvta_generic_to_shared(smem)),
+               "l"(gmem)
+               : "memory");
+}
+__device__ __forceinline__ void async_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
+template <int RPW>
+__device__ __forceinline__ void rom_gemm_rows(const SimDev* __restrict__ sims,
                                               const RomInstDev* __restrict__ insts,
-                                              const GemmGroupDev& g, const GemmWork& gw,
-                                              const int* __restrict__ ginst, int par) {
-  __shared__ float Ms[32][33];
-  __shared__ float Vs[32][33];
+                                              const GemmGroupDev g, const GemmWork gw,
+                                              const int* __restrict__ ginst, int par, float* smem) {
   __shared__ const float* s_in[32];
   __shared__ float* s_out[32];
   __shared__ const float* s_hz[32];
@@ -272,75 +379,72 @@ __device__ __forceinline__ void rom_gemm_tile(const SimDev* __restrict__ sims,
   __shared__ const int* s_ye[32];
   __shared__ float* s_ex[32];
   __shared__ float* s_ey[32];
-  const int tid = threadIdx.x;
-  if (tid < 32) {
-    const int col = gw.c0 + tid;
-    s_in[tid] = nullptr;
-    if (col < g.B) {
-      const RomInstDev ri = insts[ginst[g.inst_off + col]];
-      const SimDev* sd = sims + ri.sim;
-      s_in[tid] = par ? ri.state[1] : ri.state[0];
-      s_out[tid] = par ? ri.state[0] : ri.state[1];
-      s_hz[tid] = par ? sd->hz[0] : sd->hz[1];
-      s_ex[tid] = par ? sd->ex[0] : sd->ex[1];
-      s_ey[tid] = par ? sd->ey[0] : sd->ey[1];
-      s_hc[tid] = ri.h_cell;
-      s_ye[tid] = ri.y_edge;
-    }
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  constexpr int nwarp = kRomRowsPerCta;
+  const int nc = min(32, g.B - gw.c0);
+  const int ld = g.ld, ms = ld + 4;
+  if (tid < nc) {
+    const RomInstDev ri = insts[ginst[g.inst_off + gw.c0 + tid]];
+    const SimDev* sd = sims + ri.sim;
+    s_in[tid] = par ? ri.state[1] : ri.state[0];
+    s_out[tid] = par ? ri.state[0] : ri.state[1];
+    s_hz[tid] = par ? sd->hz[0] : sd->hz[1];
+    s_ex[tid] = par ? sd->ex[0] : sd->ex[1];
+    s_ey[tid] = par ? sd->ey[0] : sd->ey[1];
+    s_hc[tid] = ri.h_cell;
+    s_ye[tid] = ri.y_edge;
   }
+  float* panel = smem;                          // [k][col], stride 33
+  float* mrow = smem + (size_t)ld * 33;         // [row][k], stride ld + 4
+  const int nr = min(RPW * nwarp, g.n - gw.r0);
+  const int l4 = ld >> 2;
+  for (int e = tid; e < nr * l4; e += blockDim.x) {
+    const int r = e / l4, k4 = e - r * l4;
+    async_copy16(mrow + (size_t)r * ms + 4 * k4, g.M + (size_t)(gw.r0 + r) * ld + 4 * k4);
+  }
+  __syncthreads();   // column pointers
+  for (int col = warp; col < nc; col += nwarp) {
+    const float* __restrict__ sp = s_in[col];
+    const float* __restrict__ hp = s_hz[col];
+    const int* __restrict__ hc = s_hc[col];
+    for (int k = lane; k < g.n; k += 32) async_copy4(panel + k * 33 + col, sp + k);
+#pragma unroll 4
+    for (int k = g.n + lane; k < g.n + g.ny; k += 32) async_copy4(panel + k * 33 + col, hp + hc[k - g.n]);
+    for (int k = g.n + g.ny + lane; k < ld; k += 32) panel[k * 33 + col] = 0.f;
+  }
+  async_wait_all();
   __syncthreads();
-  const int ty = tid >> 4, tx = tid & 15;   // 2 x 2 outputs per thread
-  float acc00 = 0.f, acc01 = 0.f, acc10 = 0.f, acc11 = 0.f;
-  float mreg[4], vreg[4];
-  auto load = [&](int k0) {
+  const int rb = RPW * warp;
+  if (gw.r0 + rb >= g.n || lane >= nc) return;
+  const float* m0 = mrow + (size_t)rb * ms;
+  const float* pc = panel + lane;
+  float acc[RPW];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int e = tid + 256 * u, row = e >> 5, kk = e & 31;
-      const int r = gw.r0 + row, k = k0 + kk;
-      mreg[u] = (r < g.n && k < g.ld) ? g.M[(size_t)r * g.ld + k] : 0.f;
-      const float* sp = s_in[row];   // here `row` indexes the column of V
-      float v = 0.f;
-      if (sp) {
-        if (k < g.n) v = sp[k];
-        else if (k < g.n + g.ny) v = s_hz[row][s_hc[row][k - g.n]];
-      }
-      vreg[u] = v;
-    }
-  };
-  load(0);
-  for (int k0 = 0; k0 < g.ld; k0 += 32) {
+  for (int i = 0; i < RPW; ++i) acc[i] = 0.f;
+#pragma unroll 2
+  for (int k = 0; k < ld; k += 4) {
+    const float p0 = pc[k * 33], p1 = pc[(k + 1) * 33], p2 = pc[(k + 2) * 33], p3 = pc[(k + 3) * 33];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int e = tid + 256 * u, row = e >> 5, kk = e & 31;
-      Ms[kk][row] = mreg[u];
-      Vs[kk][row] = vreg[u];
+    for (int i = 0; i < RPW; ++i) {
+      const float4 w = *reinterpret_cast<const float4*>(m0 + i * ms + k);
+      acc[i] = fmaf(w.x, p0, acc[i]);
+      acc[i] = fmaf(w.y, p1, acc[i]);
+      acc[i] = fmaf(w.z, p2, acc[i]);
+      acc[i] = fmaf(w.w, p3, acc[i]);
     }
-    __syncthreads();
-    if (k0 + 32 < g.ld) load(k0 + 32);
-#pragma unroll 8
-    for (int kk = 0; kk < 32; ++kk) {
-      const float a0 = Ms[kk][2 * ty], a1 = Ms[kk][2 * ty + 1];
-      const float b0 = Vs[kk][2 * tx], b1 = Vs[kk][2 * tx + 1];
-      acc00 = fmaf(a0, b0, acc00);
-      acc01 = fmaf(a0, b1, acc01);
-      acc10 = fmaf(a1, b0, acc10);
-      acc11 = fmaf(a1, b1, acc11);
-    }
-    __syncthreads();
   }
-  const float accs[2][2] = {{acc00, acc01}, {acc10, acc11}};
+  float* __restrict__ so = s_out[lane];
+  const int* __restrict__ ye = s_ye[lane];
+  float* __restrict__ bx = s_ex[lane];
+  float* __restrict__ by = s_ey[lane];
 #pragma unroll
-  for (int i = 0; i < 2; ++i) {
-#pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      const int r = gw.r0 + 2 * ty + i, cc = 2 * tx + j;
-      if (r < g.n && s_in[cc]) {
-        s_out[cc][r] = accs[i][j];
-        if (r < g.ny) {
-          const int code = s_ye[cc][r];
-          float* base = (code >> 30) ? s_ey[cc] : s_ex[cc];
-          base[code & 0x3fffffff] = accs[i][j];
-        }
+  for (int i = 0; i < RPW; ++i) {
+    const int r = gw.r0 + rb + i;
+    if (r < g.n) {
+      so[r] = acc[i];
+      if (r < g.ny) {
+        const int code = ye[r];
+        ((code >> 30) ? by : bx)[code & 0x3fffffff] = acc[i];
       }
     }
   }
@@ -356,7 +460,10 @@ rom_post_kernel(const SimDev* __restrict__ sims, const RomInstDev* __restrict__ 
   if ((int)blockIdx.x >= nwork && (int)blockIdx.x < nwork + ngwork) {
     const GemmWork gw = gwork[blockIdx.x - nwork];
     const GemmGroupDev g = groups[gw.group];
-    rom_gemm_tile(sims, insts, g, gw, ginst, par);
+    if (g.rpw == 4)
+      rom_gemm_rows<4>(sims, insts, g, gw, ginst, par, reinterpret_cast<float*>(smem4));
+    else
+      rom_gemm_rows<1>(sims, insts, g, gw, ginst, par, reinterpret_cast<float*>(smem4));
     return;
   }
   if ((int)blockIdx.x < nwork) {
@@ -452,6 +559,100 @@ rom_post_kernel(const SimDev* __restrict__ sims, const RomInstDev* __restrict__ 
         a.y -= v * sn;
         run->dft_acc[q] = a;
       }
+    }
+  }
+}
+
+// Fine-region fields from a model state, x_hat = blkdiag(V1, V2) x~ (Sec. III):
+// one warp per output row, x~ staged in shared memory.  Rows [0, nE) are the
+// E unknowns (all Ex then all Ey), rows [nE, nE + nH) the Hz unknowns.
+__global__ void __launch_bounds__(256)
+fine_fields_kernel(const float* __restrict__ V1, const float* __restrict__ V2,
+                   const float* __restrict__ xt, int nE, int nH, int qE, int qH, int nEx,
+                   float* __restrict__ Ex, float* __restrict__ Ey, float* __restrict__ Hz) {
+  extern __shared__ float xs[];
+  for (int k = threadIdx.x; k < qE + qH; k += blockDim.x) xs[k] = xt[k];
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  for (int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < nE + nH; row += nw) {
+    const bool e = row < nE;
+    const float* __restrict__ v = e ? V1 + (size_t)row * qE : V2 + (size_t)(row - nE) * qH;
+    const float* x = e ? xs : xs + qE;
+    const int q = e ? qE : qH;
+    float acc = 0.f;
+    for (int k = lane; k < q; k += 32) acc = fmaf(v[k], x[k], acc);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) {
+      if (row < nEx) Ex[row] = acc;
+      else if (e) Ey[row - nEx] = acc;
+      else Hz[row - nE] = acc;
+    }
+  }
+}
+
+// ---- convolutional PML (open boundaries) ----------------------------------
+// Run after the stencil kernel has written every cell and edge: the layer
+// cells' Hz^{n+1/2} is recomputed with stretched differences, then every E
+// edge next to a layer cell (its E^{n+1} used the old Hz there).  Each list
+// entry is {simulation, j * pitch + i}; auxiliaries psi are per entry.
+//   Hz' = Hz + dt/mu0 [ (1/ky) dEx/dy + psi_hy - (1/kx) dEy/dx - psi_hx ],
+//   psi_hx = bx psi_hx + ax dEy/dx,  psi_hy = by psi_hy + ay dEx/dy.
+__global__ void __launch_bounds__(256)
+pml_h_kernel(const SimDev* __restrict__ sims, const PmlSimDev* __restrict__ pml,
+             const int2* __restrict__ cells, int n, float* __restrict__ psi_hx,
+             float* __restrict__ psi_hy, int par) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    const int2 ce = cells[k];
+    const SimDev& sd = sims[ce.x];
+    const PmlSimDev& pm = pml[ce.x];
+    const int P = sd.pitch, off = ce.y, j = off / P, i = off - j * P;
+    const float* ex = par ? sd.ex[1] : sd.ex[0];
+    const float* ey = par ? sd.ey[1] : sd.ey[0];
+    const float* hz = par ? sd.hz[1] : sd.hz[0];
+    float* hzo = par ? sd.hz[0] : sd.hz[1];
+    const float dEx = __fmul_rn(__fsub_rn(ex[off + P], ex[off]), sd.rdy);
+    const float dEy = __fmul_rn(__fsub_rn(ey[off + 1], ey[off]), sd.rdx);
+    const float py = __fmaf_rn(pm.yh[pm.nyh + j], dEx, __fmul_rn(pm.yh[j], psi_hy[k]));
+    const float px = __fmaf_rn(pm.xh[pm.nxh + i], dEy, __fmul_rn(pm.xh[i], psi_hx[k]));
+    psi_hy[k] = py;
+    psi_hx[k] = px;
+    const float d = __fsub_rn(__fadd_rn(__fmul_rn(dEx, pm.yh[2 * pm.nyh + j]), py),
+                              __fadd_rn(__fmul_rn(dEy, pm.xh[2 * pm.nxh + i]), px));
+    hzo[off] = __fmaf_rn(pm.dtmu, d, hz[off]);
+  }
+}
+
+//   Ex' = ca Ex + cb [ (1/ky) dHz/dy + psi_ex ],  psi_ex = by psi_ex + ay dHz/dy,
+//   Ey' = ca Ey - cb [ (1/kx) dHz/dx + psi_ey ],  psi_ey = bx psi_ey + ax dHz/dx.
+// Entries [0, nex) are Ex edges, [nex, nex + ney) Ey edges.
+__global__ void __launch_bounds__(256)
+pml_e_kernel(const SimDev* __restrict__ sims, const PmlSimDev* __restrict__ pml,
+             const int2* __restrict__ edges, int nex, int ney, float* __restrict__ psi_e, int par) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nex + ney; k += gridDim.x * blockDim.x) {
+    const int2 ed = edges[k];
+    const SimDev& sd = sims[ed.x];
+    const PmlSimDev& pm = pml[ed.x];
+    const int P = sd.pitch, off = ed.y, j = off / P, i = off - j * P;
+    const float* hzo = par ? sd.hz[0] : sd.hz[1];
+    float ca, cb;
+    if (k < nex) {
+      const float* ex = par ? sd.ex[1] : sd.ex[0];
+      float* exo = par ? sd.ex[0] : sd.ex[1];
+      const float dH = __fmul_rn(__fsub_rn(hzo[off], hzo[off - P]), sd.rdy);
+      const float ps = __fmaf_rn(pm.ye[pm.nye + j], dH, __fmul_rn(pm.ye[j], psi_e[k]));
+      psi_e[k] = ps;
+      edge_coef(sd.mat[off - P], sd.mat[off], ca, cb);
+      exo[off] = __fmaf_rn(ca, ex[off], __fmul_rn(cb, __fadd_rn(__fmul_rn(dH, pm.ye[2 * pm.nye + j]), ps)));
+    } else {
+      const float* ey = par ? sd.ey[1] : sd.ey[0];
+      float* eyo = par ? sd.ey[0] : sd.ey[1];
+      const float dH = __fmul_rn(__fsub_rn(hzo[off], hzo[off - 1]), sd.rdx);
+      const float ps = __fmaf_rn(pm.xe[pm.nxe + i], dH, __fmul_rn(pm.xe[i], psi_e[k]));
+      psi_e[k] = ps;
+      edge_coef(sd.mat[off - 1], sd.mat[off], ca, cb);
+      eyo[off] = __fmaf_rn(ca, ey[off], -__fmul_rn(cb, __fadd_rn(__fmul_rn(dH, pm.xe[2 * pm.nxe + i]), ps)));
     }
   }
 }
@@ -700,6 +901,8 @@ struct fdtd_ctx {
   std::vector<SimHost> sims;
   std::vector<TileWork> tiles;
   int vec = 4;                     // columns per lane of the stencil kernel (2 or 4)
+  bool stencil_tma = false;        // bulk-copy (TMA) ring form of the stencil (V = 4)
+  unsigned* status_d = nullptr;    // kernels' status word (RunDev::status)
   SimDev* sims_d = nullptr;
   TileWork* tiles_d = nullptr;
   std::vector<Instance> insts;
@@ -720,6 +923,24 @@ struct fdtd_ctx {
   DevBuf<const float*> waves;
   DevBuf<int> probe_sim, probe_cell;
   DevBuf<float> host_waves, host_probes;
+  // convolutional PML (fdtd_set_pml): per simulation its descriptor and
+  // coefficient arrays, and the concatenated cell / edge lists of all
+  // simulations with their auxiliaries
+  std::vector<fdtd_pml_desc> pml_desc;          // ncells = 0: none
+  std::vector<std::vector<float>> pml_coef;     // per sim: xh | yh | xe | ye
+  std::vector<int2> pml_cells, pml_edges;       // edges: all Ex entries, then all Ey
+  int pml_nex = 0;
+  DevBuf<float> pml_coef_d;
+  DevBuf<PmlSimDev> pml_sims_d;
+  DevBuf<int2> pml_cells_d, pml_edges_d;
+  DevBuf<float> pml_psi;                        // hx | hy (per cell), e (per edge)
+  // device FP32 copies of model bases (fdtd_fine_fields), per model id
+  struct Basis {
+    long long id;
+    float* V1;
+    float* V2;
+  };
+  std::vector<Basis> bases;
   // running DFT monitors (fdtd_dft_set)
   int dft_nmon = 0, dft_nfreq = 0;
   DevBuf<int> dft_sim, dft_cell;
@@ -766,6 +987,18 @@ int fail(fdtd_ctx* ctx, int code, const std::string& msg) {
       return fail(ctx, FDTD_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
   } while (0)
 
+// After a synchronisation: FDTD_ETIMEOUT (and the word cleared) if a
+// kernel's bounded wait gave up since the last check.
+int check_status(fdtd_ctx* ctx) {
+  unsigned st = 0;
+  CK(cudaMemcpy(&st, ctx->status_d, sizeof(unsigned), cudaMemcpyDeviceToHost));
+  if (st) {
+    CK(cudaMemset(ctx->status_d, 0, sizeof(unsigned)));
+    return fail(ctx, FDTD_ETIMEOUT, "a kernel's bounded wait for its staged rows gave up; results are invalid");
+  }
+  return FDTD_OK;
+}
+
 void drop_graphs(fdtd_ctx* ctx) {
   for (int p = 0; p < 2; ++p) {
     if (ctx->graph[p]) cudaGraphExecDestroy(ctx->graph[p]);
@@ -790,6 +1023,7 @@ int plan_tb(fdtd_ctx* ctx) {
   ctx->tb_zones.clear();
   const char* e = getenv("FDTD_TB");
   if (!e || atoi(e) != 1) return FDTD_OK;
+  if (!ctx->pml_cells.empty()) return FDTD_OK;   // the layers' corrections need the one-step form
   const int M = kTbZoneMargin;
   std::vector<int4> zone(ctx->insts.size());
   for (size_t k = 0; k < ctx->insts.size(); ++k) {
@@ -845,13 +1079,16 @@ int plan_tb(fdtd_ctx* ctx) {
 
 // Instances are stepped either one row per warp (rom_post_kernel's first
 // block range) or, when at least FDTD_ROM_GEMM_MIN (default 8) of them share
-// one coupled map, as one GEMM over the shared [P | Q] (second range).
+// one coupled map, as one GEMM over the shared [P | Q] (second range; 8 or
+// 32 rows x up to 32 simulations per CTA, FDTD_GEMM_RPW = 1 or 4).
 int upload_instances(fdtd_ctx* ctx) {
   std::vector<RomInstDev> h(ctx->insts.size());
   std::vector<RomWork> wk;
   size_t smem = 0;
   int gemm_min = 8;
   if (const char* e = getenv("FDTD_ROM_GEMM_MIN")) gemm_min = std::max(1, atoi(e));
+  int gemm_rpw = 1;   // rows per warp of the GEMM form (1 or 4)
+  if (const char* e = getenv("FDTD_GEMM_RPW")) gemm_rpw = atoi(e) == 4 ? 4 : 1;
   std::vector<const CoupledMap*> maps;
   std::vector<std::vector<int>> members;
   for (size_t k = 0; k < ctx->insts.size(); ++k) {
@@ -867,12 +1104,15 @@ int upload_instances(fdtd_ctx* ctx) {
   std::vector<char> in_gemm(ctx->insts.size(), 0);
   for (size_t g = 0; g < maps.size(); ++g) {
     if ((int)members[g].size() < gemm_min) continue;
+    // the GEMM's shared-memory panel must fit one CTA; else row per warp
+    if (sizeof(float) * gemm_smem_floats(maps[g]->ld, gemm_rpw) > 200 * 1024) continue;
     const Instance& in0 = ctx->insts[members[g][0]];
-    GemmGroupDev gd{maps[g]->M_d, in0.n, in0.ny, maps[g]->ld, (int)members[g].size(), (int)ginst.size(), 0, 0, 0};
+    GemmGroupDev gd{maps[g]->M_d, in0.n, in0.ny, maps[g]->ld, (int)members[g].size(), (int)ginst.size(), gemm_rpw, 0, 0};
     for (int k : members[g]) ginst.push_back(k), in_gemm[k] = 1;
-    for (int r0 = 0; r0 < gd.n; r0 += 32)
+    for (int r0 = 0; r0 < gd.n; r0 += gemm_rpw * kRomRowsPerCta)
       for (int c0 = 0; c0 < gd.B; c0 += 32) gwork.push_back({(int)groups.size(), r0, c0, 0});
     groups.push_back(gd);
+    smem = std::max(smem, sizeof(float) * gemm_smem_floats(gd.ld, gemm_rpw));
   }
   for (size_t k = 0; k < ctx->insts.size(); ++k) {
     const Instance& in = ctx->insts[k];
@@ -934,15 +1174,30 @@ int upload_instances(fdtd_ctx* ctx) {
 
 void launch_yee(fdtd_ctx* ctx, cudaStream_t s, int par, int c) {
   const unsigned nb = (unsigned)ctx->tiles.size();
-  if (ctx->vec == 2)
+  if (ctx->stencil_tma)
+    yee_step_tma_kernel<<<nb, kCtaCols / 4, kTmaSmem, s>>>(ctx->sims_d, ctx->tiles_d, ctx->run_d, par, c);
+  else if (ctx->vec == 2)
     yee_step_kernel<2><<<nb, kCtaCols / 2, 0, s>>>(ctx->sims_d, ctx->tiles_d, ctx->run_d, par, c);
   else
     yee_step_kernel<4><<<nb, kCtaCols / 4, 0, s>>>(ctx->sims_d, ctx->tiles_d, ctx->run_d, par, c);
 }
 
+// PML corrections of one step (after the stencil, before the model maps).
+void launch_pml(fdtd_ctx* ctx, cudaStream_t s, int par) {
+  const int nc = (int)ctx->pml_cells.size(), ne = (int)ctx->pml_edges.size();
+  if (nc == 0) return;
+  float* psi = ctx->pml_psi.p;
+  pml_h_kernel<<<std::min(1024, (nc + 255) / 256), 256, 0, s>>>(ctx->sims_d, ctx->pml_sims_d.p,
+                                                                ctx->pml_cells_d.p, nc, psi, psi + nc, par);
+  if (ne > 0)
+    pml_e_kernel<<<std::min(1024, (ne + 255) / 256), 256, 0, s>>>(
+        ctx->sims_d, ctx->pml_sims_d.p, ctx->pml_edges_d.p, ctx->pml_nex, ne - ctx->pml_nex, psi + 2 * nc, par);
+}
+
 // Launches one step (chunk index c) on stream s.
 void launch_step(fdtd_ctx* ctx, cudaStream_t s, int par, int c, int nprobe_blocks) {
   launch_yee(ctx, s, par, c);
+  launch_pml(ctx, s, par);
   const int nb = ctx->nromwork + ctx->ngwork + nprobe_blocks;
   if (nb > 0)
     rom_post_kernel<<<nb, kRomRowsPerCta * 32, ctx->post_smem, s>>>(
@@ -964,6 +1219,24 @@ int ensure_graph(fdtd_ctx* ctx, int par, int nprobe_blocks) {
   if (e != cudaSuccess) return fail(ctx, FDTD_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
   ctx->graph_nprobe_blocks[par] = nprobe_blocks;
   return FDTD_OK;
+}
+
+// Whether cell (i, j) of simulation sim lies in one of its PML layers.
+bool pml_cell(const fdtd_ctx* ctx, int sim, int i, int j) {
+  if (sim >= (int)ctx->pml_desc.size()) return false;
+  const fdtd_pml_desc& d = ctx->pml_desc[sim];
+  if (d.sides == 0 || d.ncells == 0) return false;
+  const SimHost& sh = ctx->sims[sim];
+  const int n = d.ncells;
+  return ((d.sides & FDTD_PML_W) && i < n) || ((d.sides & FDTD_PML_E) && i >= sh.nx - n) ||
+         ((d.sides & FDTD_PML_S) && j < n) || ((d.sides & FDTD_PML_N) && j >= sh.ny - n);
+}
+
+// Whether an E edge is recomputed by the PML kernels (a cell beside it is a
+// layer cell).
+bool pml_edge(const fdtd_ctx* ctx, int sim, int comp, int i, int j) {
+  if (comp == 0) return pml_cell(ctx, sim, i, j - 1) || pml_cell(ctx, sim, i, j);
+  return pml_cell(ctx, sim, i - 1, j) || pml_cell(ctx, sim, i, j);
 }
 
 bool edge_updated(const SimHost& s, int comp, int i, int j) {
@@ -994,6 +1267,8 @@ int prepare_run(fdtd_ctx* ctx, long long nsteps, const fdtd_source* src, int nsr
       if (!edge_updated(sh, so.comp, i, j))
         return fail(ctx, FDTD_EINVAL, "fdtd_run: source " + std::to_string(s) +
                                           " drives a PEC, interface or covered edge");
+      if (pml_edge(ctx, so.sim, so.comp, i, j))
+        return fail(ctx, FDTD_EINVAL, "fdtd_run: source " + std::to_string(s) + " drives an edge next to a PML cell");
       const int tile = sh.tile_base + (j / sh.th) * sh.ncx + i / kCtaCols;
       for (const SrcEdge& o : per[tile])
         if (o.sim == so.sim && o.comp == so.comp && o.i == i && o.j == j)
@@ -1110,6 +1385,7 @@ int prepare_run(fdtd_ctx* ctx, long long nsteps, const fdtd_source* src, int nsr
   rd.dft_cell = ctx->dft_cell.p;
   rd.dft_acc = ctx->dft_acc.p;
   rd.nfreq = ctx->dft_nfreq;
+  rd.status = ctx->status_d;
   // Pageable host sources: cudaMemcpyAsync returns once the data are staged,
   // so the host vectors may go out of scope; the copies stay stream-ordered.
   CK(cudaMemcpyAsync(ctx->run_d, &rd, sizeof(RunDev), cudaMemcpyHostToDevice, st));
@@ -1171,6 +1447,7 @@ int march_timed(fdtd_ctx* ctx, long long nsteps, int nprobe) {
     CK(cudaEventRecord(e[0], ctx->stream));
     // the step index for sources/probes is base + c with base = 0 here
     launch_yee(ctx, ctx->stream, par, 0);
+    launch_pml(ctx, ctx->stream, par);
     CK(cudaEventRecord(e[1], ctx->stream));
     if (post)
       rom_post_kernel<<<ctx->nromwork + ctx->ngwork + nprobe_blocks, kRomRowsPerCta * 32, ctx->post_smem,
@@ -1268,10 +1545,14 @@ void plan_tiles(fdtd_ctx* ctx) {
   int vec = 4;
   if (const char* e = getenv("FDTD_VEC")) vec = (atoi(e) == 2) ? 2 : 4;
   ctx->vec = vec;
+  ctx->stencil_tma = false;
+  if (const char* e = getenv("FDTD_STENCIL")) ctx->stencil_tma = (vec == 4) && std::string(e) == "tma";
   int dev = 0, nsm = 1, occ = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  if (vec == 2)
+  if (ctx->stencil_tma)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, yee_step_tma_kernel, kCtaCols / 4, kTmaSmem);
+  else if (vec == 2)
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, yee_step_kernel<2>, kCtaCols / 2, 0);
   else
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, yee_step_kernel<4>, kCtaCols / 4, 0);
@@ -1381,6 +1662,7 @@ void fdtd_destroy(fdtd_ctx* ctx) {
   ctx->tb_src.release();
   ctx->tb_prb.release();
   cudaFree(ctx->run_d);
+  cudaFree(ctx->status_d);
   cudaFree(ctx->einst_d);
   cudaFree(ctx->tile_base_d);
   ctx->energy_scratch.release();
@@ -1391,6 +1673,19 @@ void fdtd_destroy(fdtd_ctx* ctx) {
   ctx->probe_cell.release();
   ctx->host_waves.release();
   ctx->host_probes.release();
+  ctx->pml_coef_d.release();
+  ctx->pml_sims_d.release();
+  ctx->pml_cells_d.release();
+  ctx->pml_edges_d.release();
+  ctx->pml_psi.release();
+  ctx->dft_sim.release();
+  ctx->dft_cell.release();
+  ctx->dft_fdt.release();
+  ctx->dft_acc.release();
+  for (auto& b : ctx->bases) {
+    cudaFree(b.V1);
+    cudaFree(b.V2);
+  }
   for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
   if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
   delete ctx;
@@ -1484,7 +1779,9 @@ int fdtd_create(const fdtd_grid_desc* g, void* cuda_stream, fdtd_ctx** out) {
   if (plan_tb(ctx) != FDTD_OK) return bail(FDTD_ECUDA);
   if (cudaMalloc(&ctx->sims_d, sizeof(SimDev) * sdev.size()) != cudaSuccess ||
       cudaMalloc(&ctx->tiles_d, sizeof(TileWork) * ctx->tiles.size()) != cudaSuccess ||
-      cudaMalloc(&ctx->run_d, sizeof(RunDev)) != cudaSuccess) {
+      cudaMalloc(&ctx->run_d, sizeof(RunDev)) != cudaSuccess ||
+      cudaMalloc(&ctx->status_d, sizeof(unsigned)) != cudaSuccess ||
+      cudaMemset(ctx->status_d, 0, sizeof(unsigned)) != cudaSuccess) {
     ctx->err = "fdtd_create: device allocation failed";
     return bail(FDTD_ENOMEM);
   }
@@ -1524,6 +1821,10 @@ int rom_embed(fdtd_ctx* ctx, const rom_model* m, int sim, int i0, int j0, int* i
     for (int i = i0 - 1; i <= i0 + a; ++i)
       if (sh.region[(size_t)j * sh.nx + i])
         return fail(ctx, FDTD_EINVAL, "rom_embed: region overlaps or touches another region");
+  for (int j = j0 - 2; j < j0 + b + 2; ++j)
+    for (int i = i0 - 2; i < i0 + a + 2; ++i)
+      if (pml_cell(ctx, sim, i, j))
+        return fail(ctx, FDTD_EINVAL, "rom_embed: region within two cells of a PML layer");
   Instance in;
   in.sim = sim, in.i0 = i0, in.j0 = j0, in.a = a, in.b = b, in.q = m->qE + m->qH;
   in.itf = make_interface(i0, j0, a, b, ctx->dx, ctx->dy, ctx->dt, sh.eps_r.data(), sh.sigma.data(), sh.nx);
@@ -1657,6 +1958,8 @@ int fdtd_run_host(fdtd_ctx* ctx, long long nsteps, const fdtd_source* src, int n
     CK(cudaMemcpyAsync(probe_out_host, ctx->host_probes.p, sizeof(float) * nsteps * nprobe,
                        cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
+  rc = check_status(ctx);
+  if (rc) return rc;
   for (long long k = 0; k < nsteps * nprobe; ++k)
     if (!std::isfinite(probe_out_host[k]))
       return fail(ctx, FDTD_EUNSTABLE, "fdtd_run_host: non-finite probe sample at step " + std::to_string(k / nprobe));
@@ -1669,6 +1972,8 @@ int fdtd_get_fields(fdtd_ctx* ctx, int sim, float* Ex, float* Ey, float* Hz) {
   const int c = ctx->cur;
   const size_t sp = sizeof(float) * sh.pitch;
   CK(cudaStreamSynchronize(ctx->stream));
+  int rc = check_status(ctx);
+  if (rc) return rc;
   if (Ex) CK(cudaMemcpy2D(Ex, sizeof(float) * sh.nx, sh.ex[c], sp, sizeof(float) * sh.nx, sh.ny + 1, cudaMemcpyDeviceToHost));
   if (Ey) CK(cudaMemcpy2D(Ey, sizeof(float) * (sh.nx + 1), sh.ey[c], sp, sizeof(float) * (sh.nx + 1), sh.ny, cudaMemcpyDeviceToHost));
   if (Hz) CK(cudaMemcpy2D(Hz, sizeof(float) * sh.nx, sh.hz[c], sp, sizeof(float) * sh.nx, sh.ny, cudaMemcpyDeviceToHost));
@@ -1812,11 +2117,15 @@ int fdtd_get_kernel_times(fdtd_ctx* ctx, double* yee_ms, long long* yee_launches
 
 // State buffer: magic, step, cur-independent field copies (Ex, Ey, Hz per
 // simulation, pitched as on the device), every instance's [y; x~].
+static size_t pml_psi_count(const fdtd_ctx* ctx) {
+  return ctx->pml_cells.empty() ? 0 : 2 * ctx->pml_cells.size() + ctx->pml_edges.size();
+}
+
 static size_t state_bytes(const fdtd_ctx* ctx) {
   size_t b = 4 * sizeof(long long);
   for (const SimHost& sh : ctx->sims) b += 3 * sizeof(float) * (size_t)(sh.ny + 1) * sh.pitch;
   for (const Instance& in : ctx->insts) b += sizeof(float) * (size_t)in.n;
-  return b;
+  return b + sizeof(float) * pml_psi_count(ctx);
 }
 
 int fdtd_save_state(fdtd_ctx* ctx, void* buf, size_t* size) {
@@ -1844,6 +2153,7 @@ int fdtd_save_state(fdtd_ctx* ctx, void* buf, size_t* size) {
     CK(cudaMemcpy(p, in.state_d[c], sizeof(float) * in.n, cudaMemcpyDeviceToHost));
     p += sizeof(float) * in.n;
   }
+  if (pml_psi_count(ctx)) CK(cudaMemcpy(p, ctx->pml_psi.p, sizeof(float) * pml_psi_count(ctx), cudaMemcpyDeviceToHost));
   *size = need;
   return FDTD_OK;
 }
@@ -1871,7 +2181,165 @@ int fdtd_load_state(fdtd_ctx* ctx, const void* buf, size_t size) {
     CK(cudaMemcpy(in.state_d[c], p, sizeof(float) * in.n, cudaMemcpyHostToDevice));
     p += sizeof(float) * in.n;
   }
+  if (pml_psi_count(ctx)) CK(cudaMemcpy(ctx->pml_psi.p, p, sizeof(float) * pml_psi_count(ctx), cudaMemcpyHostToDevice));
   ctx->step = hdr[1];
+  return FDTD_OK;
+}
+
+int fdtd_set_pml(fdtd_ctx* ctx, int sim, const fdtd_pml_desc* pd) {
+  if (!ctx || !pd || sim < 0 || sim >= (int)ctx->sims.size())
+    return fail(ctx, FDTD_EINVAL, "fdtd_set_pml: bad argument");
+  const SimHost& sh = ctx->sims[sim];
+  fdtd_pml_desc d = *pd;
+  if (d.sides < 0 || d.sides > 15) return fail(ctx, FDTD_EINVAL, "fdtd_set_pml: bad sides");
+  if (d.sides != 0) {
+    const int n = d.ncells;
+    const int lx = ((d.sides & FDTD_PML_W) ? n : 0) + ((d.sides & FDTD_PML_E) ? n : 0);
+    const int ly = ((d.sides & FDTD_PML_S) ? n : 0) + ((d.sides & FDTD_PML_N) ? n : 0);
+    if (n < 1 || lx > sh.nx - 2 || ly > sh.ny - 2)
+      return fail(ctx, FDTD_EINVAL, "fdtd_set_pml: layers must leave two interior cells");
+    if (!(d.m > 0) || !(d.kappa_max >= 1) || !(d.alpha_max >= 0) || !std::isfinite(d.sigma_max))
+      return fail(ctx, FDTD_EINVAL, "fdtd_set_pml: bad profile");
+  }
+  if ((int)ctx->pml_desc.size() < (int)ctx->sims.size()) {
+    fdtd_pml_desc none{};
+    ctx->pml_desc.resize(ctx->sims.size(), none);
+    ctx->pml_coef.resize(ctx->sims.size());
+  }
+  const fdtd_pml_desc old = ctx->pml_desc[sim];
+  ctx->pml_desc[sim] = d;
+  for (const Instance& in : ctx->insts) {
+    if (in.sim != sim) continue;
+    for (int j = in.j0 - 2; j < in.j0 + in.b + 2; ++j)
+      for (int i = in.i0 - 2; i < in.i0 + in.a + 2; ++i)
+        if (pml_cell(ctx, sim, i, j)) {
+          ctx->pml_desc[sim] = old;
+          return fail(ctx, FDTD_EINVAL, "fdtd_set_pml: a layer comes within two cells of an embedded region");
+        }
+  }
+  // coefficient arrays of this simulation, FP64 then rounded
+  std::vector<float>& cf = ctx->pml_coef[sim];
+  cf.clear();
+  if (d.sides != 0) {
+    const double eta0 = std::sqrt(kMu0 / kEps0), dt = ctx->dt;
+    auto arr = [&](int len, double off, int extent, bool lo, bool hi, double h) {
+      const double smax = d.sigma_max > 0 ? d.sigma_max : 0.8 * (d.m + 1) / (eta0 * h);
+      std::vector<float> b(len), a(len), rk(len);
+      for (int k = 0; k < len; ++k) {
+        const double pos = k + off;
+        double dep = 0;
+        if (lo) dep = std::max(dep, d.ncells - pos);
+        if (hi) dep = std::max(dep, pos - (extent - d.ncells));
+        const double rho = std::min(std::max(dep, 0.0), (double)d.ncells) / d.ncells;
+        double sg = 0, kp = 1, al = 0;
+        if (rho > 0) {
+          sg = smax * std::pow(rho, d.m);
+          kp = 1 + (d.kappa_max - 1) * std::pow(rho, d.m);
+          al = d.alpha_max * (1 - rho);
+        }
+        const double bb = std::exp(-(sg / kp + al) * dt / kEps0);
+        const double den = sg * kp + kp * kp * al;
+        b[k] = (float)bb;
+        a[k] = (float)(sg > 0 ? sg / den * (bb - 1) : 0.0);
+        rk[k] = (float)(1.0 / kp);
+      }
+      cf.insert(cf.end(), b.begin(), b.end());
+      cf.insert(cf.end(), a.begin(), a.end());
+      cf.insert(cf.end(), rk.begin(), rk.end());
+    };
+    const bool W = d.sides & FDTD_PML_W, E = d.sides & FDTD_PML_E, S = d.sides & FDTD_PML_S,
+               N = d.sides & FDTD_PML_N;
+    arr(sh.nx, 0.5, sh.nx, W, E, ctx->dx);       // xh: Hz, Ex columns at (i + 1/2) dx
+    arr(sh.ny, 0.5, sh.ny, S, N, ctx->dy);       // yh: Hz, Ey rows at (j + 1/2) dy
+    arr(sh.nx + 1, 0.0, sh.nx, W, E, ctx->dx);   // xe: Ey columns at i dx
+    arr(sh.ny + 1, 0.0, sh.ny, S, N, ctx->dy);   // ye: Ex rows at j dy
+  }
+  // lists and device tables of every simulation
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->pml_cells.clear();
+  std::vector<int2> exl, eyl;
+  std::vector<PmlSimDev> tab(ctx->sims.size());
+  std::vector<float> coef;
+  std::vector<size_t> coff(ctx->sims.size(), 0);
+  for (int t = 0; t < (int)ctx->sims.size(); ++t) {
+    coff[t] = coef.size();
+    coef.insert(coef.end(), ctx->pml_coef[t].begin(), ctx->pml_coef[t].end());
+    const fdtd_pml_desc& dt_ = ctx->pml_desc[t];
+    if (dt_.sides == 0) continue;
+    const SimHost& st = ctx->sims[t];
+    for (int j = 0; j < st.ny; ++j)
+      for (int i = 0; i < st.nx; ++i)
+        if (pml_cell(ctx, t, i, j)) ctx->pml_cells.push_back(make_int2(t, j * st.pitch + i));
+    for (int j = 1; j < st.ny; ++j)
+      for (int i = 0; i < st.nx; ++i)
+        if (edge_updated(st, 0, i, j) && pml_edge(ctx, t, 0, i, j)) exl.push_back(make_int2(t, j * st.pitch + i));
+    for (int j = 0; j < st.ny; ++j)
+      for (int i = 1; i < st.nx; ++i)
+        if (edge_updated(st, 1, i, j) && pml_edge(ctx, t, 1, i, j)) eyl.push_back(make_int2(t, j * st.pitch + i));
+  }
+  ctx->pml_nex = (int)exl.size();
+  ctx->pml_edges = exl;
+  ctx->pml_edges.insert(ctx->pml_edges.end(), eyl.begin(), eyl.end());
+  const size_t nc = ctx->pml_cells.size(), ne = ctx->pml_edges.size();
+  if (nc > 0) {
+    CK(ctx->pml_coef_d.reserve(coef.size()));
+    CK(cudaMemcpy(ctx->pml_coef_d.p, coef.data(), sizeof(float) * coef.size(), cudaMemcpyHostToDevice));
+    for (int t = 0; t < (int)ctx->sims.size(); ++t) {
+      const SimHost& st = ctx->sims[t];
+      PmlSimDev& pm = tab[t];
+      pm = PmlSimDev{};
+      if (ctx->pml_coef[t].empty()) continue;
+      const float* base = ctx->pml_coef_d.p + coff[t];
+      pm.nxh = st.nx, pm.nyh = st.ny, pm.nxe = st.nx + 1, pm.nye = st.ny + 1;
+      pm.xh = base;
+      pm.yh = pm.xh + 3 * pm.nxh;
+      pm.xe = pm.yh + 3 * pm.nyh;
+      pm.ye = pm.xe + 3 * pm.nxe;
+      pm.dtmu = (float)(ctx->dt / kMu0);
+    }
+    CK(ctx->pml_sims_d.reserve(tab.size()));
+    CK(cudaMemcpy(ctx->pml_sims_d.p, tab.data(), sizeof(PmlSimDev) * tab.size(), cudaMemcpyHostToDevice));
+    CK(ctx->pml_cells_d.reserve(nc));
+    CK(cudaMemcpy(ctx->pml_cells_d.p, ctx->pml_cells.data(), sizeof(int2) * nc, cudaMemcpyHostToDevice));
+    CK(ctx->pml_edges_d.reserve(std::max<size_t>(ne, 1)));
+    if (ne) CK(cudaMemcpy(ctx->pml_edges_d.p, ctx->pml_edges.data(), sizeof(int2) * ne, cudaMemcpyHostToDevice));
+    CK(ctx->pml_psi.reserve(2 * nc + ne));
+    CK(cudaMemset(ctx->pml_psi.p, 0, sizeof(float) * (2 * nc + ne)));
+  }
+  drop_graphs(ctx);
+  return plan_tb(ctx);
+}
+
+int fdtd_fine_fields(fdtd_ctx* ctx, int inst, const rom_model* m, float* Ex, float* Ey, float* Hz) {
+  if (!ctx || !m || !Ex || !Ey || !Hz || inst < 0 || inst >= (int)ctx->insts.size())
+    return fail(ctx, FDTD_EINVAL, "fdtd_fine_fields: bad argument");
+  const Instance& in = ctx->insts[inst];
+  if (in.map->model_id != m->id)
+    return fail(ctx, FDTD_EINVAL, "fdtd_fine_fields: instance was embedded with another model");
+  const int nE = m->V1.r, nH = m->V2.r, qE = m->V1.c, qH = m->V2.c;
+  const int nEx = m->nxf * (m->nyf + 1);
+  fdtd_ctx::Basis* b = nullptr;
+  for (auto& x : ctx->bases)
+    if (x.id == m->id) b = &x;
+  if (!b) {
+    fdtd_ctx::Basis nb{m->id, nullptr, nullptr};
+    std::vector<float> h1(m->V1.a.begin(), m->V1.a.end()), h2(m->V2.a.begin(), m->V2.a.end());
+    CK(cudaMalloc(&nb.V1, sizeof(float) * std::max<size_t>(h1.size(), 1)));
+    if (cudaMalloc(&nb.V2, sizeof(float) * std::max<size_t>(h2.size(), 1)) != cudaSuccess) {
+      cudaFree(nb.V1);
+      return fail(ctx, FDTD_ENOMEM, "fdtd_fine_fields: device allocation failed");
+    }
+    ctx->bases.push_back(nb);
+    b = &ctx->bases.back();
+    CK(cudaMemcpy(b->V1, h1.data(), sizeof(float) * h1.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(b->V2, h2.data(), sizeof(float) * h2.size(), cudaMemcpyHostToDevice));
+  }
+  const float* xt = in.state_d[ctx->cur] + in.ny;   // x~ follows y in [y; x~]
+  const int rows = nE + nH;
+  const unsigned nb = (unsigned)std::min(1024, (rows + 7) / 8);
+  fine_fields_kernel<<<nb, 256, sizeof(float) * std::max(qE + qH, 1), ctx->stream>>>(
+      b->V1, b->V2, xt, nE, nH, qE, qH, nEx, Ex, Ey, Hz);
+  CK(cudaGetLastError());
   return FDTD_OK;
 }
 

@@ -26,6 +26,7 @@ struct rom_model {
   int nxf = 0, nyf = 0, nE = 0, nH = 0, nu = 0;
   int qE = 0, qH = 0;
   la::Mat R11, R22, Kt, Sig, BE, LE;   // BE, LE: qE x nu
+  la::Mat V1, V2;                      // projection bases: nE x qE, nH x qH (Sec. III)
   std::vector<double> S_hat;           // nu, Eq. (25)
   rom_build_report rep{};
 };

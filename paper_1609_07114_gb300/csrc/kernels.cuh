@@ -65,11 +65,13 @@ struct RomInstDev {
 constexpr int kRomRowsPerCta = 8;   // one row per warp
 
 // Simulations that share one coupled map step it as one GEMM:
-// [S'] = [P | Q] [S; H] with one column per simulation (32 x 32 tiles).
+// [S'] = [P | Q] [S; H] with one column per simulation (CTA: 8 rpw rows x
+// 32 columns).
 struct GemmGroupDev {
   const float* M;       // [P | Q | 0], n x ld
   int n, ny, ld, B;     // B instances, listed at ginst[inst_off ...]
-  int inst_off, pad0, pad1, pad2;
+  int inst_off, rpw;    // rpw: rows per warp of the CTA tiles (1 or 4)
+  int pad1, pad2;
 };
 
 struct GemmWork {
@@ -78,6 +80,21 @@ struct GemmWork {
 
 struct RomWork {    // one CTA of rom_post: rows [row0, row1) of one instance
   int inst, row0, row1, pad;
+};
+
+// Convolutional PML of one simulation: per coordinate the coefficients
+// {b, a, 1/kappa} of the stretched differences ([3][len] arrays, at the
+// positions where each difference is taken: x-arrays of Hz/Ex over nx
+// columns, of Ey over nx + 1; y-arrays of Hz/Ey over ny rows, of Ex over
+// ny + 1).
+struct PmlSimDev {
+  const float* xh;
+  const float* yh;
+  const float* xe;
+  const float* ye;
+  int nxh, nyh, nxe, nye;   // array lengths
+  float dtmu;               // dt / mu0
+  int pad;
 };
 
 struct EnergyInstDev {  // storage-function data of one embedded model
@@ -109,6 +126,7 @@ struct RunDev {
   double2* dft_acc;
   int nfreq;
   int pad;
+  unsigned* status;          // device word: bit 0 = a bounded wait in a kernel gave up
 };
 
 }  // namespace fdtdrom

@@ -385,6 +385,8 @@ extern "C" int rom_build(const rom_desc* d, rom_model** out, rom_build_report* r
         m->LE(i, p) = V1(f.port_row[p], i);
         m->BE(i, p) = V1(f.port_row[p], i) * f.S_hat[p];
       }
+    m->V1 = V1;
+    m->V2 = V2;
     // Sec. V-E: singular values of R11^{-1/2} K~ R22^{-1/2} (Eq. (27)).
     const Mat r11m = spd_pow(m->R11, -0.5), r22m = spd_pow(m->R22, -0.5);
     const Mat M = la::matmul(la::matmul(r11m, m->Kt), r22m);
@@ -466,5 +468,14 @@ extern "C" int rom_get_blocks(const rom_model* m, double* R11, double* R22, doub
   put(m->Kt, Kt);
   put(m->Sig, Sig);
   put(m->LE, LE);
+  return FDTD_OK;
+}
+
+extern "C" int rom_get_basis(const rom_model* m, int* nE, int* nH, double* V1, double* V2) {
+  if (!m) return fdtdrom::set_global_error(FDTD_EINVAL, "rom_get_basis: null model");
+  if (nE) *nE = m->V1.r;
+  if (nH) *nH = m->V2.r;
+  if (V1) std::memcpy(V1, m->V1.a.data(), sizeof(double) * m->V1.a.size());
+  if (V2) std::memcpy(V2, m->V2.a.data(), sizeof(double) * m->V2.a.size());
   return FDTD_OK;
 }

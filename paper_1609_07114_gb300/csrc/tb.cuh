@@ -145,7 +145,9 @@ yee_tb2_kernel(const SimDev* __restrict__ sims, const TbTile* __restrict__ tiles
       float hn[4];
 #pragma unroll
       for (int t = 0; t < 4; ++t)
-        hn[t] = mx[t] >= 0.f ? comp(h, t) + sd.chx * (comp(e1, t) - comp(e0, t)) - sd.chy * (yA[t + 1] - yA[t]) : 0.f;
+        hn[t] = mx[t] >= 0.f ? __fsub_rn(__fmaf_rn(sd.chx, __fsub_rn(comp(e1, t), comp(e0, t)), comp(h, t)),
+                                          __fmul_rn(sd.chy, __fsub_rn(yA[t + 1], yA[t])))
+                            : 0.f;
       st4(sHz + s, make_float4(hn[0], hn[1], hn[2], hn[3]));
     }
   };
@@ -171,7 +173,7 @@ yee_tb2_kernel(const SimDev* __restrict__ sims, const TbTile* __restrict__ tiles
         if (md[t].x >= 0.f && m[t].x >= 0.f) {
           float ca, cb;
           edge_coef(md[t], m[t], ca, cb);
-          v = ca * v + cb * sd.rdy * (comp(h, t) - comp(hd, t));
+          v = __fmaf_rn(ca, v, __fmul_rn(__fmul_rn(cb, sd.rdy), __fsub_rn(comp(h, t), comp(hd, t))));
         }
         xo[t] = v;
         const float2 ml = t == 0 ? mL : m[t - 1];
@@ -180,7 +182,7 @@ yee_tb2_kernel(const SimDev* __restrict__ sims, const TbTile* __restrict__ tiles
         if (ml.x >= 0.f && m[t].x >= 0.f) {
           float ca, cb;
           edge_coef(ml, m[t], ca, cb);
-          w = ca * w - cb * sd.rdx * (comp(h, t) - hl);
+          w = __fmaf_rn(ca, w, -__fmul_rn(__fmul_rn(cb, sd.rdx), __fsub_rn(comp(h, t), hl)));
         }
         yo[t] = w;
       }
@@ -195,7 +197,8 @@ yee_tb2_kernel(const SimDev* __restrict__ sims, const TbTile* __restrict__ tiles
       const int s = S(se.i, se.j);
       float ca, cb;
       edge_coef(se.comp == 0 ? sM[s - kTbSW] : sM[s - 1], sM[s], ca, cb);
-      (se.comp == 0 ? sEx : sEy)[s] -= cb * run->waves[se.src][n];
+      float& d = (se.comp == 0 ? sEx : sEy)[s];
+      d = __fsub_rn(d, __fmul_rn(cb, run->waves[se.src][n]));
     }
   };
   auto probes = [&](long long n) {

@@ -141,3 +141,17 @@ def test_bad_descriptors():
     with pytest.raises(pg.FdtdError):
         pg.rom_build(2, 2, 2, 1e-3, 1e-3, 1e-13, np.ones(16), np.zeros(16), 3)   # odd order
     assert abs(pg.fdtd_cfl_limit(1e-3, 2e-3) - yee.cfl_limit(1e-3, 2e-3)) < 1e-25
+
+
+@pytest.mark.parametrize("order", [60, 120])
+def test_projection_bases_span_the_oracle_bases(order):
+    """rom_get_basis: orthonormal V1, V2 spanning the oracle's subspaces
+    (principal angles ~ 0; the model depends only on the spans)."""
+    w = workloads.cavity_60(10)
+    m, b = compare_to_oracle(w, couple.DUAL, order)
+    V1, V2 = m.basis()
+    for Vg, Vo in ((V1, b.rom.V1), (V2, b.rom.V2)):
+        assert Vg.shape == Vo.shape
+        assert np.abs(Vg.T @ Vg - np.eye(Vg.shape[1])).max() < 1e-10
+        cosines = np.linalg.svd(Vg.T @ Vo, compute_uv=False)
+        assert cosines.min() > 1 - 1e-8
