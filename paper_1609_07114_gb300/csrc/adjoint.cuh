@@ -253,6 +253,249 @@ adj_e_kernel(const AdjSimDev* __restrict__ sims, const TileWork* __restrict__ ti
   }
 }
 
+// Fused form of adj_h + adj_e: one pass per reverse step, marching 128-column
+// strips up the tile like the forward kernel (lane l owns 4 columns, float4
+// loads, the next row's loads in flight while the current row is computed).
+// Each E edge's mu = cb g_E and its material terms are formed once and used
+// by both cells beside it; g_H'(j-1) is carried in registers for the Ex
+// update of row j, g_H'(i-1) comes from the neighbouring lane (lane 0
+// recomputes the halo column c0 - 1, the first row of a tile the halo row
+// j0 - 1, neither of which accumulates material gradients).
+struct AdjRowIn {
+  float4 gx1, gy, gh;   // g_Ex(j+1), g_Ey(j), g_H(j) (after the model/probe terms)
+  float4 m1a, m1b;      // mat(j+1)
+  float4 x0, x1;        // Ex frames E^n, E^{n+1} of edge row j+1
+  float4 y0, y1;        // Ey frames of row j
+  float gyR, y0R, y1R;  // lane 31: Ey edge (c0 + 128, j)
+  float2 mR;            // lane 31: mat(c0 + 128, j)
+  float gx1L, gyL, ghL; // lane 0: g_Ex(c0-1, j+1), g_Ey(c0-1, j), g_H(c0-1, j)
+  float2 m1L, mLL;      // lane 0: mat(c0-1, j+1), mat(c0-2, j)
+};
+
+__device__ __forceinline__ void adj_load_row(AdjRowIn& r, const AdjSimDev& sd, const float* __restrict__ gexa,
+                                             const float* __restrict__ geya, const float* __restrict__ gha,
+                                             const float* __restrict__ ex0, const float* __restrict__ ex1,
+                                             const float* __restrict__ ey0, const float* __restrict__ ey1,
+                                             size_t row, int P, int cl, int c0, int lane, bool halo,
+                                             bool right) {
+  r.gx1 = ld4(gexa + row + P + cl);
+  r.gy = ld4(geya + row + cl);
+  r.gh = ld4(gha + row + cl);
+  r.m1a = ld4(reinterpret_cast<const float*>(sd.mat + row + P + cl));
+  r.m1b = ld4(reinterpret_cast<const float*>(sd.mat + row + P + cl + 2));
+  r.x0 = ld4(ex0 + row + P + cl);
+  r.x1 = ld4(ex1 + row + P + cl);
+  r.y0 = ld4(ey0 + row + cl);
+  r.y1 = ld4(ey1 + row + cl);
+  if (right) {
+    r.gyR = geya[row + c0 + 128];
+    r.y0R = ey0[row + c0 + 128];
+    r.y1R = ey1[row + c0 + 128];
+    r.mR = sd.mat[row + c0 + 128];
+  } else {
+    r.gyR = r.y0R = r.y1R = 0.f;
+    r.mR = make_float2(-1.f, 0.f);
+  }
+  if (halo) {
+    r.gx1L = gexa[row + P + c0 - 1];
+    r.gyL = geya[row + c0 - 1];
+    r.ghL = gha[row + c0 - 1];
+    r.m1L = sd.mat[row + P + c0 - 1];
+    r.mLL = sd.mat[row + c0 - 2];
+  } else {
+    r.gx1L = r.gyL = r.ghL = 0.f;
+    r.m1L = r.mLL = make_float2(-1.f, 0.f);
+  }
+}
+
+__global__ void __launch_bounds__(128, 3)
+adj_cell_kernel(const AdjSimDev* __restrict__ sims, const TileWork* __restrict__ tiles, int par, int t) {
+  const unsigned FULL = 0xffffffffu;
+  const TileWork tw = tiles[blockIdx.x];
+  const AdjSimDev sd = sims[tw.sim];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int c0 = tw.x0 + warp * 128;
+  const int nx = sd.nx, ny = sd.ny, P = sd.pitch;
+  if (c0 >= nx) return;
+  const float* __restrict__ gexa = par ? sd.gex[1] : sd.gex[0];
+  const float* __restrict__ geya = par ? sd.gey[1] : sd.gey[0];
+  const float* __restrict__ gha = par ? sd.ghz[1] : sd.ghz[0];
+  float* __restrict__ gexb = par ? sd.gex[0] : sd.gex[1];
+  float* __restrict__ geyb = par ? sd.gey[0] : sd.gey[1];
+  float* __restrict__ ghb = par ? sd.ghz[0] : sd.ghz[1];
+  const float* __restrict__ ex0 = sd.exF + (size_t)t * sd.fstride;
+  const float* __restrict__ ex1 = ex0 + sd.fstride;
+  const float* __restrict__ ey0 = sd.eyF + (size_t)t * sd.fstride;
+  const float* __restrict__ ey1 = ey0 + sd.fstride;
+  const int cl = c0 + 4 * lane;
+  const int j0 = tw.y0, j1 = tw.y1;
+  const int js = j0 > 0 ? j0 - 1 : 0;
+  const bool halo = lane == 0 && c0 > 0;
+  const bool right = lane == 31 && c0 + 128 <= nx - 1;
+  // carried state: mat(j), mu / material terms / ca of the Ex edges of row j
+  // (cells j-1, j), g_Ex(j), g_H'(j-1); lane 0 the same for column c0 - 1
+  float2 mj[4];
+  float mux[4], edx[4], esx[4], cgx[4], ghp[4];   // cgx = ca g_Ex of the Ex edges of row j
+  float2 mjL = make_float2(-1.f, 0.f);
+  float muxL = 0.f;
+  {
+    const size_t row = (size_t)js * P;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      mj[q] = sd.mat[row + cl + q];
+      mux[q] = edx[q] = esx[q] = cgx[q] = ghp[q] = 0.f;
+      if (js >= 1 && cl + q < nx) {
+        const float2 mo = sd.mat[row - P + cl + q];
+        if (mo.x >= 0.f && mj[q].x >= 0.f) {
+          float ca, cb;
+          cb_ca(mo, mj[q], ca, cb);
+          mux[q] = cb * gexa[row + cl + q];
+        }
+      }
+    }
+    if (halo) {
+      mjL = sd.mat[row + c0 - 1];
+      if (js >= 1) {
+        const float2 mo = sd.mat[row - P + c0 - 1];
+        if (mo.x >= 0.f && mjL.x >= 0.f) {
+          float ca, cb;
+          cb_ca(mo, mjL, ca, cb);
+          muxL = cb * gexa[row + c0 - 1];
+        }
+      }
+    }
+  }
+  AdjRowIn cur, nxt;
+  adj_load_row(cur, sd, gexa, geya, gha, ex0, ex1, ey0, ey1, (size_t)js * P, P, cl, c0, lane, halo, right);
+  for (int j = js; j < j1; ++j) {
+    const size_t row = (size_t)j * P;
+    if (j + 1 < j1)
+      adj_load_row(nxt, sd, gexa, geya, gha, ex0, ex1, ey0, ey1, row + P, P, cl, c0, lane, halo, right);
+    const float2 m1[4] = {make_float2(cur.m1a.x, cur.m1a.y), make_float2(cur.m1a.z, cur.m1a.w),
+                          make_float2(cur.m1b.x, cur.m1b.y), make_float2(cur.m1b.z, cur.m1b.w)};
+    // Ex edges of row j+1 (cells j, j+1)
+    float mux1[4], edx1[4], esx1[4], cgx1[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      mux1[q] = edx1[q] = esx1[q] = cgx1[q] = 0.f;
+      if (j + 1 <= ny - 1 && cl + q < nx && mj[q].x >= 0.f && m1[q].x >= 0.f) {
+        float ca, cb;
+        cb_ca(mj[q], m1[q], ca, cb);
+        const float mu = cb * comp(cur.gx1, q);
+        mux1[q] = mu;
+        edx1[q] = mu * (comp(cur.x0, q) - comp(cur.x1, q));
+        esx1[q] = mu * (comp(cur.x0, q) + comp(cur.x1, q));
+        cgx1[q] = ca * comp(cur.gx1, q);
+      }
+    }
+    // Ey edges of row j at i = cl + q (cells i-1, i)
+    float2 mleft = make_float2(__shfl_up_sync(FULL, mj[3].x, 1), __shfl_up_sync(FULL, mj[3].y, 1));
+    if (lane == 0) mleft = mjL;
+    float muy[4], edy[4], esy[4], cay[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int i = cl + q;
+      const float2 ml = q == 0 ? mleft : mj[q - 1];
+      muy[q] = edy[q] = esy[q] = cay[q] = 0.f;
+      if (i >= 1 && i <= nx - 1 && ml.x >= 0.f && mj[q].x >= 0.f) {
+        float ca, cb;
+        cb_ca(ml, mj[q], ca, cb);
+        const float mu = cb * comp(cur.gy, q);
+        muy[q] = mu;
+        edy[q] = mu * (comp(cur.y0, q) - comp(cur.y1, q));
+        esy[q] = mu * (comp(cur.y0, q) + comp(cur.y1, q));
+        cay[q] = ca;
+      }
+    }
+    // the Ey edge right of the lane's last column: the next lane's first
+    float muyR = __shfl_down_sync(FULL, muy[0], 1);
+    float edyR = __shfl_down_sync(FULL, edy[0], 1);
+    float esyR = __shfl_down_sync(FULL, esy[0], 1);
+    if (lane == 31) {
+      muyR = edyR = esyR = 0.f;
+      if (right && mj[3].x >= 0.f && cur.mR.x >= 0.f) {
+        float ca, cb;
+        cb_ca(mj[3], cur.mR, ca, cb);
+        muyR = cb * cur.gyR;
+        edyR = muyR * (cur.y0R - cur.y1R);
+        esyR = muyR * (cur.y0R + cur.y1R);
+      }
+    }
+    // g_H' of the row's cells and their material terms
+    float gn[4];
+    const bool own = j >= j0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const bool live = cl + q < nx && mj[q].x >= 0.f;
+      const float mr = q < 3 ? muy[q + 1] : muyR;
+      gn[q] = live ? comp(cur.gh, q) + sd.rdy * mux[q] - sd.rdy * mux1[q] - sd.rdx * muy[q] + sd.rdx * mr : 0.f;
+      if (own && live) {
+        const float er = q < 3 ? edy[q + 1] : edyR;
+        const float sr = q < 3 ? esy[q + 1] : esyR;
+        const float qe = edx[q] + edx1[q] + edy[q] + er;
+        const float qs = esx[q] + esx1[q] + esy[q] + sr;
+        const size_t off = row + cl + q;
+        sd.geps[off] += 0.5f * sd.inv_dt * qe;
+        sd.gsig[off] -= 0.25f * qs;
+      }
+    }
+    // lane 0: g_H' of the halo column c0 - 1
+    float gnL = 0.f;
+    if (halo) {
+      float muxL1 = 0.f, muyL = 0.f;
+      float ca, cb;
+      if (j + 1 <= ny - 1 && mjL.x >= 0.f && cur.m1L.x >= 0.f) {
+        cb_ca(mjL, cur.m1L, ca, cb);
+        muxL1 = cb * cur.gx1L;
+      }
+      if (c0 - 1 >= 1 && cur.mLL.x >= 0.f && mjL.x >= 0.f) {
+        cb_ca(cur.mLL, mjL, ca, cb);
+        muyL = cb * cur.gyL;
+      }
+      gnL = mjL.x >= 0.f ? cur.ghL + sd.rdy * muxL - sd.rdy * muxL1 - sd.rdx * muyL + sd.rdx * muy[0] : 0.f;
+      muxL = muxL1;
+    }
+    float gL = __shfl_up_sync(FULL, gn[3], 1);
+    if (lane == 0) gL = gnL;
+    if (own) {
+      float vx[4], vy[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int i = cl + q;
+        // Ex(i, j): H(i, j-1) has +chx Ex, H(i, j) has -chx Ex (g_H' = 0 on covered cells)
+        float v = 0.f;
+        if (j >= 1 && i < nx) {
+          v = sd.chx * (ghp[q] - gn[q]);
+          v += cgx[q];   // 0 unless both cells are coarse cells
+        }
+        vx[q] = v;
+        // Ey(i, j): H(i, j) has +chy Ey, H(i-1, j) has -chy Ey
+        float w = 0.f;
+        if (i >= 1 && i < nx) {
+          w = sd.chy * (gn[q] - (q == 0 ? gL : gn[q - 1]));
+          w += cay[q] * comp(cur.gy, q);
+        }
+        vy[q] = w;
+      }
+      st4(gexb + row + cl, make_float4(vx[0], vx[1], vx[2], vx[3]));
+      st4(geyb + row + cl, make_float4(vy[0], vy[1], vy[2], vy[3]));
+      st4(ghb + row + cl, make_float4(gn[0], gn[1], gn[2], gn[3]));
+    }
+    // carry to row j + 1
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      mj[q] = m1[q];
+      mux[q] = mux1[q];
+      edx[q] = edx1[q];
+      esx[q] = esx1[q];
+      cgx[q] = cgx1[q];
+      ghp[q] = gn[q];
+    }
+    if (halo) mjL = cur.m1L;
+    cur = nxt;
+  }
+}
+
 // Moves a segment's FP32 accumulators into the FP64 totals and clears them.
 __global__ void adj_flush_kernel(float* __restrict__ g32, double* __restrict__ g64, size_t n) {
   for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
@@ -501,6 +744,9 @@ int run_grad(fdtd_ctx* ctx, long long nsteps, const fdtd_source* src, int nsrc,
   }
   const unsigned ntiles = (unsigned)ctx->tiles.size();
   const int npre_extra = (nprobe + nedges + 127) / 128;
+  // one fused cell pass per reverse step (FDTD_ADJ_FUSED=0: the two-pass form)
+  const char* fe = getenv("FDTD_ADJ_FUSED");
+  const bool fused = !(fe && atoi(fe) == 0);
   int par = 0;
   for (long long k = S - 1; k >= 0; --k) {
     const int L = (int)std::min<long long>(C, nsteps - k * C);
@@ -530,8 +776,12 @@ int run_grad(fdtd_ctx* ctx, long long nsteps, const fdtd_source* src, int nsrc,
       const int nb = (int)aw.size() + npre_extra;
       if (nb > 0)
         adj_pre_kernel<<<nb, 128, pre_smem, st>>>(asd_d, aid_d, aw_d, (int)aw.size(), ar_d, par, t, n);
-      adj_h_kernel<<<ntiles, 256, 0, st>>>(asd_d, ctx->tiles_d, par, t);
-      adj_e_kernel<<<ntiles, 256, 0, st>>>(asd_d, ctx->tiles_d, par);
+      if (fused) {
+        adj_cell_kernel<<<ntiles, 128, 0, st>>>(asd_d, ctx->tiles_d, par, t);
+      } else {
+        adj_h_kernel<<<ntiles, 256, 0, st>>>(asd_d, ctx->tiles_d, par, t);
+        adj_e_kernel<<<ntiles, 256, 0, st>>>(asd_d, ctx->tiles_d, par);
+      }
       par ^= 1;
     }
     CK(cudaGetLastError());

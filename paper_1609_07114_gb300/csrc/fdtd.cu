@@ -289,8 +289,10 @@ __device__ __forceinline__ void stencil_sources(const RunDev* __restrict__ run, 
   }
 }
 
-template <int V>
-__global__ void __launch_bounds__(kCtaCols / V, V == 4 ? 4 : 3)
+// MB: resident CTAs per SM the register budget is cut for (4: no spills;
+// 5: a few spilled registers for 25% more warps).
+template <int V, int MB = (V == 4 ? 4 : 3)>
+__global__ void __launch_bounds__(kCtaCols / V, MB)
 yee_step_kernel(const SimDev* __restrict__ sims, const TileWork* __restrict__ work,
                 const RunDev* __restrict__ run, int par, int c) {
   constexpr int kStrip = 32 * V;
@@ -902,6 +904,7 @@ struct fdtd_ctx {
   std::vector<TileWork> tiles;
   int vec = 4;                     // columns per lane of the stencil kernel (2 or 4)
   bool stencil_tma = false;        // bulk-copy (TMA) ring form of the stencil (V = 4)
+  bool stencil_occ5 = false;       // register-prefetch form cut for 5 CTAs per SM (V = 4)
   unsigned* status_d = nullptr;    // kernels' status word (RunDev::status)
   SimDev* sims_d = nullptr;
   TileWork* tiles_d = nullptr;
@@ -1087,8 +1090,11 @@ int upload_instances(fdtd_ctx* ctx) {
   size_t smem = 0;
   int gemm_min = 8;
   if (const char* e = getenv("FDTD_ROM_GEMM_MIN")) gemm_min = std::max(1, atoi(e));
-  int gemm_rpw = 1;   // rows per warp of the GEMM form (1 or 4)
-  if (const char* e = getenv("FDTD_GEMM_RPW")) gemm_rpw = atoi(e) == 4 ? 4 : 1;
+  // rows per warp of the GEMM form: 4 when the map is shared by >= 32
+  // simulations (the panel is re-staged less often), else 1 (more CTAs);
+  // FDTD_GEMM_RPW = 1 or 4 overrides (same results, speed only)
+  int rpw_env = 0;
+  if (const char* e = getenv("FDTD_GEMM_RPW")) rpw_env = atoi(e) == 4 ? 4 : 1;
   std::vector<const CoupledMap*> maps;
   std::vector<std::vector<int>> members;
   for (size_t k = 0; k < ctx->insts.size(); ++k) {
@@ -1104,6 +1110,7 @@ int upload_instances(fdtd_ctx* ctx) {
   std::vector<char> in_gemm(ctx->insts.size(), 0);
   for (size_t g = 0; g < maps.size(); ++g) {
     if ((int)members[g].size() < gemm_min) continue;
+    const int gemm_rpw = rpw_env ? rpw_env : ((int)members[g].size() >= 32 ? 4 : 1);
     // the GEMM's shared-memory panel must fit one CTA; else row per warp
     if (sizeof(float) * gemm_smem_floats(maps[g]->ld, gemm_rpw) > 200 * 1024) continue;
     const Instance& in0 = ctx->insts[members[g][0]];
@@ -1176,6 +1183,8 @@ void launch_yee(fdtd_ctx* ctx, cudaStream_t s, int par, int c) {
   const unsigned nb = (unsigned)ctx->tiles.size();
   if (ctx->stencil_tma)
     yee_step_tma_kernel<<<nb, kCtaCols / 4, kTmaSmem, s>>>(ctx->sims_d, ctx->tiles_d, ctx->run_d, par, c);
+  else if (ctx->stencil_occ5)
+    yee_step_kernel<4, 5><<<nb, kCtaCols / 4, 0, s>>>(ctx->sims_d, ctx->tiles_d, ctx->run_d, par, c);
   else if (ctx->vec == 2)
     yee_step_kernel<2><<<nb, kCtaCols / 2, 0, s>>>(ctx->sims_d, ctx->tiles_d, ctx->run_d, par, c);
   else
@@ -1550,8 +1559,12 @@ void plan_tiles(fdtd_ctx* ctx) {
   int dev = 0, nsm = 1, occ = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  ctx->stencil_occ5 = false;
+  if (const char* e = getenv("FDTD_STENCIL")) ctx->stencil_occ5 = (vec == 4) && std::string(e) == "ldg5";
   if (ctx->stencil_tma)
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, yee_step_tma_kernel, kCtaCols / 4, kTmaSmem);
+  else if (ctx->stencil_occ5)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, yee_step_kernel<4, 5>, kCtaCols / 4, 0);
   else if (vec == 2)
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, yee_step_kernel<2>, kCtaCols / 2, 0);
   else
