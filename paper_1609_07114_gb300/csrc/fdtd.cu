@@ -289,10 +289,8 @@ __device__ __forceinline__ void stencil_sources(const RunDev* __restrict__ run, 
   }
 }
 
-// MB: resident CTAs per SM the register budget is cut for (4: no spills;
-// 5: a few spilled registers for 25% more warps).
-template <int V, int MB = (V == 4 ? 4 : 3)>
-__global__ void __launch_bounds__(kCtaCols / V, MB)
+template <int V>
+__global__ void __launch_bounds__(kCtaCols / V, V == 4 ? 4 : 3)
 yee_step_kernel(const SimDev* __restrict__ sims, const TileWork* __restrict__ work,
                 const RunDev* __restrict__ run, int par, int c) {
   constexpr int kStrip = 32 * V;
@@ -904,7 +902,6 @@ struct fdtd_ctx {
   std::vector<TileWork> tiles;
   int vec = 4;                     // columns per lane of the stencil kernel (2 or 4)
   bool stencil_tma = false;        // bulk-copy (TMA) ring form of the stencil (V = 4)
-  bool stencil_occ5 = false;       // register-prefetch form cut for 5 CTAs per SM (V = 4)
   unsigned* status_d = nullptr;    // kernels' status word (RunDev::status)
   SimDev* sims_d = nullptr;
   TileWork* tiles_d = nullptr;
@@ -1183,8 +1180,6 @@ void launch_yee(fdtd_ctx* ctx, cudaStream_t s, int par, int c) {
   const unsigned nb = (unsigned)ctx->tiles.size();
   if (ctx->stencil_tma)
     yee_step_tma_kernel<<<nb, kCtaCols / 4, kTmaSmem, s>>>(ctx->sims_d, ctx->tiles_d, ctx->run_d, par, c);
-  else if (ctx->stencil_occ5)
-    yee_step_kernel<4, 5><<<nb, kCtaCols / 4, 0, s>>>(ctx->sims_d, ctx->tiles_d, ctx->run_d, par, c);
   else if (ctx->vec == 2)
     yee_step_kernel<2><<<nb, kCtaCols / 2, 0, s>>>(ctx->sims_d, ctx->tiles_d, ctx->run_d, par, c);
   else
@@ -1559,12 +1554,8 @@ void plan_tiles(fdtd_ctx* ctx) {
   int dev = 0, nsm = 1, occ = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  ctx->stencil_occ5 = false;
-  if (const char* e = getenv("FDTD_STENCIL")) ctx->stencil_occ5 = (vec == 4) && std::string(e) == "ldg5";
   if (ctx->stencil_tma)
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, yee_step_tma_kernel, kCtaCols / 4, kTmaSmem);
-  else if (ctx->stencil_occ5)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, yee_step_kernel<4, 5>, kCtaCols / 4, 0);
   else if (vec == 2)
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, yee_step_kernel<2>, kCtaCols / 2, 0);
   else
