@@ -281,7 +281,7 @@ def run_adjoint(args):
     import workloads
     pbuild.build()
     N = args.tsteps if args.tsteps != 2000 else 10000
-    w = workloads.adjoint_16(N)
+    w = workloads.adjoint_16(N, nsim=args.adj_nsim)
     models = [pg.rom_build(md["a"], md["b"], md["r"], w["dx"], w["dy"], w["dt"], md["eps_r"],
                            md["sigma"], md["q"], f0=md["f0"]) for md in w["models"]]
 
@@ -326,7 +326,7 @@ def run_adjoint(args):
         "metric": "adjoint/forward time ratio", "value": ta / tf, "unit": "x", "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ta * 1e3, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "adjoint_16: 16 x 1024^2 coarse grids, 2 shared ROMs r=3 q=120 each, "
+        "config": {"workload": f"adjoint_16: {args.adj_nsim} x 1024^2 coarse grids, 2 shared ROMs r=3 q=120 each, "
                                "8 probes per simulation, J = sum Hz^2, checkpoints every 500 steps",
                    "time_steps": N, "cells": cells, "forward_s": tf, "adjoint_s": ta,
                    "forward_gcell_steps_per_s": cells * N / tf / 1e9,
@@ -465,6 +465,8 @@ def main():
     ap.add_argument("--grid", type=int, default=4096, help="coarse grid size (4096 = the benchmark)")
     ap.add_argument("--workload", default="grid", choices=["grid", "batched", "adjoint", "lattice"])
     ap.add_argument("--lossless", action="store_true", help="lattice: sigma = 0 everywhere")
+    ap.add_argument("--adj-nsim", type=int, default=16,
+                    help="adjoint: simulations in the batch (16 = the configuration)")
     ap.add_argument("--lattice-n", type=int, default=8192,
                     help="lattice: grid size (8192 = the configuration; 64 models at pitch n/8)")
     ap.add_argument("--energy-every", type=int, default=0,
