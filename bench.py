@@ -46,6 +46,23 @@ def dist_env():
     return ws, int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0"))
 
 
+def max_over_ranks(el_ms, dist, device):
+    """The slowest rank's time: the job's time (replicas run independently;
+    this timing reduction is the only collective)."""
+    if not dist:
+        return el_ms
+    import torch
+    t = torch.tensor([el_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(cells, tsteps, steps, ranks, el_ms):
+    """Whole-job Gcell-steps/s: every rank advanced `cells` cells by
+    tsteps x steps time steps in at most el_ms."""
+    return cells * tsteps * steps * ranks / (el_ms / 1e3) / 1e9
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -553,13 +570,9 @@ def main():
         torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    el_ms = e0.elapsed_time(e1)
-    if dist:
-        t = torch.tensor([el_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        el_ms = float(t.item())
+    el_ms = max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
     cells = w["nx"] * w["ny"]
-    value = cells * T * K * ws / (el_ms / 1e3) / 1e9
+    value = replica_throughput(cells, T, K, ws, el_ms)
 
     # Per-kernel device time of the dominant (stencil) kernel, CUDA events on
     # the launching stream, over a second pass of the same K steps.
