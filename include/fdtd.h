@@ -139,6 +139,18 @@ int rom_get_info(const rom_model* model, int* qE, int* qH, int* n_u);
 int rom_get_blocks(const rom_model* model, double* R11, double* R22, double* Kt,
                    double* Sig, double* LE);
 
+/* rom_build with the block Krylov basis, its orthonormalisation and the
+ * congruences of Eq. (12) computed on the GPU in FP64 (stream cuda_stream;
+ * the banded factorisation, small eigenproblems and Eq. (27) stay on the
+ * host).  Orthonormalisation goes through Gram matrices in two stages (the
+ * second on what the first leaves), which resolve singular values down to
+ * the same deflation tolerance as rom_build, so both builds give the same
+ * reduced space to rounding.  Same outputs, ownership and errors as
+ * rom_build, plus FDTD_ECUDA on a device failure.  Synchronises the
+ * stream. */
+int rom_build_gpu(const rom_desc* desc, void* cuda_stream, rom_model** model,
+                  rom_build_report* report);
+
 /* Projection bases of a model (Sec. III: x_hat ~ V x~, V = blkdiag(V1, V2)),
  * row-major FP64: V1 is nE x qE over the fine E unknowns, V2 nH x qH over the
  * fine Hz unknowns, in the fine state order (all Ex [r b + 1][r a], then all

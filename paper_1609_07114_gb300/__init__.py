@@ -90,6 +90,7 @@ def lib() -> C.CDLL:
         "fdtd_destroy": (None, [vp]),
         "fdtd_cfl_limit": (i, [d, d, _dp]),
         "rom_build": (i, [C.POINTER(rom_desc), C.POINTER(vp), C.POINTER(rom_build_report)]),
+        "rom_build_gpu": (i, [C.POINTER(rom_desc), vp, C.POINTER(vp), C.POINTER(rom_build_report)]),
         "rom_free": (None, [vp]),
         "rom_get_info": (i, [vp, C.POINTER(i), C.POINTER(i), C.POINTER(i)]),
         "rom_get_blocks": (i, [vp, _dp, _dp, _dp, _dp, _dp]),
@@ -217,6 +218,20 @@ def rom_build(a, b, r, dx, dy, dt, eps_r, sigma, q, rule=FDTD_RULE_DUAL, f0=30e9
     h = C.c_void_p()
     rep = rom_build_report()
     _check(lib().rom_build(C.byref(d), C.byref(h), C.byref(rep)))
+    return RomModel(h, rep, a, b, r)
+
+
+def rom_build_gpu(a, b, r, dx, dy, dt, eps_r, sigma, q, rule=FDTD_RULE_DUAL, f0=30e9,
+                  gamma=0.99, defl_tol=0.0, stream=None) -> RomModel:
+    """``rom_build_gpu``: the same model built with the Krylov basis and the
+    congruences on the GPU (FP64)."""
+    e, s = _f64(eps_r), _f64(sigma)
+    assert e.size == r * a * r * b and s.size == e.size
+    d = rom_desc(a, b, r, dx, dy, dt, e.ctypes.data_as(_dp), s.ctypes.data_as(_dp), q, rule,
+                 f0, gamma, defl_tol)
+    h = C.c_void_p()
+    rep = rom_build_report()
+    _check(lib().rom_build_gpu(C.byref(d), _stream_handle(stream), C.byref(h), C.byref(rep)))
     return RomModel(h, rep, a, b, r)
 
 

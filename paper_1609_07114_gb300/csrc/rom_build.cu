@@ -24,6 +24,7 @@
 #include <cmath>
 #include <cstring>
 #include <new>
+#include <stdexcept>
 
 #include "internal.hpp"
 
@@ -251,9 +252,78 @@ Mat spd_pow(const Mat& A, double p) {
   return la::sym_pow(A, p);
 }
 
+// The part of a build after the congruences (m->R11, Sig, R22, Kt set):
+// port blocks, Eq. (27) and the report.
+rom_build_report finish_model(rom_model* m, const FineSys& f, const rom_desc* d, int n_inputs) {
+  const Mat& V1 = m->V1;
+  m->LE = Mat(m->qE, f.nu);
+  m->BE = Mat(m->qE, f.nu);
+  for (int p = 0; p < f.nu; ++p)
+    for (int i = 0; i < m->qE; ++i) {
+      m->LE(i, p) = V1(f.port_row[p], i);
+      m->BE(i, p) = V1(f.port_row[p], i) * f.S_hat[p];
+    }
+  // Sec. V-E: singular values of R11^{-1/2} K~ R22^{-1/2} (Eq. (27)).
+  const Mat r11m = spd_pow(m->R11, -0.5), r22m = spd_pow(m->R22, -0.5);
+  const Mat M = la::matmul(la::matmul(r11m, m->Kt), r22m);
+  Mat U, Wt;
+  std::vector<double> s;
+  la::svd(M, U, s, Wt);
+  const double lim = 2.0 / d->dt;
+  rom_build_report r{};
+  r.qE = m->qE, r.qH = m->qH, r.n_inputs = n_inputs;
+  r.smax_before = s.empty() ? 0.0 : s[0] / lim;
+  r.smax_after = r.smax_before;
+  if (d->gamma > 0 && !s.empty() && s[0] > d->gamma * lim) {
+    std::vector<double> sc = s;
+    for (auto& v : sc)
+      if (v > d->gamma * lim) v = d->gamma * lim, ++r.n_clamped;
+    Mat US = U;
+    for (int i = 0; i < US.r; ++i)
+      for (int j = 0; j < US.c; ++j) US(i, j) *= sc[j];
+    const Mat Mc = la::matmul_nt(US, Wt);
+    m->Kt = la::matmul(la::matmul(spd_pow(m->R11, 0.5), Mc), spd_pow(m->R22, 0.5));
+    r.smax_after = sc[0] / lim;
+  }
+  // Eq. (26a) at the run dt, Eq. (26c).
+  {
+    const int q = m->qE + m->qH;
+    Mat R(q, q);
+    for (int i = 0; i < m->qE; ++i)
+      for (int j = 0; j < m->qE; ++j) R(i, j) = m->R11(i, j) / d->dt;
+    for (int i = 0; i < m->qH; ++i)
+      for (int j = 0; j < m->qH; ++j) R(m->qE + i, m->qE + j) = m->R22(i, j) / d->dt;
+    for (int i = 0; i < m->qE; ++i)
+      for (int j = 0; j < m->qH; ++j) R(i, m->qE + j) = R(m->qE + j, i) = -0.5 * m->Kt(i, j);
+    if (q <= 1200) {
+      std::vector<double> w;
+      Mat Qe;
+      la::eig_sym(R, w, Qe);
+      r.min_eig_R = w.empty() ? 0.0 : w[0] / std::fabs(w.back());
+    } else {
+      r.min_eig_R = la::chol_ok(R) ? 1.0 : -1.0;  // sign only for very large models
+    }
+    double num = 0.0, den = 0.0;
+    for (int i = 0; i < m->qE; ++i)
+      for (int p = 0; p < f.nu; ++p) {
+        const double dv = m->BE(i, p) - m->LE(i, p) * f.S_hat[p];
+        num += dv * dv;
+        den += m->BE(i, p) * m->BE(i, p);
+      }
+    r.cond3_residual = den > 0 ? std::sqrt(num / den) : 0.0;
+  }
+  return r;
+}
+
+
+#include "rom_build_gpu.cuh"
+
 }  // namespace
 
-extern "C" int rom_build(const rom_desc* d, rom_model** out, rom_build_report* rep) {
+namespace {
+
+// gpu: the Krylov basis and the Eq. (12) blocks on the device (stream st).
+int rom_build_impl(const rom_desc* d, rom_model** out, rom_build_report* rep, bool gpu, cudaStream_t st) {
   using fdtdrom::set_global_error;
   if (!d || !out) return set_global_error(FDTD_EINVAL, "rom_build: null argument");
   if (d->a < 1 || d->b < 1 || d->r < 1 || !(d->dx > 0) || !(d->dy > 0) || !(d->dt > 0) ||
@@ -314,6 +384,15 @@ extern "C" int rom_build(const rom_desc* d, rom_model** out, rom_build_report* r
           else col = 2 * d->a + d->b + (p - 2 * nxf - nyf) / d->r;
         }
         W(f.port_row[p], col) += f.S_hat[p];
+      }
+      if (gpu) {
+        gpu_blocks(f, ps, psi0, dt_b, W, d->q / 2, tol, st, m);
+        rom_build_report r = finish_model(m, f, d, n_inputs);
+        r.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        m->rep = r;
+        if (rep) *rep = r;
+        *out = m;
+        return FDTD_OK;
       }
       auto pencil_inv = [&](const double* x, double* y) {
         std::memcpy(y, x, sizeof(double) * N);
@@ -378,73 +457,31 @@ extern "C" int rom_build(const rom_desc* d, rom_model** out, rom_build_report* r
       }
       m->Kt = la::matmul_tn(V1, KV2);
     }
-    m->LE = Mat(m->qE, f.nu);
-    m->BE = Mat(m->qE, f.nu);
-    for (int p = 0; p < f.nu; ++p)
-      for (int i = 0; i < m->qE; ++i) {
-        m->LE(i, p) = V1(f.port_row[p], i);
-        m->BE(i, p) = V1(f.port_row[p], i) * f.S_hat[p];
-      }
     m->V1 = V1;
     m->V2 = V2;
-    // Sec. V-E: singular values of R11^{-1/2} K~ R22^{-1/2} (Eq. (27)).
-    const Mat r11m = spd_pow(m->R11, -0.5), r22m = spd_pow(m->R22, -0.5);
-    const Mat M = la::matmul(la::matmul(r11m, m->Kt), r22m);
-    Mat U, Wt;
-    std::vector<double> s;
-    la::svd(M, U, s, Wt);
-    const double lim = 2.0 / d->dt;
-    rom_build_report r{};
-    r.qE = m->qE, r.qH = m->qH, r.n_inputs = n_inputs;
-    r.smax_before = s.empty() ? 0.0 : s[0] / lim;
-    r.smax_after = r.smax_before;
-    if (d->gamma > 0 && !s.empty() && s[0] > d->gamma * lim) {
-      std::vector<double> sc = s;
-      for (auto& v : sc)
-        if (v > d->gamma * lim) v = d->gamma * lim, ++r.n_clamped;
-      Mat US = U;
-      for (int i = 0; i < US.r; ++i)
-        for (int j = 0; j < US.c; ++j) US(i, j) *= sc[j];
-      const Mat Mc = la::matmul_nt(US, Wt);
-      m->Kt = la::matmul(la::matmul(spd_pow(m->R11, 0.5), Mc), spd_pow(m->R22, 0.5));
-      r.smax_after = sc[0] / lim;
-    }
-    // Eq. (26a) at the run dt, Eq. (26c).
-    {
-      const int q = m->qE + m->qH;
-      Mat R(q, q);
-      for (int i = 0; i < m->qE; ++i)
-        for (int j = 0; j < m->qE; ++j) R(i, j) = m->R11(i, j) / d->dt;
-      for (int i = 0; i < m->qH; ++i)
-        for (int j = 0; j < m->qH; ++j) R(m->qE + i, m->qE + j) = m->R22(i, j) / d->dt;
-      for (int i = 0; i < m->qE; ++i)
-        for (int j = 0; j < m->qH; ++j) R(i, m->qE + j) = R(m->qE + j, i) = -0.5 * m->Kt(i, j);
-      if (q <= 1200) {
-        std::vector<double> w;
-        Mat Qe;
-        la::eig_sym(R, w, Qe);
-        r.min_eig_R = w.empty() ? 0.0 : w[0] / std::fabs(w.back());
-      } else {
-        r.min_eig_R = la::chol_ok(R) ? 1.0 : -1.0;  // sign only for very large models
-      }
-      double num = 0.0, den = 0.0;
-      for (int i = 0; i < m->qE; ++i)
-        for (int p = 0; p < f.nu; ++p) {
-          const double dv = m->BE(i, p) - m->LE(i, p) * f.S_hat[p];
-          num += dv * dv;
-          den += m->BE(i, p) * m->BE(i, p);
-        }
-      r.cond3_residual = den > 0 ? std::sqrt(num / den) : 0.0;
-    }
+    rom_build_report r = finish_model(m, f, d, n_inputs);
     r.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     m->rep = r;
     if (rep) *rep = r;
   } catch (const std::bad_alloc&) {
     delete m;
-    return set_global_error(FDTD_ENOMEM, "rom_build: out of host memory");
+    return set_global_error(FDTD_ENOMEM, "rom_build: out of host or device memory");
+  } catch (const std::runtime_error& e) {
+    delete m;
+    return set_global_error(FDTD_ECUDA, e.what());
   }
   *out = m;
   return FDTD_OK;
+}
+
+}  // namespace
+
+extern "C" int rom_build(const rom_desc* d, rom_model** out, rom_build_report* rep) {
+  return rom_build_impl(d, out, rep, false, nullptr);
+}
+
+extern "C" int rom_build_gpu(const rom_desc* d, void* cuda_stream, rom_model** out, rom_build_report* rep) {
+  return rom_build_impl(d, out, rep, true, static_cast<cudaStream_t>(cuda_stream));
 }
 
 extern "C" void rom_free(rom_model* m) { delete m; }
