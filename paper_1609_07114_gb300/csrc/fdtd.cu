@@ -38,6 +38,14 @@ __device__ __forceinline__ float comp(const float4& v, int t) {
   return t == 0 ? v.x : (t == 1 ? v.y : (t == 2 ? v.z : v.w));
 }
 
+// Programmatic dependent launch: a kernel lets the next one in the stream
+// start early (pdl_trigger), and the next one runs only its prologue, which
+// reads nothing the earlier kernel writes, before pdl_wait returns (the
+// earlier kernel complete and its writes visible).  Both are no-ops for a
+// kernel launched without the programmatic-serialisation attribute.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // E-edge coefficients from the two adjacent cells {eps/dt, sigma/2}
 // (edge material = mean of the two cells, Sec. II-A).
 __device__ __forceinline__ void edge_coef(float2 m1, float2 m2, float& ca, float& cb) {
@@ -296,6 +304,8 @@ yee_step_kernel(const SimDev* __restrict__ sims, const TileWork* __restrict__ wo
   constexpr int kStrip = 32 * V;
   const TileWork tw = work[blockIdx.x];
   const SimDev sd = sims[tw.sim];
+  pdl_trigger();
+  pdl_wait();   // fields, run data: written by the previous kernels
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int c0 = tw.x0 + warp * kStrip;
   const int nx = sd.nx, P = sd.pitch;
@@ -402,6 +412,7 @@ __device__ __forceinline__ void rom_gemm_rows(const SimDev* __restrict__ sims,
     const int r = e / l4, k4 = e - r * l4;
     async_copy16(mrow + (size_t)r * ms + 4 * k4, g.M + (size_t)(gw.r0 + r) * ld + 4 * k4);
   }
+  pdl_wait();        // model states and Hz^{n+1/2}: written by the previous kernels
   __syncthreads();   // column pointers
   for (int col = warp; col < nc; col += nwarp) {
     const float* __restrict__ sp = s_in[col];
@@ -457,6 +468,7 @@ rom_post_kernel(const SimDev* __restrict__ sims, const RomInstDev* __restrict__ 
                 const GemmWork* __restrict__ gwork, int ngwork, const int* __restrict__ ginst) {
   extern __shared__ float4 smem4[];
   const unsigned FULL = 0xffffffffu;
+  pdl_trigger();
   if ((int)blockIdx.x >= nwork && (int)blockIdx.x < nwork + ngwork) {
     const GemmWork gw = gwork[blockIdx.x - nwork];
     const GemmGroupDev g = groups[gw.group];
@@ -489,6 +501,7 @@ rom_post_kernel(const SimDev* __restrict__ sims, const RomInstDev* __restrict__ 
       const int k = lane + 32 * u;
       mpre[u] = (has && k < l4) ? Mr[k] : make_float4(0.f, 0.f, 0.f, 0.f);
     }
+    pdl_wait();   // model states and Hz^{n+1/2}: written by the previous kernels
     float* v = reinterpret_cast<float*>(smem4);
     for (int k = threadIdx.x; k < ri.ld; k += blockDim.x) {
       float x = 0.f;
@@ -532,6 +545,7 @@ rom_post_kernel(const SimDev* __restrict__ sims, const RomInstDev* __restrict__ 
   } else {
     // Probe blocks, then running-DFT blocks (one thread per monitor and
     // frequency; each accumulator has one owner, steps are stream-ordered).
+    pdl_wait();
     const int b = blockIdx.x - nwork - ngwork;
     const int pb = (run->nprobe + blockDim.x - 1) / blockDim.x;
     const long long n = run->base + c;
@@ -902,6 +916,7 @@ struct fdtd_ctx {
   std::vector<TileWork> tiles;
   int vec = 4;                     // columns per lane of the stencil kernel (2 or 4)
   bool stencil_tma = false;        // bulk-copy (TMA) ring form of the stencil (V = 4)
+  bool pdl = true;                 // programmatic dependent launch of the step kernels (FDTD_PDL=0: off)
   unsigned* status_d = nullptr;    // kernels' status word (RunDev::status)
   SimDev* sims_d = nullptr;
   TileWork* tiles_d = nullptr;
@@ -1176,14 +1191,34 @@ int upload_instances(fdtd_ctx* ctx) {
   return plan_tb(ctx);
 }
 
+// Launch with the programmatic-serialisation attribute when pdl is set (the
+// kernel's prologue may overlap the previous kernel's tail; see pdl_wait).
+template <typename... KArgs, typename... Args>
+void launch_k(void (*k)(KArgs...), unsigned grid, unsigned block, size_t smem, cudaStream_t s, bool pdl,
+              Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl ? 1 : 0;
+  cudaLaunchKernelEx(&cfg, k, args...);
+}
+
 void launch_yee(fdtd_ctx* ctx, cudaStream_t s, int par, int c) {
   const unsigned nb = (unsigned)ctx->tiles.size();
   if (ctx->stencil_tma)
     yee_step_tma_kernel<<<nb, kCtaCols / 4, kTmaSmem, s>>>(ctx->sims_d, ctx->tiles_d, ctx->run_d, par, c);
   else if (ctx->vec == 2)
-    yee_step_kernel<2><<<nb, kCtaCols / 2, 0, s>>>(ctx->sims_d, ctx->tiles_d, ctx->run_d, par, c);
+    launch_k(yee_step_kernel<2>, nb, kCtaCols / 2, 0, s, ctx->pdl, (const SimDev*)ctx->sims_d,
+             (const TileWork*)ctx->tiles_d, (const RunDev*)ctx->run_d, par, c);
   else
-    yee_step_kernel<4><<<nb, kCtaCols / 4, 0, s>>>(ctx->sims_d, ctx->tiles_d, ctx->run_d, par, c);
+    launch_k(yee_step_kernel<4>, nb, kCtaCols / 4, 0, s, ctx->pdl, (const SimDev*)ctx->sims_d,
+             (const TileWork*)ctx->tiles_d, (const RunDev*)ctx->run_d, par, c);
 }
 
 // PML corrections of one step (after the stencil, before the model maps).
@@ -1204,9 +1239,11 @@ void launch_step(fdtd_ctx* ctx, cudaStream_t s, int par, int c, int nprobe_block
   launch_pml(ctx, s, par);
   const int nb = ctx->nromwork + ctx->ngwork + nprobe_blocks;
   if (nb > 0)
-    rom_post_kernel<<<nb, kRomRowsPerCta * 32, ctx->post_smem, s>>>(
-        ctx->sims_d, ctx->insts_d, ctx->romwork_d, ctx->nromwork, ctx->run_d, par, c, ctx->groups_d,
-        ctx->gwork_d, ctx->ngwork, ctx->ginst_d);
+    launch_k(rom_post_kernel, (unsigned)nb, kRomRowsPerCta * 32, ctx->post_smem, s,
+             ctx->pdl && ctx->pml_cells.empty(), (const SimDev*)ctx->sims_d, (const RomInstDev*)ctx->insts_d,
+             (const RomWork*)ctx->romwork_d, ctx->nromwork, (const RunDev*)ctx->run_d, par, c,
+             (const GemmGroupDev*)ctx->groups_d, (const GemmWork*)ctx->gwork_d, ctx->ngwork,
+             (const int*)ctx->ginst_d);
 }
 
 int ensure_graph(fdtd_ctx* ctx, int par, int nprobe_blocks) {
@@ -1551,6 +1588,8 @@ void plan_tiles(fdtd_ctx* ctx) {
   ctx->vec = vec;
   ctx->stencil_tma = false;
   if (const char* e = getenv("FDTD_STENCIL")) ctx->stencil_tma = (vec == 4) && std::string(e) == "tma";
+  ctx->pdl = true;
+  if (const char* e = getenv("FDTD_PDL")) ctx->pdl = atoi(e) != 0;
   int dev = 0, nsm = 1, occ = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
