@@ -743,6 +743,20 @@ int run_grad(fdtd_ctx* ctx, long long nsteps, const fdtd_source* src, int nsrc,
     CK(cudaMemcpy(run2_d, &rd, sizeof(RunDev), cudaMemcpyHostToDevice));
   }
   const unsigned ntiles = (unsigned)ctx->tiles.size();
+  // the reverse cell pass has its own tile plan (fewer resident CTAs per SM
+  // than the forward kernel, so other tile heights fill whole waves)
+  TileWork* atiles_d = nullptr;
+  unsigned natiles = 0;
+  {
+    int dev = 0, nsm = 1, occ = 1;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, adj_cell_kernel, 128, 0));
+    const std::vector<TileWork> at = tile_table(ctx->sims, best_tile_rows(ctx->sims, (long long)nsm * std::max(occ, 1)));
+    CK(A.alloc(&atiles_d, at.size()));
+    CK(cudaMemcpy(atiles_d, at.data(), sizeof(TileWork) * at.size(), cudaMemcpyHostToDevice));
+    natiles = (unsigned)at.size();
+  }
   const int npre_extra = (nprobe + nedges + 127) / 128;
   // one fused cell pass per reverse step (FDTD_ADJ_FUSED=0: the two-pass form)
   const char* fe = getenv("FDTD_ADJ_FUSED");
@@ -777,7 +791,7 @@ int run_grad(fdtd_ctx* ctx, long long nsteps, const fdtd_source* src, int nsrc,
       if (nb > 0)
         adj_pre_kernel<<<nb, 128, pre_smem, st>>>(asd_d, aid_d, aw_d, (int)aw.size(), ar_d, par, t, n);
       if (fused) {
-        adj_cell_kernel<<<ntiles, 128, 0, st>>>(asd_d, ctx->tiles_d, par, t);
+        adj_cell_kernel<<<natiles, 128, 0, st>>>(asd_d, atiles_d, par, t);
       } else {
         adj_h_kernel<<<ntiles, 256, 0, st>>>(asd_d, ctx->tiles_d, par, t);
         adj_e_kernel<<<ntiles, 256, 0, st>>>(asd_d, ctx->tiles_d, par);

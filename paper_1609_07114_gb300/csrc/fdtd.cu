@@ -1576,6 +1576,35 @@ int march(fdtd_ctx* ctx, long long nsteps, int nprobe) {
 
 namespace {
 
+// Tile height th minimising ceil(T / slots) * (th + 1) over 8..128 rows
+// (T = tiles of kCtaCols columns x th rows over every simulation).
+int best_tile_rows(const std::vector<SimHost>& sims, long long slots) {
+  auto total = [&](int th) {
+    long long t = 0;
+    for (const SimHost& sh : sims) t += (long long)((sh.nx + kCtaCols - 1) / kCtaCols) * ((sh.ny + th - 1) / th);
+    return t;
+  };
+  int best = 32;
+  long long best_cost = -1;
+  for (int th = 8; th <= 128; ++th) {
+    const long long cost = ((total(th) + slots - 1) / slots) * (th + 1);
+    if (best_cost < 0 || cost <= best_cost) best_cost = cost, best = th;
+  }
+  return best;
+}
+
+// Tile table of kCtaCols x th tiles over every simulation.
+std::vector<TileWork> tile_table(const std::vector<SimHost>& sims, int th) {
+  std::vector<TileWork> t;
+  for (int s = 0; s < (int)sims.size(); ++s) {
+    const SimHost& sh = sims[s];
+    for (int ty = 0; ty < (sh.ny + th - 1) / th; ++ty)
+      for (int tx = 0; tx < (sh.nx + kCtaCols - 1) / kCtaCols; ++tx)
+        t.push_back({s, tx * kCtaCols, ty * th, std::min(sh.ny, (ty + 1) * th)});
+  }
+  return t;
+}
+
 // Tile plan of the stencil kernel.  A CTA covers kCtaCols columns; the tile
 // height th (same for every simulation) is chosen so that the tiles fill
 // whole waves of resident CTAs: minimise ceil(T / slots) * (th + 1) (the +1
@@ -1600,21 +1629,9 @@ void plan_tiles(fdtd_ctx* ctx) {
   else
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, yee_step_kernel<4>, kCtaCols / 4, 0);
   const long long slots = (long long)nsm * std::max(occ, 1);
-  auto total = [&](int th) {
-    long long t = 0;
-    for (const SimHost& sh : ctx->sims) t += (long long)((sh.nx + kCtaCols - 1) / kCtaCols) * ((sh.ny + th - 1) / th);
-    return t;
-  };
-  int best = 32;
-  if (const char* e = getenv("FDTD_TILE_ROWS")) {
+  int best = best_tile_rows(ctx->sims, slots);
+  if (const char* e = getenv("FDTD_TILE_ROWS"))
     best = std::min(512, std::max(4, atoi(e)));   // <= 512: one warp's 32 bit words cover a tile
-  } else {
-    long long best_cost = -1;
-    for (int th = 8; th <= 128; ++th) {
-      const long long cost = ((total(th) + slots - 1) / slots) * (th + 1);
-      if (best_cost < 0 || cost <= best_cost) best_cost = cost, best = th;
-    }
-  }
   ctx->tiles.clear();
   for (int s = 0; s < (int)ctx->sims.size(); ++s) {
     SimHost& sh = ctx->sims[s];
