@@ -1093,14 +1093,14 @@ int plan_tb(fdtd_ctx* ctx) {
 }
 
 // Instances are stepped either one row per warp (rom_post_kernel's first
-// block range) or, when at least FDTD_ROM_GEMM_MIN (default 8) of them share
+// block range) or, when at least FDTD_ROM_GEMM_MIN (default 20) of them share
 // one coupled map, as one GEMM over the shared [P | Q] (second range; 8 or
 // 32 rows x up to 32 simulations per CTA, FDTD_GEMM_RPW = 1 or 4).
 int upload_instances(fdtd_ctx* ctx) {
   std::vector<RomInstDev> h(ctx->insts.size());
   std::vector<RomWork> wk;
   size_t smem = 0;
-  int gemm_min = 8;
+  int gemm_min = 20;   // measured: below ~20 simulations per map one row per warp is as fast or faster
   if (const char* e = getenv("FDTD_ROM_GEMM_MIN")) gemm_min = std::max(1, atoi(e));
   // rows per warp of the GEMM form: 4 when the map is shared by >= 32
   // simulations (the panel is re-staged less often), else 1 (more CTAs);
@@ -1240,7 +1240,8 @@ void launch_step(fdtd_ctx* ctx, cudaStream_t s, int par, int c, int nprobe_block
   const int nb = ctx->nromwork + ctx->ngwork + nprobe_blocks;
   if (nb > 0)
     launch_k(rom_post_kernel, (unsigned)nb, kRomRowsPerCta * 32, ctx->post_smem, s,
-             ctx->pdl && ctx->pml_cells.empty(), (const SimDev*)ctx->sims_d, (const RomInstDev*)ctx->insts_d,
+             ctx->pdl, (const SimDev*)ctx->sims_d,
+             (const RomInstDev*)ctx->insts_d,
              (const RomWork*)ctx->romwork_d, ctx->nromwork, (const RunDev*)ctx->run_d, par, c,
              (const GemmGroupDev*)ctx->groups_d, (const GemmWork*)ctx->gwork_d, ctx->ngwork,
              (const int*)ctx->ginst_d);

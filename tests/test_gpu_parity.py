@@ -328,3 +328,12 @@ def test_non_finite_state_is_reported():
     with pytest.raises(pg.FdtdError) as ei:
         ctx.energy()
     assert ei.value.code == -6
+
+
+@pytest.mark.parametrize("rpw", ["1", "4"])
+def test_batched_layout_through_gemm_form(monkeypatch, rpw):
+    """The same case with every shared map stepped as a GEMM (threshold 1),
+    both CTA shapes of the GEMM form."""
+    monkeypatch.setenv("FDTD_ROM_GEMM_MIN", "1")
+    monkeypatch.setenv("FDTD_GEMM_RPW", rpw)
+    test_batched_layout_parity()
