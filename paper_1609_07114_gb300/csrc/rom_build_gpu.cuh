@@ -24,11 +24,10 @@
 
 // ---------------------------------------------------------------- kernels
 
-// X_E <- X_E / a11 (kept in T), then X_H <- X_H - c K^T T (first half of
-// the pencil solve).  Column c of X at X + c * N.
-__global__ void pencil_pre_kernel(double* __restrict__ X, double* __restrict__ T, int N, int nE, int nH,
-                                  int m, const double* __restrict__ a11, const int* __restrict__ kte,
-                                  const double* __restrict__ ktv, double c) {
+// T = X_E / a11 (first step of the pencil solve; pencil_h_kernel then forms
+// X_H - c K^T T).  Column c of X at X + c * N.
+__global__ void pencil_pre_kernel(const double* __restrict__ X, double* __restrict__ T, int N, int nE, int m,
+                                  const double* __restrict__ a11) {
   const long long tot = (long long)m * nE;
   for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < tot; k += (long long)gridDim.x * blockDim.x) {
     const int col = (int)(k / nE), e = (int)(k - (long long)col * nE);
@@ -338,7 +337,7 @@ struct GpuBuild {
 
   // X <- (psi0 R + F)^{-1} X, X N x m column-major.
   void pencil_solve(double* X, int m, double psi0, double* T) {
-    pencil_pre_kernel<<<grid((long long)m * nE), 256, 0, st>>>(X, T, N, nE, nH, m, a11, kte, ktv, 0.0);
+    pencil_pre_kernel<<<grid((long long)m * nE), 256, 0, st>>>(X, T, N, nE, m, a11);
     pencil_h_kernel<<<grid((long long)m * nH), 256, 0, st>>>(X, T, N, nE, nH, m, kte, ktv, 0.5 * (1.0 - psi0));
     const int wpb = 4;
     band_solve_kernel<<<(m + wpb - 1) / wpb, 32 * wpb, sizeof(double) * wpb * (bw + 1), st>>>(X, N, nE, nH, m, L, bw);
