@@ -90,10 +90,10 @@ def profile_traffic():
 def stencil_source_sha():
     """Hash of the stencil kernel's source: the grid and tile structures of
     kernels.cuh (up to the reduced-model structures) plus the part of fdtd.cu
-    from the stencil kernel up to the reduced-model kernel."""
+    from the edge-coefficient helper up to the reduced-model kernel."""
     d = os.path.join(ROOT, "paper_1609_07114_gb300", "csrc")
     cu = open(os.path.join(d, "fdtd.cu")).read()
-    a = cu.index("// Fused coarse H and E half steps")
+    a = cu.index("// E-edge coefficients from the two adjacent cells")
     b = cu.index("// Eq. (23) for every embedded model")
     kh = open(os.path.join(d, "kernels.cuh")).read()
     kh = kh[:kh.index("struct RomInstDev")]

@@ -48,11 +48,14 @@ __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;"
 
 // E-edge coefficients from the two adjacent cells {eps/dt, sigma/2}
 // (edge material = mean of the two cells, Sec. II-A).
+// ca = (A - S)/(A + S) is formed as 1 - 2 S cb: exactly 1 on a lossless
+// edge (A cb rounded can fall one unit below 1, which would damp lossless
+// media by ~1e-7 per step).
 __device__ __forceinline__ void edge_coef(float2 m1, float2 m2, float& ca, float& cb) {
   const float A = 0.5f * (m1.x + m2.x);
   const float S = 0.5f * (m1.y + m2.y);
   cb = __frcp_rn(A + S);
-  ca = (A - S) * cb;
+  ca = __fmaf_rn(-2.f * S, cb, 1.f);
 }
 
 // Fused coarse H and E half steps over one tile (module header).
