@@ -297,6 +297,11 @@ struct GpuBuild {
 
   unsigned grid(long long work) const { return (unsigned)std::min<long long>(4096, (work + 255) / 256); }
 
+  static void check(const char* what) {
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) throw std::runtime_error(std::string(what) + ": " + cudaGetErrorString(e));
+  }
+
   // C (ka x kb, column-major, host) = A^T B over n rows.
   Mat gram(const double* A, int lda, const double* B, int ldb, int n, int ka, int kb) {
     const int nsplit = (n + kGemmChunk - 1) / kGemmChunk;
@@ -313,6 +318,7 @@ struct GpuBuild {
     dim3 g((ka + 31) / 32, (kb + 31) / 32, nsplit);
     gemm_tn_partial_kernel<<<g, 256, 0, st>>>(A, lda, B, ldb, n, ka, kb, part);
     gemm_reduce_kernel<<<grid((long long)ka * kb), 256, 0, st>>>(part, nsplit, ka * kb, C);
+    check("rom_build_gpu: kernel launch failed");
     std::vector<double> h((size_t)ka * kb);
     if (cudaMemcpyAsync(h.data(), C, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess)
@@ -339,9 +345,13 @@ struct GpuBuild {
   void pencil_solve(double* X, int m, double psi0, double* T) {
     pencil_pre_kernel<<<grid((long long)m * nE), 256, 0, st>>>(X, T, N, nE, m, a11);
     pencil_h_kernel<<<grid((long long)m * nH), 256, 0, st>>>(X, T, N, nE, nH, m, kte, ktv, 0.5 * (1.0 - psi0));
-    const int wpb = 4;
-    band_solve_kernel<<<(m + wpb - 1) / wpb, 32 * wpb, sizeof(double) * wpb * (bw + 1), st>>>(X, N, nE, nH, m, L, bw);
+    // warps per block so that their rings fit the default 48 KB of shared memory
+    const size_t ring = sizeof(double) * (bw + 1);
+    if (ring > 48 * 1024) throw std::runtime_error("rom_build_gpu: fine region wider than 6143 cells");
+    const int wpb = (int)std::max<size_t>(1, std::min<size_t>(4, (48 * 1024) / ring));
+    band_solve_kernel<<<(m + wpb - 1) / wpb, 32 * wpb, ring * wpb, st>>>(X, N, nE, nH, m, L, bw);
     pencil_post_kernel<<<grid((long long)m * nE), 256, 0, st>>>(X, T, N, nE, m, a11, kh, kv, 0.5 * (psi0 + 1.0));
+    check("rom_build_gpu: kernel launch failed");
   }
 };
 
