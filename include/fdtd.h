@@ -307,6 +307,14 @@ int fdtd_fine_fields(fdtd_ctx* ctx, int inst, const rom_model* model, float* Ex,
 
 /* ------------------------------------------------------------------ state */
 
+/* Self-test of failure detection (no counterpart in the paper): launches a
+ * kernel whose bounded wait on a barrier that nothing arrives at gives up
+ * after a short limit and reports through the context's status word, the
+ * same path the bulk-copy stencil uses; returns FDTD_ETIMEOUT when the path
+ * works (FDTD_OK would mean the wait did not give up), and the context stays
+ * usable.  Synchronises. */
+int fdtd_selftest_timeout(fdtd_ctx* ctx);
+
 /* Host copies of the current fields of one simulation (E^n, Hz^{n-1/2}). */
 int fdtd_get_fields(fdtd_ctx* ctx, int sim, float* Ex, float* Ey, float* Hz);
 /* Overwrites the fields; values on PEC walls and inside regions are

@@ -114,6 +114,7 @@ def lib() -> C.CDLL:
         "fdtd_dft_get": (i, [vp, _dp]),
         "fdtd_fine_fields": (i, [vp, i, vp, vp, vp, vp]),
         "fdtd_set_pml": (i, [vp, i, C.POINTER(fdtd_pml_desc)]),
+        "fdtd_selftest_timeout": (i, [vp]),
         "rom_get_basis": (i, [vp, C.POINTER(i), C.POINTER(i), _dp, _dp]),
         "fdtd_set_timing": (i, [vp, i]),
         "fdtd_get_kernel_times": (i, [vp, _dp, C.POINTER(ll), _dp, C.POINTER(ll)]),
@@ -356,6 +357,11 @@ class FdtdContext:
         """``fdtd_load_state``."""
         buf = C.create_string_buffer(data, len(data))
         self._ck(lib().fdtd_load_state(self._h, buf, len(data)))
+
+    def selftest_timeout(self):
+        """``fdtd_selftest_timeout``: the status code of the bounded-wait
+        failure path (FDTD_ETIMEOUT when it works)."""
+        return lib().fdtd_selftest_timeout(self._h)
 
     def set_pml(self, sim, sides, ncells, m=3.0, sigma_max=0.0, kappa_max=1.0, alpha_max=0.0):
         """Convolutional PML layers of simulation `sim` (``fdtd_set_pml``);

@@ -18,6 +18,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "internal.hpp"
 #include "kernels.cuh"
 
@@ -1017,6 +1019,12 @@ int check_status(fdtd_ctx* ctx) {
   return FDTD_OK;
 }
 
+// NVTX range for the duration of a scope (profiler timelines).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
+
 void drop_graphs(fdtd_ctx* ctx) {
   for (int p = 0; p < 2; ++p) {
     if (ctx->graph[p]) cudaGraphExecDestroy(ctx->graph[p]);
@@ -1872,6 +1880,7 @@ int fdtd_create(const fdtd_grid_desc* g, void* cuda_stream, fdtd_ctx** out) {
 }
 
 int rom_embed(fdtd_ctx* ctx, const rom_model* m, int sim, int i0, int j0, int* inst_out) {
+  NvtxRange nvtx_("rom_embed");
   if (!ctx || !m) return fail(ctx, FDTD_EINVAL, "rom_embed: null argument");
   if (sim < 0 || sim >= (int)ctx->sims.size()) return fail(ctx, FDTD_EINVAL, "rom_embed: sim out of range");
   if (std::fabs(m->dt - ctx->dt) > 1e-12 * ctx->dt || std::fabs(m->dx - ctx->dx) > 1e-12 * ctx->dx ||
@@ -1989,6 +1998,7 @@ int fdtd_get_rom_map(const fdtd_ctx* ctx, int inst, int* n, int* ny, double* P, 
 
 int fdtd_run(fdtd_ctx* ctx, long long nsteps, const fdtd_source* src, int nsrc,
              const fdtd_probe* probes, int nprobe, float* probe_out) {
+  NvtxRange nvtx_("fdtd_run");
   if (!ctx || nsteps < 0 || nsrc < 0 || nprobe < 0 || (nsrc && !src) || (nprobe && !probes))
     return fail(ctx, FDTD_EINVAL, "fdtd_run: bad argument");
   if (nsteps == 0) return FDTD_OK;
@@ -2001,6 +2011,7 @@ int fdtd_run(fdtd_ctx* ctx, long long nsteps, const fdtd_source* src, int nsrc,
 
 int fdtd_run_host(fdtd_ctx* ctx, long long nsteps, const fdtd_source* src, int nsrc,
                   const fdtd_probe* probes, int nprobe, float* probe_out_host) {
+  NvtxRange nvtx_("fdtd_run_host");
   if (!ctx || nsteps < 0 || nsrc < 0 || nprobe < 0 || (nsrc && !src) || (nprobe && !probes) ||
       (nprobe && !probe_out_host))
     return fail(ctx, FDTD_EINVAL, "fdtd_run_host: bad argument");
@@ -2097,6 +2108,7 @@ int fdtd_set_rom_state(fdtd_ctx* ctx, int inst, const float* x) {
 }
 
 int fdtd_energy(fdtd_ctx* ctx, double* out) {
+  NvtxRange nvtx_("fdtd_energy");
   if (!ctx || !out) return fail(ctx, FDTD_EINVAL, "fdtd_energy: bad argument");
   const int ntiles = (int)ctx->tiles.size(), ninst = (int)ctx->insts.size();
   const int nsim = (int)ctx->sims.size();
@@ -2149,6 +2161,7 @@ int fdtd_energy_noalloc(fdtd_ctx* ctx, double* out) {
 int fdtd_grad(fdtd_ctx* ctx, long long nsteps, const fdtd_source* src, int nsrc,
               const fdtd_probe* probes, int nprobe, int ckpt_every, float* dJ_deps,
               float* dJ_dsigma, float* dJ_dsrc, double* J_out) {
+  NvtxRange nvtx_("fdtd_grad");
   if (!ctx) return fail(ctx, FDTD_EINVAL, "fdtd_grad: null context");
   if (ctx->timing) return fail(ctx, FDTD_EINVAL, "fdtd_grad: switch timing off first");
   return run_grad(ctx, nsteps, src, nsrc, probes, nprobe, ckpt_every, dJ_deps, dJ_dsigma, dJ_dsrc, J_out);
@@ -2248,6 +2261,17 @@ int fdtd_load_state(fdtd_ctx* ctx, const void* buf, size_t size) {
   if (pml_psi_count(ctx)) CK(cudaMemcpy(ctx->pml_psi.p, p, sizeof(float) * pml_psi_count(ctx), cudaMemcpyHostToDevice));
   ctx->step = hdr[1];
   return FDTD_OK;
+}
+
+int fdtd_selftest_timeout(fdtd_ctx* ctx) {
+  if (!ctx) return set_global_error(FDTD_EINVAL, "fdtd_selftest_timeout: null context");
+  CK(cudaStreamSynchronize(ctx->stream));
+  int rc = check_status(ctx);   // report anything earlier first
+  if (rc) return rc;
+  wait_selftest_kernel<<<1, 64, 0, ctx->stream>>>(ctx->status_d, 1000u);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(ctx->stream));
+  return check_status(ctx);
 }
 
 int fdtd_set_pml(fdtd_ctx* ctx, int sim, const fdtd_pml_desc* pd) {

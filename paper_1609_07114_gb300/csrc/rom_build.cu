@@ -26,6 +26,8 @@
 #include <new>
 #include <stdexcept>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "internal.hpp"
 
 namespace {
@@ -477,11 +479,17 @@ int rom_build_impl(const rom_desc* d, rom_model** out, rom_build_report* rep, bo
 }  // namespace
 
 extern "C" int rom_build(const rom_desc* d, rom_model** out, rom_build_report* rep) {
-  return rom_build_impl(d, out, rep, false, nullptr);
+  nvtxRangePushA("rom_build");
+  const int rc = rom_build_impl(d, out, rep, false, nullptr);
+  nvtxRangePop();
+  return rc;
 }
 
 extern "C" int rom_build_gpu(const rom_desc* d, void* cuda_stream, rom_model** out, rom_build_report* rep) {
-  return rom_build_impl(d, out, rep, true, static_cast<cudaStream_t>(cuda_stream));
+  nvtxRangePushA("rom_build_gpu");
+  const int rc = rom_build_impl(d, out, rep, true, static_cast<cudaStream_t>(cuda_stream));
+  nvtxRangePop();
+  return rc;
 }
 
 extern "C" void rom_free(rom_model* m) { delete m; }

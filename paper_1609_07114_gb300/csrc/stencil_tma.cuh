@@ -71,10 +71,25 @@ __device__ __forceinline__ void fence_proxy_async_smem() {
 }
 
 // Bounded wait; false if the limit was reached.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
-  for (unsigned k = 0; k < kTmaSpinLimit; ++k)
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, unsigned limit = kTmaSpinLimit) {
+  for (unsigned k = 0; k < limit; ++k)
     if (mbar_try_wait(bar, parity)) return true;
   return false;
+}
+
+// Self-test of the failure path of the bounded waits: every thread waits on
+// a barrier that nothing arrives at (no copy is ever issued to it), gives up
+// after `limit` polls and reports through the status word, as the stencil's
+// waits do.
+__global__ void wait_selftest_kernel(unsigned* status, unsigned limit) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  const bool ok = mbar_wait(&bar, 0u, limit);
+  if (__any_sync(0xffffffffu, !ok) && (threadIdx.x & 31) == 0) atomicOr(status, 1u);
 }
 
 __global__ void __launch_bounds__(kCtaCols / 4, 4)
