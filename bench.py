@@ -498,6 +498,10 @@ def main():
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
+        # one host core, as reported (numpy's BLAS would otherwise thread the
+        # small model products); set before numpy is first imported
+        for v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+            os.environ.setdefault(v, "1")
         run_reference(args)
         return
     if args.workload == "adjoint":
