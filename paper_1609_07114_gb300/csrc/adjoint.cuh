@@ -96,8 +96,18 @@ adj_pre_kernel(const AdjSimDev* __restrict__ sims, const AdjInstDev* __restrict_
     }
     __syncthreads();
     for (int c = w.c0 + threadIdx.x; c < w.c1; c += blockDim.x) {
+      // column c of [P | Q] against g_s, in order r = 0, 1, ...; the loads of
+      // 16 rows are issued before their products so they are in flight together
       float acc = 0.f;
-      for (int r = 0; r < ai.n; ++r) acc = fmaf(ai.M[(size_t)r * ai.ld + c], gsh[r], acc);
+      const float* __restrict__ Mc = ai.M + c;
+      for (int r0 = 0; r0 < ai.n; r0 += 16) {
+        float mv[16];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) mv[u] = r0 + u < ai.n ? Mc[(size_t)(r0 + u) * ai.ld] : 0.f;
+#pragma unroll
+        for (int u = 0; u < 16; ++u)
+          if (r0 + u < ai.n) acc = fmaf(mv[u], gsh[r0 + u], acc);
+      }
       if (c < ai.n) {
         gsb[c] = acc;
       } else {
