@@ -140,3 +140,49 @@ def test_multi_strip_gradients_match_oracle():
     assert rel_l2(ge[0], deps) < GTOL
     assert rel_l2(gs[0], dsig) < GTOL
     assert rel_l2(gw[0], gsrc[0]) < GTOL
+
+
+def test_full_size_gradient_properties():
+    """The gradient configuration at full batch size (16 x 1024^2, two shared
+    models each), in the benchmark's launch configuration, over 3000 steps
+    with checkpoints every 500: J is quadratic in the sources, so
+    J = 1/2 sum s . dJ/ds (Euler); and the eps gradient at the cell with the
+    largest sensitivity matches a central difference of two forward runs."""
+    N = 3000
+    w = workloads.adjoint_16(N)
+    models = [pg.rom_build(md["a"], md["b"], md["r"], w["dx"], w["dy"], w["dt"], md["eps_r"],
+                           md["sigma"], md["q"], f0=md["f0"]) for md in w["models"]]
+
+    def ctx_for(eps_list):
+        ctx = pg.FdtdContext(w["dx"], w["dy"], w["dt"], [(e, s["sigma"]) for e, s in zip(eps_list, w["sims"])])
+        for k, s in enumerate(w["sims"]):
+            for (mi, i0, j0) in s["place"]:
+                ctx.rom_embed(models[mi], k, i0, j0)
+        return ctx
+
+    waves = [torch.tensor(np.asarray(s["source"]["wave"], np.float32), device="cuda") for s in w["sims"]]
+    src = [dict(s["source"], sim=k, wave=waves[k]) for k, s in enumerate(w["sims"])]
+    probes = [(k, i, j) for k, s in enumerate(w["sims"]) for (i, j) in s["probes"]]
+    eps0 = [s["eps_r"] for s in w["sims"]]
+    J, ge, gs, gw = ctx_for(eps0).fdtd_grad(N, src, probes, 500)
+    assert J > 0
+    gw = gw.cpu().numpy()
+    euler = 0.5 * sum(float(np.dot(np.asarray(s["source"]["wave"][:N], np.float64), gw[k]))
+                      for k, s in enumerate(w["sims"]))
+    assert abs(euler - J) < 1e-3 * J
+    gmax = [float(g.abs().max()) for g in ge]
+    k = int(np.argmax(gmax))
+    gk = ge[k].cpu().numpy()
+    j, i = np.unravel_index(np.argmax(np.abs(gk)), gk.shape)
+    h = 1e-3 * eps0[k][j, i]
+
+    def J_at(delta):
+        eps = [e.copy() for e in eps0]
+        eps[k][j, i] += delta
+        ctx = ctx_for(eps)
+        out = torch.zeros((N, len(probes)), dtype=torch.float32, device="cuda")
+        ctx.fdtd_run(N, src, probes, out)
+        return float((out.double() ** 2).sum())
+
+    fd = (J_at(h) - J_at(-h)) / (2 * h)
+    assert abs(fd - gk[j, i]) < 2e-2 * abs(gk[j, i])

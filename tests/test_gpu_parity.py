@@ -337,3 +337,38 @@ def test_batched_layout_through_gemm_form(monkeypatch, rpw):
     monkeypatch.setenv("FDTD_ROM_GEMM_MIN", "1")
     monkeypatch.setenv("FDTD_GEMM_RPW", rpw)
     test_batched_layout_parity()
+
+
+def test_full_batched_256_sampled_simulations():
+    """All 256 simulations of the batched configuration (four maps shared by
+    64 simulations each, so the GEMM form with 32-row CTAs) in one context,
+    as the benchmark runs them; one simulation of each size is recomputed by
+    the oracle and compared probe by probe and field by field."""
+    N = 300
+    wb = workloads.batched_256(N)
+    ctx = pg.FdtdContext(wb["dx"], wb["dy"], wb["dt"], [(s["eps_r"], s["sigma"]) for s in wb["sims"]])
+    models = [pg.rom_build(md["a"], md["b"], md["r"], wb["dx"], wb["dy"], wb["dt"], md["eps_r"],
+                           md["sigma"], md["q"], f0=md["f0"]) for md in wb["models"]]
+    for k, s in enumerate(wb["sims"]):
+        for (mi, i0, j0) in s["place"]:
+            ctx.rom_embed(models[mi], k, i0, j0)
+    waves, srcs, probes = [], [], []
+    for k, s in enumerate(wb["sims"]):
+        t = torch.tensor(np.asarray(s["source"]["wave"], np.float32), device="cuda")
+        waves.append(t)
+        srcs.append(dict(s["source"], sim=k, wave=t))
+        si, sj = s["source"]["i"], s["source"]["j"]
+        probes.append((k, s["probe"][0], s["probe"][1]))
+        probes.append((k, min(si + 5, s["nx"] - 2), sj))
+    out = torch.zeros((N, len(probes)), dtype=torch.float32, device="cuda")
+    ctx.fdtd_run(N, srcs, probes, out)
+    g = out.cpu().numpy()
+    for k in (0, 64, 128, 192):          # one of each size
+        s = wb["sims"][k]
+        w = dict(nx=s["nx"], ny=s["ny"], dx=wb["dx"], dy=wb["dy"], dt=wb["dt"], eps_r=s["eps_r"],
+                 sigma=s["sigma"], roms=[dict(wb["models"][mi], i0=i0, j0=j0) for (mi, i0, j0) in s["place"]],
+                 sources=[s["source"]], probes=[p[1:] for p in probes[2 * k:2 * k + 2]], nsteps=N)
+        o, st = oracle_run(w, N)
+        assert np.abs(o).max() > 0
+        assert rel_l2(g[:, 2 * k:2 * k + 2], o) < TOL
+        check_fields(ctx, k, st)
