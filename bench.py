@@ -31,6 +31,10 @@ import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+# the CPU oracle timings run on one host core, as they report (numpy's BLAS
+# would otherwise thread the small model products); set before numpy loads
+for _v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
 
 METRIC = "Yee+ROM Gcell-steps/s"
 UNIT = "Gcell-steps/s"
@@ -498,10 +502,6 @@ def main():
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
-        # one host core, as reported (numpy's BLAS would otherwise thread the
-        # small model products); set before numpy is first imported
-        for v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
-            os.environ.setdefault(v, "1")
         run_reference(args)
         return
     if args.workload == "adjoint":
