@@ -220,7 +220,8 @@ def run_batched(args):
     import workloads
     pbuild.build()
     K, W, T = args.steps, args.warmup, args.tsteps
-    w = workloads.batched_256((W + K) * T)
+    Tp = max(T // 5, 32)      # time steps of each one-at-a-time run (two runs per simulation)
+    w = workloads.batched_256(max((W + K) * T, 2 * Tp))
     models = [pg.rom_build(md["a"], md["b"], md["r"], w["dx"], w["dy"], w["dt"], md["eps_r"],
                            md["sigma"], md["q"], f0=md["f0"]) for md in w["models"]]
     sims = w["sims"]
@@ -259,7 +260,6 @@ def run_batched(args):
     yee_ms, n_yee, post_ms, n_post = ctx.kernel_times()
     ctx.close()
     # plain: one context and one fdtd_run at a time, Tp steps each
-    Tp = max(T // 5, 32)
     el_p = 0.0
     outp = torch.zeros((Tp, 1), dtype=torch.float32, device="cuda")
     for s in sims:
