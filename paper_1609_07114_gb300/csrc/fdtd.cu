@@ -52,11 +52,19 @@ __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;"
 // (edge material = mean of the two cells, Sec. II-A).
 // ca = (A - S)/(A + S) is formed as 1 - 2 S cb: exactly 1 on a lossless
 // edge (A cb rounded can fall one unit below 1, which would damp lossless
-// media by ~1e-7 per step).
+// media by ~1e-7 per step).  cb is the hardware reciprocal (one MUFU op,
+// relative error ~1e-7: the same as a relative change of the edge's
+// material below FP32 resolution, and the same value in every kernel).
+__device__ __forceinline__ float rcp_hw(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
 __device__ __forceinline__ void edge_coef(float2 m1, float2 m2, float& ca, float& cb) {
   const float A = 0.5f * (m1.x + m2.x);
   const float S = 0.5f * (m1.y + m2.y);
-  cb = __frcp_rn(A + S);
+  cb = rcp_hw(A + S);
   ca = __fmaf_rn(-2.f * S, cb, 1.f);
 }
 
