@@ -276,6 +276,7 @@ struct AdjRowIn {
   float4 m1a, m1b;      // mat(j+1)
   float4 x0, x1;        // Ex frames E^n, E^{n+1} of edge row j+1
   float4 y0, y1;        // Ey frames of row j
+  float4 ae, as;        // the segment's eps / sigma accumulators of row j
   float gyR, y0R, y1R;  // lane 31: Ey edge (c0 + 128, j)
   float2 mR;            // lane 31: mat(c0 + 128, j)
   float gx1L, gyL, ghL; // lane 0: g_Ex(c0-1, j+1), g_Ey(c0-1, j), g_H(c0-1, j)
@@ -297,6 +298,8 @@ __device__ __forceinline__ void adj_load_row(AdjRowIn& r, const AdjSimDev& sd, c
   r.x1 = ld4(ex1 + row + P + cl);
   r.y0 = ld4(ey0 + row + cl);
   r.y1 = ld4(ey1 + row + cl);
+  r.ae = ld4(sd.geps + row + cl);
+  r.as = ld4(sd.gsig + row + cl);
   if (right) {
     r.gyR = geya[row + c0 + 128];
     r.y0R = ey0[row + c0 + 128];
@@ -432,22 +435,29 @@ adj_cell_kernel(const AdjSimDev* __restrict__ sims, const TileWork* __restrict__
       }
     }
     // g_H' of the row's cells and their material terms
-    float gn[4];
+    // (the accumulators were loaded with the row; cells that take no term
+    // keep their value, and only the tile's own rows are written back)
+    float gn[4], ae[4], as[4];
     const bool own = j >= j0;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const bool live = cl + q < nx && mj[q].x >= 0.f;
       const float mr = q < 3 ? muy[q + 1] : muyR;
       gn[q] = live ? comp(cur.gh, q) + sd.rdy * mux[q] - sd.rdy * mux1[q] - sd.rdx * muy[q] + sd.rdx * mr : 0.f;
-      if (own && live) {
+      ae[q] = comp(cur.ae, q);
+      as[q] = comp(cur.as, q);
+      if (live) {
         const float er = q < 3 ? edy[q + 1] : edyR;
         const float sr = q < 3 ? esy[q + 1] : esyR;
         const float qe = edx[q] + edx1[q] + edy[q] + er;
         const float qs = esx[q] + esx1[q] + esy[q] + sr;
-        const size_t off = row + cl + q;
-        sd.geps[off] += 0.5f * sd.inv_dt * qe;
-        sd.gsig[off] -= 0.25f * qs;
+        ae[q] += 0.5f * sd.inv_dt * qe;
+        as[q] -= 0.25f * qs;
       }
+    }
+    if (own) {
+      st4(sd.geps + row + cl, make_float4(ae[0], ae[1], ae[2], ae[3]));
+      st4(sd.gsig + row + cl, make_float4(as[0], as[1], as[2], as[3]));
     }
     // lane 0: g_H' of the halo column c0 - 1
     float gnL = 0.f;
