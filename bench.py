@@ -76,13 +76,16 @@ def peaks():
     return FALLBACK_HBM_GBS, "fallback"
 
 
-def profile_traffic():
-    """DRAM bytes per stencil launch from the committed ncu summary, if it
-    was taken on the current kernel source."""
-    summ = os.path.join(ROOT, "profiles", "yee_step_grid4096.md")
+PROFILE_OF = {"yee_step_kernel": "yee_step_grid4096.md", "yee_tb2m_kernel": "yee_tb2m_grid4096.md"}
+
+
+def profile_traffic(kernel="yee_step_kernel"):
+    """DRAM bytes per launch of `kernel` on the 4096^2 workload from the
+    committed ncu summary, if it was taken on the current kernel source."""
+    summ = os.path.join(ROOT, "profiles", PROFILE_OF[kernel])
     if not os.path.exists(summ):
         return None
-    sha = stencil_source_sha()
+    sha = stencil_source_sha() if kernel == "yee_step_kernel" else march_source_sha()
     txt = open(summ).read()
     m_sha = re.search(r"kernel source sha256\[:16\]:\s*([0-9a-f]+)", txt)
     m_b = re.search(r"dram bytes per full-size launch:\s*([0-9.eE+]+)", txt)
@@ -103,6 +106,19 @@ def stencil_source_sha():
     kh = kh[:kh.index("struct RomInstDev")]
     h = hashlib.sha256(kh.encode() + cu[a:b].encode())
     return h.hexdigest()[:16]
+
+
+def march_source_sha():
+    """Hash of the row-marching two-step kernel's source: the structures of
+    kernels.cuh, fdtd.cu's edge-coefficient helper and tb_march.cuh."""
+    d = os.path.join(ROOT, "paper_1609_07114_gb300", "csrc")
+    cu = open(os.path.join(d, "fdtd.cu")).read()
+    a = cu.index("// E-edge coefficients from the two adjacent cells")
+    b = cu.index("// Fused coarse H and E half steps over one tile")
+    kh = open(os.path.join(d, "kernels.cuh")).read()
+    kh = kh[:kh.index("struct RomInstDev")]
+    tm = open(os.path.join(d, "tb_march.cuh")).read()
+    return hashlib.sha256(kh.encode() + cu[a:b].encode() + tm.encode()).hexdigest()[:16]
 
 
 class ClockSampler:
@@ -258,6 +274,7 @@ def run_batched(args):
     ctx.set_timing(True)
     step(ctx, sims, waves, probes, 0, T, out)
     yee_ms, n_yee, post_ms, n_post = ctx.kernel_times()
+    spl = ctx.steps_per_launch()
     ctx.close()
     # plain: one context and one fdtd_run at a time, Tp steps each
     el_p = 0.0
@@ -286,7 +303,8 @@ def run_batched(args):
                    "batched_over_plain": batched / plain},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": None, "peak_kind": kind,
-                     "kernel": "yee_step_kernel", "kernel_avg_ms": yee_ms / n_yee,
+                     "kernel": "yee_tb2m_kernel" if spl == 2 else "yee_step_kernel",
+                     "kernel_avg_ms": yee_ms / n_yee, "steps_per_launch": spl,
                      "rom_post_avg_ms": post_ms / max(n_post, 1)},
         "gpu_launches": K * (2 * T + T // 16), "clocks": clk.summary()}))
 
@@ -439,8 +457,11 @@ def run_lattice(args):
         one_step(k)
     yee_ms, n_yee, post_ms, n_post = ctx.kernel_times()
     ctx.set_timing(False)
+    spl = ctx.steps_per_launch()
     f_nb = float(np.mean((w["eps_r"] != 1.0) | (w["sigma"] != 0.0)))
-    bpc = 24.0 + 8.0 * f_nb     # fields + the materials of non-background cells
+    # fields + the materials of non-background cells (the two-step kernel
+    # reads every material)
+    bpc = 32.0 if spl == 2 else 24.0 + 8.0 * f_nb
     hbm, kind = peaks()
     achieved = bpc * cells / (yee_ms / n_yee / 1e3) / 1e9
     line = {
@@ -458,7 +479,8 @@ def run_lattice(args):
                    "l2": f"inputs larger than L2: {24 * n * n / 1e9:.2f} GB of fields per time step (L2 129 MB)"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": None, "peak_kind": kind,
-                     "kernel": "yee_step_kernel", "kernel_avg_ms": yee_ms / n_yee,
+                     "kernel": "yee_tb2m_kernel" if spl == 2 else "yee_step_kernel",
+                     "kernel_avg_ms": yee_ms / n_yee, "steps_per_launch": spl,
                      "alg_bytes_per_cell_step": bpc, "rom_post_avg_ms": post_ms / max(n_post, 1)},
         "gpu_launches": (nsteps_timed // T) * (2 * T + T // 16),
         "clocks": clk.summary(),
@@ -586,6 +608,12 @@ def main():
 
     # Per-kernel device time of the dominant (stencil) kernel, CUDA events on
     # the launching stream, over a second pass of the same K steps.
+    # On the two-steps-per-launch path a launch is the row-marching kernel
+    # (with the model tiles beside it): one read and one write pass over the
+    # fields and materials for two steps, so the algorithmic bytes per launch
+    # are the same 32 B per cell.
+    spl = ctx.steps_per_launch()
+    kernel = "yee_tb2m_kernel" if spl == 2 else "yee_step_kernel"
     ctx.set_timing(True)
     for k in range(K):
         one_step(k)
@@ -595,7 +623,7 @@ def main():
     alg_bytes = BYTES_PER_CELL_STEP * cells
     hbm, kind = peaks()
     achieved = alg_bytes / yee_avg_s / 1e9
-    traffic = profile_traffic()
+    traffic = profile_traffic(kernel)
 
     # End to end through the host-buffer entry point: H2D of the step's
     # source samples from pinned memory, D2H of its probe samples.
@@ -615,7 +643,10 @@ def main():
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_sample(build_problem(args.cpu_sample_steps + 1), args.cpu_sample_steps)
 
-    launches_per_run = 2 * T + T // 16
+    if spl == 2:   # per pair: the model tiles (if any) and the row-marching kernel
+        launches_per_run = (T // 2) * (2 if models else 1) + (2 if T % 2 else 0) + T // 16
+    else:
+        launches_per_run = 2 * T + T // 16
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": W,
         "ms_per_step": el_ms / K, "higher_is_better": True, "scaling": "weak",
@@ -628,7 +659,7 @@ def main():
                    "parallelism": "replicas" if ws > 1 else "single"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": traffic, "peak_kind": kind,
-                     "kernel": "yee_step_kernel", "kernel_avg_ms": yee_avg_s * 1e3,
+                     "kernel": kernel, "kernel_avg_ms": yee_avg_s * 1e3, "steps_per_launch": spl,
                      "alg_bytes_per_launch": alg_bytes, "rom_post_avg_ms": post_ms / max(n_post, 1)},
         "cpu_baseline": cpu,
         "e2e": e2e,

@@ -377,9 +377,24 @@ int fdtd_energy_noalloc(fdtd_ctx* ctx, double* out);
  * the stencil kernel and of the reduced-model/probe kernel accumulates until
  * timing is switched on again (which resets it). */
 int fdtd_set_timing(fdtd_ctx* ctx, int on);
-/* Accumulated device time (ms) and launch counts; synchronises the stream. */
+/* Accumulated device time (ms) and launch counts; synchronises the stream.
+ * On the two-steps-per-launch path (fdtd_steps_per_launch = 2) yee_ms is the
+ * time of each two-step launch (the row-marching kernel with the model tiles
+ * beside it, Eq. (5), Eq. (3) and Eq. (23) twice) and yee_launches counts
+ * those launches; a trailing odd step is a one-step launch (stencil only, its
+ * model step counted in post_ms). */
 int fdtd_get_kernel_times(fdtd_ctx* ctx, double* yee_ms, long long* yee_launches,
                           double* post_ms, long long* post_launches);
+
+/* Time steps one stencil launch of fdtd_run advances: 2 when the context
+ * steps in pairs (temporal blocking: two steps of Eq. (5), Eq. (3) per pass
+ * over the fields, each model's Eq. (23) evaluated between them in its own
+ * tile; bit-identical to single steps), else 1.  Contexts with CPML layers
+ * and runs with DFT monitors step singly.  FDTD_TB=0 / 1 in the environment
+ * at context creation forces one or the other where the pair form applies;
+ * unset, pairs are used where the model tiles take at most 1/8 of a wave.
+ * Returns FDTD_EINVAL for a null context. */
+int fdtd_steps_per_launch(const fdtd_ctx* ctx);
 
 const char* fdtd_last_error(const fdtd_ctx* ctx);
 

@@ -118,6 +118,7 @@ def lib() -> C.CDLL:
         "rom_get_basis": (i, [vp, C.POINTER(i), C.POINTER(i), _dp, _dp]),
         "fdtd_set_timing": (i, [vp, i]),
         "fdtd_get_kernel_times": (i, [vp, _dp, C.POINTER(ll), _dp, C.POINTER(ll)]),
+        "fdtd_steps_per_launch": (i, [vp]),
         "fdtd_last_error": (C.c_char_p, [vp]),
     }
     for name, (res, args) in sig.items():
@@ -450,8 +451,16 @@ class FdtdContext:
     def set_timing(self, on: bool):
         self._ck(lib().fdtd_set_timing(self._h, int(bool(on))))
 
+    def steps_per_launch(self) -> int:
+        """2 when runs step in pairs (temporal blocking), else 1."""
+        r = lib().fdtd_steps_per_launch(self._h)
+        if r < 0:
+            self._ck(r)
+        return r
+
     def kernel_times(self):
-        """(stencil ms, stencil launches, ROM/probe ms, ROM/probe launches)."""
+        """(stencil ms, stencil launches, ROM/probe ms, ROM/probe launches);
+        a launch advances steps_per_launch() steps."""
         a, b = C.c_double(), C.c_double()
         na, nb = C.c_longlong(), C.c_longlong()
         self._ck(lib().fdtd_get_kernel_times(self._h, C.byref(a), C.byref(na), C.byref(b), C.byref(nb)))

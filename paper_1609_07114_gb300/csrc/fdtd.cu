@@ -796,6 +796,7 @@ __global__ void advance_kernel(RunDev* run, int by) {
 }  // namespace
 
 #include "tb.cuh"
+#include "tb_march.cuh"
 
 // ============================================================== host side
 
@@ -991,6 +992,22 @@ struct fdtd_ctx {
   DevBuf<int> tb_prb;
   cudaGraphExec_t tb_graph[2] = {nullptr, nullptr};
   int tb_graph_nprobe[2] = {-1, -1};
+  // row-marching form of the two-step path (tb_march.cuh): ordinary areas in
+  // yee_tb2m_kernel, tb_tiles then holds only the model tiles
+  bool tb_march = false;
+  std::vector<TileWork> tbm_tiles;
+  std::vector<int2> tbm_zone_rng;
+  std::vector<int4> tbm_zones;
+  TileWork* tbm_tiles_d = nullptr;
+  int2* tbm_zone_rng_d = nullptr;
+  int4* tbm_zones_d = nullptr;
+  TbMarchDev* tbm_d = nullptr;
+  DevBuf<int2> tbm_src_rng, tbm_prb_rng;
+  DevBuf<int> tbm_ent_sim;
+  DevBuf<MarchSrc> tbm_src;
+  DevBuf<MarchPrb> tbm_prb;
+  int tbm_th = 0;
+  int tbm_pf = 0;                  // rows prefetched into L2 ahead of the loads (FDTD_TB_PF)
   // measurement mode (fdtd_set_timing)
   bool timing = false;
   std::vector<cudaEvent_t> ev;
@@ -1044,27 +1061,47 @@ void drop_graphs(fdtd_ctx* ctx) {
   }
 }
 
-// Plan of the two-steps-per-launch path: ordinary kTbW x kTbH tiles, one
-// tile per model whose output is the model's zone, and the zone lists.  The
-// path is used only when every model fits the in-CTA model step and no model
-// lies within reach (two steps plus the zone margin) of another's tile.
-// Opt-in (FDTD_TB=1): on GB300 it halves the DRAM bytes per step but is
-// issue-bound and slower than the one-step kernel (measured 118 vs 186
-// Gcell-steps/s at 4096^2).
+// Plan of the two-steps-per-pass path: one tile per model whose output is
+// the model's zone (yee_tb2_kernel), and for the rest either the row-marching
+// kernel's kMarchCols x th tiles (default) or, with FDTD_TB_SMEM=1, ordinary
+// kTbW x kTbH shared-memory tiles of yee_tb2_kernel (issue-bound: measured
+// 118 against 186 Gcell-steps/s for the one-step kernel at 4096^2); and the
+// zone lists.  The path is used only when every model fits the in-CTA model
+// step and no model lies within reach (two steps plus the zone margin) of
+// another's tile.
 int plan_tb(fdtd_ctx* ctx) {
   ctx->tb = false;
+  ctx->tb_march = false;
   ctx->tb_tiles.clear();
   ctx->tb_zones.clear();
+  ctx->tbm_tiles.clear();
+  ctx->tbm_zone_rng.clear();
+  ctx->tbm_zones.clear();
+  // FDTD_TB=0: off; 1: on wherever it applies; unset: the row-marching form
+  // where it applies and the model tiles take at most 1/8 of the slots of a
+  // wave (otherwise the one-step kernel, whose sparse-material path and four
+  // resident CTAs per SM win: measured on the 64-model lattice)
   const char* e = getenv("FDTD_TB");
-  if (!e || atoi(e) != 1) return FDTD_OK;
+  const int mode = e ? atoi(e) : -1;
+  if (mode == 0) return FDTD_OK;
   if (!ctx->pml_cells.empty()) return FDTD_OK;   // the layers' corrections need the one-step form
+  const char* es = getenv("FDTD_TB_SMEM");
+  const bool march = !(mode == 1 && es && atoi(es) == 1);
+  if (mode != 1) {
+    int dev = 0, nsm = 1, occ = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, yee_tb2m_kernel, 128, 0);
+    if (16 * (long long)ctx->insts.size() > (long long)nsm * std::max(occ, 1)) return FDTD_OK;
+  }
   const int M = kTbZoneMargin;
   std::vector<int4> zone(ctx->insts.size());
   for (size_t k = 0; k < ctx->insts.size(); ++k) {
     const Instance& in = ctx->insts[k];
     const SimHost& sh = ctx->sims[in.sim];
     if (in.map->ld > kTbMaxRomN) return FDTD_OK;
-    int4 z{std::max(in.i0 - M, 0), std::max(in.j0 - M, 0), std::min(in.i0 + in.a + M, sh.nx),
+    // columns rounded out to multiples of 4 (whole float4 groups of the march)
+    int4 z{std::max(in.i0 - M, 0) & ~3, std::max(in.j0 - M, 0), std::min((in.i0 + in.a + M + 3) & ~3, sh.nx),
            std::min(in.j0 + in.b + M, sh.ny)};
     if ((z.z - (z.x & ~3)) + 4 + 2 > kTbSW - 2 || z.w - z.y > kTbH) return FDTD_OK;
     zone[k] = z;
@@ -1078,21 +1115,84 @@ int plan_tb(fdtd_ctx* ctx) {
         return FDTD_OK;
     }
   ctx->tb_base.assign(ctx->sims.size(), 0);
-  for (int s = 0; s < (int)ctx->sims.size(); ++s) {
-    const SimHost& sh = ctx->sims[s];
-    ctx->tb_base[s] = (int)ctx->tb_tiles.size();
-    for (int y0 = 0; y0 < sh.ny; y0 += kTbH)
-      for (int x0 = 0; x0 < sh.nx; x0 += kTbW) {
-        TbTile t{s, x0, std::min(x0 + kTbW, sh.nx), y0, std::min(y0 + kTbH, sh.ny), -1, 0, 0, 0, 0, 0, 0};
-        t.zone_b = (int)ctx->tb_zones.size();
-        for (size_t k = 0; k < ctx->insts.size(); ++k) {
-          if (ctx->insts[k].sim != s) continue;
-          const int4 z = zone[k];
-          if (z.x < t.x1 && z.z > t.x0 && z.y < t.y1 && z.w > t.y0) ctx->tb_zones.push_back(z);
+  if (march) {
+    // kMarchCols x th tiles; th fills whole waves of resident CTAs:
+    // minimise ceil(T / slots) * (th + 3) (three rows of sub-step halo).
+    // The model tiles run beside the first wave; each takes the registers
+    // of two of this kernel's CTAs, so those slots are left to them.
+    int dev = 0, nsm = 1, occ = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, yee_tb2m_kernel, 128, 0);
+    const long long slots =
+        std::max((long long)nsm, (long long)nsm * std::max(occ, 1) - 2 * (long long)ctx->insts.size());
+    auto tiles_for = [&](int th) {
+      long long t = 0;
+      for (const SimHost& sh : ctx->sims)
+        t += (long long)((sh.nx + kMarchCols - 1) / kMarchCols) * ((sh.ny + th - 1) / th);
+      return t;
+    };
+    int th = 8;
+    long long best = -1;
+    for (int h = 8; h <= 2048; ++h) {
+      const long long cost = ((tiles_for(h) + slots - 1) / slots) * (h + 3);
+      if (best < 0 || cost < best) best = cost, th = h;
+    }
+    if (const char* er = getenv("FDTD_TB_ROWS")) th = std::min(4096, std::max(4, atoi(er)));
+    ctx->tbm_pf = 0;
+    if (const char* ep = getenv("FDTD_TB_PF")) ctx->tbm_pf = std::min(16, std::max(0, atoi(ep)));
+    ctx->tbm_th = th;
+    for (int s = 0; s < (int)ctx->sims.size(); ++s) {
+      const SimHost& sh = ctx->sims[s];
+      ctx->tb_base[s] = (int)ctx->tbm_tiles.size();
+      for (int y0 = 0; y0 < sh.ny; y0 += th)
+        for (int x0 = 0; x0 < sh.nx; x0 += kMarchCols) {
+          const TileWork t{s, x0, y0, std::min(y0 + th, sh.ny)};
+          int2 zr{(int)ctx->tbm_zones.size(), 0};
+          for (size_t k = 0; k < ctx->insts.size(); ++k) {
+            if (ctx->insts[k].sim != s) continue;
+            const int4 z = zone[k];
+            if (z.x < x0 + kMarchCols && z.z > x0 && z.y < t.y1 && z.w > t.y0) ctx->tbm_zones.push_back(z);
+          }
+          zr.y = (int)ctx->tbm_zones.size();
+          ctx->tbm_tiles.push_back(t);
+          ctx->tbm_zone_rng.push_back(zr);
         }
-        t.zone_e = (int)ctx->tb_zones.size();
-        ctx->tb_tiles.push_back(t);
-      }
+    }
+    cudaFree(ctx->tbm_tiles_d);
+    cudaFree(ctx->tbm_zone_rng_d);
+    cudaFree(ctx->tbm_zones_d);
+    ctx->tbm_tiles_d = nullptr;
+    ctx->tbm_zone_rng_d = nullptr;
+    ctx->tbm_zones_d = nullptr;
+    const size_t nt = ctx->tbm_tiles.size();
+    CK(cudaMalloc(&ctx->tbm_tiles_d, sizeof(TileWork) * nt));
+    CK(cudaMemcpy(ctx->tbm_tiles_d, ctx->tbm_tiles.data(), sizeof(TileWork) * nt, cudaMemcpyHostToDevice));
+    CK(cudaMalloc(&ctx->tbm_zone_rng_d, sizeof(int2) * nt));
+    CK(cudaMemcpy(ctx->tbm_zone_rng_d, ctx->tbm_zone_rng.data(), sizeof(int2) * nt, cudaMemcpyHostToDevice));
+    CK(cudaMalloc(&ctx->tbm_zones_d, sizeof(int4) * std::max<size_t>(ctx->tbm_zones.size(), 1)));
+    if (!ctx->tbm_zones.empty())
+      CK(cudaMemcpy(ctx->tbm_zones_d, ctx->tbm_zones.data(), sizeof(int4) * ctx->tbm_zones.size(),
+                    cudaMemcpyHostToDevice));
+    if (!ctx->tbm_d) CK(cudaMalloc(&ctx->tbm_d, sizeof(TbMarchDev)));
+    ctx->tb_march = true;
+  } else {
+    for (int s = 0; s < (int)ctx->sims.size(); ++s) {
+      const SimHost& sh = ctx->sims[s];
+      ctx->tb_base[s] = (int)ctx->tb_tiles.size();
+      for (int y0 = 0; y0 < sh.ny; y0 += kTbH)
+        for (int x0 = 0; x0 < sh.nx; x0 += kTbW) {
+          TbTile t{s, x0, std::min(x0 + kTbW, sh.nx), y0, std::min(y0 + kTbH, sh.ny), -1, 0, 0, 0, 0, 0, 0};
+          t.zone_b = (int)ctx->tb_zones.size();
+          for (size_t k = 0; k < ctx->insts.size(); ++k) {
+            if (ctx->insts[k].sim != s) continue;
+            const int4 z = zone[k];
+            if (z.x < t.x1 && z.z > t.x0 && z.y < t.y1 && z.w > t.y0) ctx->tb_zones.push_back(z);
+          }
+          t.zone_e = (int)ctx->tb_zones.size();
+          ctx->tb_tiles.push_back(t);
+        }
+    }
   }
   for (size_t k = 0; k < ctx->insts.size(); ++k) {
     const int4 z = zone[k];
@@ -1376,15 +1476,35 @@ int prepare_run(fdtd_ctx* ctx, long long nsteps, const fdtd_source* src, int nsr
     std::vector<std::vector<SrcEdge>> ts(nt);
     std::vector<std::vector<int>> tp(nt);
     const int first_rom_tile = nt - (int)ctx->insts.size();
+    const int nw = ctx->tb_march ? 4 * (int)ctx->tbm_tiles.size() : 0;
+    std::vector<std::vector<MarchSrc>> ms(nw);
+    std::vector<std::vector<MarchPrb>> mq(nw);
+    const int th = ctx->tbm_th;
     for (const SrcEdge& e : edges) {
       const SimHost& sh = ctx->sims[e.sim];
-      const int ncx = (sh.nx + kTbW - 1) / kTbW, ncy = (sh.ny + kTbH - 1) / kTbH;
-      for (int ty = std::max(0, (e.j - 1) / kTbH); ty <= std::min(ncy - 1, (e.j + 1) / kTbH); ++ty)
-        for (int tx = std::max(0, (e.i - 1) / kTbW); tx <= std::min(ncx - 1, (e.i + 1) / kTbW); ++tx) {
-          const int t = ctx->tb_base[e.sim] + ty * ncx + tx;
-          const TbTile& tt = ctx->tb_tiles[t];
-          if (e.i >= tt.x0 - 1 && e.i <= tt.x1 && e.j >= tt.y0 - 1 && e.j <= tt.y1) ts[t].push_back(e);
+      if (ctx->tb_march) {
+        // every warp whose computed columns [c0 - 4, c0 + 124) and rows
+        // [max(y0 - 2, 0), min(y1, ny)] hold the edge; c0 = 120 k
+        const int ncx = (sh.nx + kMarchCols - 1) / kMarchCols, ncy = (sh.ny + th - 1) / th;
+        for (int ty = std::max(0, e.j / th - 1); ty <= std::min(ncy - 1, (e.j + 2) / th); ++ty) {
+          const int y0 = ty * th, y1 = std::min(y0 + th, sh.ny);
+          if (e.j < std::max(y0 - 2, 0) || e.j > std::min(y1, sh.ny)) continue;
+          for (int k = std::max(0, (e.i + 4) / kMarchOut - 1); k <= (e.i + 4) / kMarchOut; ++k) {
+            const int c0 = kMarchOut * k;
+            if (c0 >= sh.nx || e.i < c0 - 4 || e.i >= c0 + 124) continue;
+            const int t = ctx->tb_base[e.sim] + ty * ncx + k / 4;
+            ms[4 * t + k % 4].push_back({e.j, e.i, e.comp | (e.src << 1), 0.f});
+          }
         }
+      } else {
+        const int ncx = (sh.nx + kTbW - 1) / kTbW, ncy = (sh.ny + kTbH - 1) / kTbH;
+        for (int ty = std::max(0, (e.j - 1) / kTbH); ty <= std::min(ncy - 1, (e.j + 1) / kTbH); ++ty)
+          for (int tx = std::max(0, (e.i - 1) / kTbW); tx <= std::min(ncx - 1, (e.i + 1) / kTbW); ++tx) {
+            const int t = ctx->tb_base[e.sim] + ty * ncx + tx;
+            const TbTile& tt = ctx->tb_tiles[t];
+            if (e.i >= tt.x0 - 1 && e.i <= tt.x1 && e.j >= tt.y0 - 1 && e.j <= tt.y1) ts[t].push_back(e);
+          }
+      }
       for (int t = first_rom_tile; t < nt; ++t) {
         const TbTile& tt = ctx->tb_tiles[t];
         if (tt.sim == e.sim && e.i >= tt.x0 - 1 && e.i <= tt.x1 && e.j >= tt.y0 - 1 && e.j <= tt.y1)
@@ -1398,11 +1518,18 @@ int prepare_run(fdtd_ctx* ctx, long long nsteps, const fdtd_source* src, int nsr
         const TbTile& tt = ctx->tb_tiles[t];
         if (tt.sim == sim && i >= tt.x0 && i < tt.x1 && j >= tt.y0 && j < tt.y1) owner = t;
       }
-      if (owner < 0) {
-        const SimHost& sh = ctx->sims[sim];
-        owner = ctx->tb_base[sim] + (j / kTbH) * ((sh.nx + kTbW - 1) / kTbW) + i / kTbW;
+      if (owner >= 0) {
+        tp[owner].push_back(p);
+        continue;
       }
-      tp[owner].push_back(p);
+      const SimHost& sh = ctx->sims[sim];
+      if (ctx->tb_march) {
+        const int ncx = (sh.nx + kMarchCols - 1) / kMarchCols;
+        const int t = ctx->tb_base[sim] + (j / th) * ncx + i / kMarchCols;
+        mq[4 * t + (i % kMarchCols) / kMarchOut].push_back({j, i, p, 0});
+      } else {
+        tp[ctx->tb_base[sim] + (j / kTbH) * ((sh.nx + kTbW - 1) / kTbW) + i / kTbW].push_back(p);
+      }
     }
     std::vector<SrcEdge> fs;
     std::vector<int> fp;
@@ -1417,17 +1544,53 @@ int prepare_run(fdtd_ctx* ctx, long long nsteps, const fdtd_source* src, int nsr
     }
     CK(ctx->tb_src.reserve(fs.size()));
     CK(ctx->tb_prb.reserve(fp.size()));
-    if (!ctx->tb_tiles_d || ctx->tb_tiles_cap < ctx->tb_tiles.size()) {
+    if (nt > 0 && (!ctx->tb_tiles_d || ctx->tb_tiles_cap < ctx->tb_tiles.size())) {
       cudaFree(ctx->tb_tiles_d);
       ctx->tb_tiles_d = nullptr;
       CK(cudaMalloc(&ctx->tb_tiles_d, sizeof(TbTile) * ctx->tb_tiles.size()));
       ctx->tb_tiles_cap = ctx->tb_tiles.size();
     }
-    CK(cudaMemcpyAsync(ctx->tb_tiles_d, ctx->tb_tiles.data(), sizeof(TbTile) * nt, cudaMemcpyHostToDevice, st));
+    if (nt > 0) CK(cudaMemcpyAsync(ctx->tb_tiles_d, ctx->tb_tiles.data(), sizeof(TbTile) * nt, cudaMemcpyHostToDevice, st));
     if (!fs.empty()) CK(cudaMemcpyAsync(ctx->tb_src.p, fs.data(), sizeof(SrcEdge) * fs.size(), cudaMemcpyHostToDevice, st));
     if (!fp.empty()) CK(cudaMemcpyAsync(ctx->tb_prb.p, fp.data(), sizeof(int) * fp.size(), cudaMemcpyHostToDevice, st));
     TbRun tr{ctx->tb_zones_d, ctx->tb_src.p, ctx->tb_prb.p};
     CK(cudaMemcpyAsync(ctx->tb_run_d, &tr, sizeof(TbRun), cudaMemcpyHostToDevice, st));
+    if (ctx->tb_march) {   // per-warp lists, rows ascending
+      std::vector<int2> srng(nw), prng(nw);
+      std::vector<MarchSrc> fms;
+      std::vector<MarchPrb> fmq;
+      std::vector<int> fsim;
+      for (int w = 0; w < nw; ++w) {
+        std::stable_sort(ms[w].begin(), ms[w].end(), [](const MarchSrc& a, const MarchSrc& b) {
+          return a.j != b.j ? a.j < b.j : (a.cs & 1) < (b.cs & 1);
+        });
+        std::stable_sort(mq[w].begin(), mq[w].end(), [](const MarchPrb& a, const MarchPrb& b) { return a.j < b.j; });
+        srng[w] = make_int2((int)fms.size(), (int)(fms.size() + ms[w].size()));
+        fms.insert(fms.end(), ms[w].begin(), ms[w].end());
+        fsim.insert(fsim.end(), ms[w].size(), ctx->tbm_tiles[w / 4].sim);
+        prng[w] = make_int2((int)fmq.size(), (int)(fmq.size() + mq[w].size()));
+        fmq.insert(fmq.end(), mq[w].begin(), mq[w].end());
+      }
+      CK(ctx->tbm_src_rng.reserve(nw));
+      CK(ctx->tbm_prb_rng.reserve(nw));
+      CK(ctx->tbm_src.reserve(fms.size()));
+      CK(ctx->tbm_prb.reserve(fmq.size()));
+      CK(cudaMemcpyAsync(ctx->tbm_src_rng.p, srng.data(), sizeof(int2) * nw, cudaMemcpyHostToDevice, st));
+      CK(cudaMemcpyAsync(ctx->tbm_prb_rng.p, prng.data(), sizeof(int2) * nw, cudaMemcpyHostToDevice, st));
+      CK(ctx->tbm_ent_sim.reserve(fsim.size()));
+      if (!fms.empty()) {
+        CK(cudaMemcpyAsync(ctx->tbm_src.p, fms.data(), sizeof(MarchSrc) * fms.size(), cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(ctx->tbm_ent_sim.p, fsim.data(), sizeof(int) * fsim.size(), cudaMemcpyHostToDevice, st));
+        const int ne = (int)fms.size();
+        march_src_cb_kernel<<<(ne + 127) / 128, 128, 0, st>>>(ctx->sims_d, ctx->tbm_ent_sim.p, ctx->tbm_src.p, ne);
+        CK(cudaGetLastError());
+      }
+      if (!fmq.empty())
+        CK(cudaMemcpyAsync(ctx->tbm_prb.p, fmq.data(), sizeof(MarchPrb) * fmq.size(), cudaMemcpyHostToDevice, st));
+      const TbMarchDev tmd{ctx->tbm_src_rng.p, ctx->tbm_src.p, ctx->tbm_prb_rng.p, ctx->tbm_prb.p,
+                           ctx->tbm_zone_rng_d, ctx->tbm_zones_d};
+      CK(cudaMemcpyAsync(ctx->tbm_d, &tmd, sizeof(TbMarchDev), cudaMemcpyHostToDevice, st));
+    }
   }
   RunDev rd{};
   rd.base = 0;
@@ -1484,7 +1647,7 @@ int march_timed(fdtd_ctx* ctx, long long nsteps, int nprobe) {
     ctx->ev.push_back(e);
   }
   long long t = 0;
-  if (ctx->tb && ctx->dft_nmon == 0) {   // pairs of steps in one stencil launch; n_yee counts steps
+  if (ctx->tb && ctx->dft_nmon == 0) {   // pairs of steps in one stencil launch
     for (; t + 2 <= nsteps; t += 2) {
       const int par = ctx->cur ^ (int)(t & 1);
       cudaEvent_t* e = &ctx->ev[ctx->ev_used];
@@ -1494,7 +1657,7 @@ int march_timed(fdtd_ctx* ctx, long long nsteps, int nprobe) {
       CK(cudaEventRecord(e[2], ctx->stream));
       advance_kernel<<<1, 32, 0, ctx->stream>>>(ctx->run_d, 2);
       CK(cudaGetLastError());
-      ctx->n_yee += 2;
+      ctx->n_yee += 1;   // one launch of two steps
       ctx->ev_used += 3;
       if (ctx->ev_used == (int)ctx->ev.size()) {
         int rc = drain_events(ctx);
@@ -1531,8 +1694,14 @@ int march_timed(fdtd_ctx* ctx, long long nsteps, int nprobe) {
 }
 
 void launch_tb(fdtd_ctx* ctx, cudaStream_t s, int par, int c) {
-  yee_tb2_kernel<<<(unsigned)ctx->tb_tiles.size(), kTbThreads, kTbSmemFields, s>>>(
-      ctx->sims_d, ctx->tb_tiles_d, ctx->insts_d, ctx->run_d, ctx->tb_run_d, par, c);
+  const unsigned ntb = (unsigned)ctx->tb_tiles.size();
+  if (ntb > 0)
+    yee_tb2_kernel<<<ntb, kTbThreads, kTbSmemFields, s>>>(ctx->sims_d, ctx->tb_tiles_d, ctx->insts_d, ctx->run_d,
+                                                          ctx->tb_run_d, par, c);
+  if (ctx->tb_march)   // overlaps the model tiles (programmatic serialisation) when there are any
+    launch_k(yee_tb2m_kernel, (unsigned)ctx->tbm_tiles.size(), 128, 0, s, ctx->pdl && ntb > 0,
+             (const SimDev*)ctx->sims_d, (const TileWork*)ctx->tbm_tiles_d, (const RunDev*)ctx->run_d,
+             (const TbMarchDev*)ctx->tbm_d, par, c, ctx->tbm_pf);
 }
 
 int ensure_tb_graph(fdtd_ctx* ctx, int par, int nprobe) {
@@ -1741,6 +1910,15 @@ void fdtd_destroy(fdtd_ctx* ctx) {
   cudaFree(ctx->tb_run_d);
   ctx->tb_src.release();
   ctx->tb_prb.release();
+  cudaFree(ctx->tbm_tiles_d);
+  cudaFree(ctx->tbm_zone_rng_d);
+  cudaFree(ctx->tbm_zones_d);
+  cudaFree(ctx->tbm_d);
+  ctx->tbm_src_rng.release();
+  ctx->tbm_ent_sim.release();
+  ctx->tbm_prb_rng.release();
+  ctx->tbm_src.release();
+  ctx->tbm_prb.release();
   cudaFree(ctx->run_d);
   cudaFree(ctx->status_d);
   cudaFree(ctx->einst_d);
@@ -2186,6 +2364,11 @@ int fdtd_set_timing(fdtd_ctx* ctx, int on) {
   ctx->n_yee = ctx->n_post = 0;
   ctx->ev_used = 0;
   return FDTD_OK;
+}
+
+int fdtd_steps_per_launch(const fdtd_ctx* ctx) {
+  if (!ctx) return set_global_error(FDTD_EINVAL, "fdtd_steps_per_launch: null context");
+  return ctx->tb ? 2 : 1;
 }
 
 int fdtd_get_kernel_times(fdtd_ctx* ctx, double* yee_ms, long long* yee_launches, double* post_ms,

@@ -89,6 +89,7 @@ yee_tb2_kernel(const SimDev* __restrict__ sims, const TbTile* __restrict__ tiles
   float* sEy = sEx + kTbSH * kTbSW;
   float* sHz = sEy + kTbSH * kTbSW;
   float2* sM = reinterpret_cast<float2*>(sHz + kTbSH * kTbSW);
+  pdl_trigger();   // the row-marching kernel of the same two steps may start
   const TbTile tt = tiles[blockIdx.x];
   const SimDev sd = sims[tt.sim];
   const int nx = sd.nx, ny = sd.ny, P = sd.pitch;

@@ -1,6 +1,9 @@
-"""The opt-in two-steps-per-launch path (FDTD_TB=1): the parity cases of the
-one-step path rerun through it against the FP64 oracle, and the two paths
-against each other on the same inputs."""
+"""The two-steps-per-pass path (FDTD_TB=1; chosen by default where the
+model tiles take a small share of a wave) in both forms (the
+row-marching kernel with model tiles, and FDTD_TB_SMEM=1 shared-memory
+tiles): the parity cases of the one-step path rerun through it against the
+FP64 oracle, and the paths against each other on the same inputs (the
+row-marching form bit for bit: it uses the one-step kernel's operations)."""
 import numpy as np
 import pytest
 
@@ -14,9 +17,10 @@ import test_gpu_parity as tp
 pytestmark = pytest.mark.gpu
 
 
-@pytest.fixture
-def tb_on(monkeypatch):
+@pytest.fixture(params=["march", "smem"])
+def tb_on(monkeypatch, request):
     monkeypatch.setenv("FDTD_TB", "1")
+    monkeypatch.setenv("FDTD_TB_SMEM", "1" if request.param == "smem" else "0")
 
 
 @pytest.mark.parametrize("case", [
@@ -33,6 +37,7 @@ def test_parity_case_through_two_step_path(tb_on, case):
 
 
 def test_two_step_path_agrees_with_one_step_path(monkeypatch):
+    monkeypatch.setenv("FDTD_TB_SMEM", "1")
     w = workloads.random_grid(7, 700, 150, 3, 6, 3, 40, 301, n_probes=12)
     for rd in w["roms"]:
         w["probes"] += [(rd["i0"] - 1, rd["j0"]), (rd["i0"] + rd["a"], rd["j0"] + rd["b"] - 1)]
@@ -44,3 +49,78 @@ def test_two_step_path_agrees_with_one_step_path(monkeypatch):
     assert tp.rel_l2(res["1"][0], res["0"][0]) < 1e-6
     for a, b in zip(res["1"][1], res["0"][1]):
         assert tp.rel_l2(a, b) < 1e-6
+
+
+def _covered(w, i, j, pad=1):
+    return any(rd["i0"] - pad <= i < rd["i0"] + rd["a"] + pad and rd["j0"] - pad <= j < rd["j0"] + rd["b"] + pad
+               for rd in w["roms"])
+
+
+def _boundary_workloads(nsteps):
+    """Two grids (same r, so the same dt) with probes on both sides of the
+    120-column strip and 480-column tile boundaries, a Jy line source along a
+    strip boundary and an Ex point source, models placed at random (their
+    zones straddle strips and tiles; 12 cells apart, so that no model is
+    within reach of another's tile and the two-step path is taken)."""
+    ws = [workloads.random_grid(21, 1000, 300, 5, 6, 3, 40, nsteps, n_probes=6, margin=12),
+          workloads.random_grid(22, 250, 470, 3, 5, 3, 30, nsteps, n_probes=6, margin=12)]
+    g = np.random.default_rng(5)
+    for w in ws:
+        for c0 in range(120, w["nx"] - 1, 120):
+            for i in (c0 - 2, c0 - 1, c0, c0 + 1):
+                j = int(g.integers(1, w["ny"] - 1))
+                if 0 <= i < w["nx"] and not _covered(w, i, j):
+                    w["probes"].append((i, j))
+        wave = w["sources"][0]["wave"]
+        for x in (480, 479, 240, 241, 120):
+            if x < w["nx"] and not any(_covered(w, x, j) or _covered(w, x - 1, j) for j in range(w["ny"])):
+                w["sources"].append(dict(comp=1, i=x, j=0, len=w["ny"], wave=0.5 * wave))
+                break
+        for (i, j) in ((361, 17), (100, 34), (479, 51)):
+            if i < w["nx"] and j < w["ny"] and not (_covered(w, i, j) or _covered(w, i, j - 1)):
+                w["sources"].append(dict(comp=0, i=i, j=j, len=1, wave=-0.25 * wave))
+    return ws
+
+
+@pytest.mark.parametrize("rows", ["17", "auto"])
+def test_row_marching_form_is_bit_identical_to_one_step(monkeypatch, rows):
+    """Probe series and final fields of the row-marching two-step form equal
+    the one-step path bit for bit over an odd step count (a trailing single
+    step), for many row tiles (17 rows) and the automatic plan."""
+    n = 203
+    ws = _boundary_workloads(n)
+    res = {}
+    for tb in ("0", "1"):
+        monkeypatch.setenv("FDTD_TB", tb)
+        monkeypatch.setenv("FDTD_TB_SMEM", "0")
+        if rows == "auto":
+            monkeypatch.delenv("FDTD_TB_ROWS", raising=False)
+        else:
+            monkeypatch.setenv("FDTD_TB_ROWS", rows)
+        ctx, _ = tp.gpu_context(ws)
+        out = tp.gpu_run(ctx, ws, n)
+        res[tb] = (out, [ctx.get_fields(s) for s in range(len(ws))])
+    assert np.abs(res["0"][0]).max() > 0
+    assert np.array_equal(res["1"][0], res["0"][0])
+    for fa, fb in zip(res["1"][1], res["0"][1]):
+        for a, b in zip(fa, fb):
+            assert np.array_equal(a, b)
+
+
+def test_default_choice_of_the_two_step_path(monkeypatch):
+    """Unset FDTD_TB: the benchmark grid (8 models) steps in pairs, the
+    64-model lattice singly; FDTD_TB=0 / 1 force the choice."""
+    import paper_1609_07114_gb300 as pg
+    import test_gpu_lattice as tl
+    monkeypatch.delenv("FDTD_TB", raising=False)
+    w = workloads.random_grid(1, 1024, 1024, 8, 16, 4, 200, 10)
+    ctx, _ = tp.gpu_context([w])
+    assert ctx.steps_per_launch() == 2
+    wl = workloads.lattice_8192(10, n=2048, pitch=256)
+    ctxl, _ = tl.lattice_context(wl)
+    assert len(wl["roms"]) == 64 and ctxl.steps_per_launch() == 1
+    monkeypatch.setenv("FDTD_TB", "0")
+    assert tp.gpu_context([w])[0].steps_per_launch() == 1
+    monkeypatch.setenv("FDTD_TB", "1")
+    assert tl.lattice_context(wl)[0].steps_per_launch() == 2
+
