@@ -1008,6 +1008,7 @@ struct fdtd_ctx {
   DevBuf<MarchPrb> tbm_prb;
   int tbm_th = 0;
   int tbm_pf = 0;                  // rows prefetched into L2 ahead of the loads (FDTD_TB_PF)
+  int tbm_mb = 4;                  // resident CTAs per SM the kernel is compiled for (FDTD_TB_MB)
   // measurement mode (fdtd_set_timing)
   bool timing = false;
   std::vector<cudaEvent_t> ev;
@@ -1091,7 +1092,7 @@ int plan_tb(fdtd_ctx* ctx) {
     int dev = 0, nsm = 1, occ = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, yee_tb2m_kernel, 128, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, yee_tb2m_kernel<4>, 128, 0);
     if (16 * (long long)ctx->insts.size() > (long long)nsm * std::max(occ, 1)) return FDTD_OK;
   }
   const int M = kTbZoneMargin;
@@ -1123,7 +1124,14 @@ int plan_tb(fdtd_ctx* ctx) {
     int dev = 0, nsm = 1, occ = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, yee_tb2m_kernel, 128, 0);
+    // compiled for 4 resident CTAs (128 registers, no spills; measured 300.7
+    // against 280.1 Gcell-steps/s for 3 CTAs at 162 registers, 4096^2)
+    ctx->tbm_mb = 4;
+    if (const char* em = getenv("FDTD_TB_MB")) ctx->tbm_mb = atoi(em) == 3 ? 3 : 4;
+    if (ctx->tbm_mb == 4)
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, yee_tb2m_kernel<4>, 128, 0);
+    else
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, yee_tb2m_kernel<3>, 128, 0);
     const long long slots =
         std::max((long long)nsm, (long long)nsm * std::max(occ, 1) - 2 * (long long)ctx->insts.size());
     auto tiles_for = [&](int th) {
@@ -1699,9 +1707,9 @@ void launch_tb(fdtd_ctx* ctx, cudaStream_t s, int par, int c) {
     yee_tb2_kernel<<<ntb, kTbThreads, kTbSmemFields, s>>>(ctx->sims_d, ctx->tb_tiles_d, ctx->insts_d, ctx->run_d,
                                                           ctx->tb_run_d, par, c);
   if (ctx->tb_march)   // overlaps the model tiles (programmatic serialisation) when there are any
-    launch_k(yee_tb2m_kernel, (unsigned)ctx->tbm_tiles.size(), 128, 0, s, ctx->pdl && ntb > 0,
-             (const SimDev*)ctx->sims_d, (const TileWork*)ctx->tbm_tiles_d, (const RunDev*)ctx->run_d,
-             (const TbMarchDev*)ctx->tbm_d, par, c, ctx->tbm_pf);
+    launch_k(ctx->tbm_mb == 4 ? yee_tb2m_kernel<4> : yee_tb2m_kernel<3>, (unsigned)ctx->tbm_tiles.size(), 128, 0, s,
+             ctx->pdl && ntb > 0, (const SimDev*)ctx->sims_d, (const TileWork*)ctx->tbm_tiles_d,
+             (const RunDev*)ctx->run_d, (const TbMarchDev*)ctx->tbm_d, par, c, ctx->tbm_pf);
 }
 
 int ensure_tb_graph(fdtd_ctx* ctx, int par, int nprobe) {

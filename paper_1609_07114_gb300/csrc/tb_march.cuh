@@ -130,7 +130,8 @@ __device__ __forceinline__ float pick4(const float (&v)[4], int t) {
   return t == 0 ? v[0] : (t == 1 ? v[1] : (t == 2 ? v[2] : v[3]));
 }
 
-__global__ void __launch_bounds__(128, 3)
+template <int kMinBlocks>
+__global__ void __launch_bounds__(128, kMinBlocks)
 yee_tb2m_kernel(const SimDev* __restrict__ sims, const TileWork* __restrict__ tiles,
                 const RunDev* __restrict__ run, const TbMarchDev* __restrict__ tm, int par, int c, int pf) {
   const unsigned FULL = 0xffffffffu;
@@ -212,21 +213,21 @@ yee_tb2m_kernel(const SimDev* __restrict__ sims, const TileWork* __restrict__ ti
       qa = march_prb_at(tm->prb, ++pA, pr.y);
     }
     // ---- A.Ex: Ex^{n+1}(j), edges between cells (i, j-1) and (i, j) (Eq. (3))
+    // (branch-free: the coefficients are formed for every edge and the
+    // update selected where the edge is updated; the carried coefficients of
+    // edges that are not are never used)
     float xa[4], nxa[4], nxr[4];
     unsigned nmask = 0;
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
-      float v = exc[t];
-      nxa[t] = nxr[t] = 0.f;
-      if (j >= 1 && cl + t < nx && mp[t].x >= 0.f && m[t].x >= 0.f) {
-        float ca, cb;
-        edge_coef(mp[t], m[t], ca, cb);
-        nxa[t] = ca;
-        nxr[t] = __fmul_rn(cb, sd.rdy);
-        v = __fmaf_rn(ca, v, __fmul_rn(nxr[t], __fsub_rn(hn[t], hzp[t])));
-        nmask |= 1u << t;
-      }
-      xa[t] = v;
+      float ca, cb;
+      edge_coef(mp[t], m[t], ca, cb);
+      nxa[t] = ca;
+      nxr[t] = __fmul_rn(cb, sd.rdy);
+      const float v = __fmaf_rn(ca, exc[t], __fmul_rn(nxr[t], __fsub_rn(hn[t], hzp[t])));
+      const bool upd = j >= 1 && cl + t < nx && mp[t].x >= 0.f && m[t].x >= 0.f;
+      xa[t] = upd ? v : exc[t];
+      nmask |= upd ? 1u << t : 0u;
     }
     while (sa.j == j && (sa.cs & 1) == 0) {
       samples(sa.cs);
@@ -290,17 +291,14 @@ yee_tb2m_kernel(const SimDev* __restrict__ sims, const TileWork* __restrict__ ti
       const int i = cl + t;
       const float2 ml = t == 0 ? mL : m[t - 1];
       const float hl = t == 0 ? hl0 : hn[t - 1];
-      float v = eyA[t];
-      nya[t] = nyr[t] = 0.f;
-      if (i >= 1 && i < nx && ml.x >= 0.f && m[t].x >= 0.f) {
-        float ca, cb;
-        edge_coef(ml, m[t], ca, cb);
-        nya[t] = ca;
-        nyr[t] = __fmul_rn(cb, sd.rdx);
-        v = __fmaf_rn(ca, v, -__fmul_rn(nyr[t], __fsub_rn(hn[t], hl)));
-        nmask |= 16u << t;
-      }
-      ya[t] = v;
+      float ca, cb;
+      edge_coef(ml, m[t], ca, cb);
+      nya[t] = ca;
+      nyr[t] = __fmul_rn(cb, sd.rdx);
+      const float v = __fmaf_rn(ca, eyA[t], -__fmul_rn(nyr[t], __fsub_rn(hn[t], hl)));
+      const bool upd = i >= 1 && i < nx && ml.x >= 0.f && m[t].x >= 0.f;
+      ya[t] = upd ? v : eyA[t];
+      nmask |= upd ? 16u << t : 0u;
     }
     while (sa.j == j) {
       samples(sa.cs);
