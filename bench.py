@@ -660,7 +660,8 @@ def main():
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": traffic, "peak_kind": kind,
                      "kernel": kernel, "kernel_avg_ms": yee_avg_s * 1e3, "steps_per_launch": spl,
-                     "alg_bytes_per_launch": alg_bytes, "rom_post_avg_ms": post_ms / max(n_post, 1)},
+                     "alg_bytes_per_launch": alg_bytes,
+                     "rom_post_avg_ms": post_ms / n_post if n_post else None},
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": K * launches_per_run,

@@ -1079,9 +1079,13 @@ int plan_tb(fdtd_ctx* ctx) {
   ctx->tbm_zone_rng.clear();
   ctx->tbm_zones.clear();
   // FDTD_TB=0: off; 1: on wherever it applies; unset: the row-marching form
-  // where it applies and the model tiles take at most 1/8 of the slots of a
-  // wave (otherwise the one-step kernel, whose sparse-material path and four
-  // resident CTAs per SM win: measured on the 64-model lattice)
+  // where it applies, the model tiles take at most 1/8 of the slots of a
+  // wave, and the march over the cells outlasts the slowest model tile
+  // (otherwise the one-step kernels win: the 64-model lattice, with its
+  // sparse-material path, and small grids, where one CTA stepping a model
+  // twice takes longer than the whole march).  Time estimates measured on
+  // GB300: the march 6.6 ps per cell and pair of steps; a model tile
+  // 0.6 ns per element of [P | Q] plus 5 us.
   const char* e = getenv("FDTD_TB");
   const int mode = e ? atoi(e) : -1;
   if (mode == 0) return FDTD_OK;
@@ -1094,6 +1098,10 @@ int plan_tb(fdtd_ctx* ctx) {
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, yee_tb2m_kernel<4>, 128, 0);
     if (16 * (long long)ctx->insts.size() > (long long)nsm * std::max(occ, 1)) return FDTD_OK;
+    double cells = 0, zone_us = 0;
+    for (const SimHost& sh : ctx->sims) cells += (double)sh.nx * sh.ny;
+    for (const Instance& in : ctx->insts) zone_us = std::max(zone_us, 0.6e-3 * in.n * (double)in.map->ld + 5.0);
+    if (cells * 6.6e-6 < 1.25 * zone_us) return FDTD_OK;
   }
   const int M = kTbZoneMargin;
   std::vector<int4> zone(ctx->insts.size());

@@ -108,14 +108,18 @@ def test_row_marching_form_is_bit_identical_to_one_step(monkeypatch, rows):
 
 
 def test_default_choice_of_the_two_step_path(monkeypatch):
-    """Unset FDTD_TB: the benchmark grid (8 models) steps in pairs, the
-    64-model lattice singly; FDTD_TB=0 / 1 force the choice."""
-    import paper_1609_07114_gb300 as pg
+    """Unset FDTD_TB: the benchmark grid (4096^2, 8 models) steps in pairs;
+    the 64-model lattice and a 1024^2 grid with the same 8 models (whose
+    model tiles would outlast the march) singly; FDTD_TB=0 / 1 force the
+    choice."""
     import test_gpu_lattice as tl
     monkeypatch.delenv("FDTD_TB", raising=False)
-    w = workloads.random_grid(1, 1024, 1024, 8, 16, 4, 200, 10)
+    w = workloads.grid_4096(10)
     ctx, _ = tp.gpu_context([w])
     assert ctx.steps_per_launch() == 2
+    ctx.close()
+    ws = workloads.random_grid(1, 1024, 1024, 8, 16, 4, 200, 10)
+    assert tp.gpu_context([ws])[0].steps_per_launch() == 1
     wl = workloads.lattice_8192(10, n=2048, pitch=256)
     ctxl, _ = tl.lattice_context(wl)
     assert len(wl["roms"]) == 64 and ctxl.steps_per_launch() == 1
