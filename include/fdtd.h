@@ -391,8 +391,10 @@ int fdtd_get_kernel_times(fdtd_ctx* ctx, double* yee_ms, long long* yee_launches
  * over the fields, each model's Eq. (23) evaluated between them in its own
  * tile; bit-identical to single steps), else 1.  Contexts with CPML layers
  * and runs with DFT monitors step singly.  FDTD_TB=0 / 1 in the environment
- * at context creation forces one or the other where the pair form applies;
- * unset, pairs are used where the model tiles take at most 1/8 of a wave.
+ * at context creation (kept for the context's life) forces one or the other
+ * where the pair form applies; unset, pairs are used where the model tiles
+ * take at most 1/8 of a wave and the pass over the cells outlasts the
+ * slowest model tile (re-decided whenever a model is embedded).
  * Returns FDTD_EINVAL for a null context. */
 int fdtd_steps_per_launch(const fdtd_ctx* ctx);
 

@@ -994,6 +994,7 @@ struct fdtd_ctx {
   int tb_graph_nprobe[2] = {-1, -1};
   // row-marching form of the two-step path (tb_march.cuh): ordinary areas in
   // yee_tb2m_kernel, tb_tiles then holds only the model tiles
+  int tb_mode = -1;                // FDTD_TB at creation: 0 off, 1 on where it applies, -1 automatic
   bool tb_march = false;
   std::vector<TileWork> tbm_tiles;
   std::vector<int2> tbm_zone_rng;
@@ -1086,8 +1087,7 @@ int plan_tb(fdtd_ctx* ctx) {
   // twice takes longer than the whole march).  Time estimates measured on
   // GB300: the march 6.6 ps per cell and pair of steps; a model tile
   // 0.6 ns per element of [P | Q] plus 5 us.
-  const char* e = getenv("FDTD_TB");
-  const int mode = e ? atoi(e) : -1;
+  const int mode = ctx->tb_mode;
   if (mode == 0) return FDTD_OK;
   if (!ctx->pml_cells.empty()) return FDTD_OK;   // the layers' corrections need the one-step form
   const char* es = getenv("FDTD_TB_SMEM");
@@ -2050,6 +2050,7 @@ int fdtd_create(const fdtd_grid_desc* g, void* cuda_stream, fdtd_ctx** out) {
     sd.rdx = (float)(1.0 / g->dx);
   }
   plan_tiles(ctx);
+  if (const char* e = getenv("FDTD_TB")) ctx->tb_mode = atoi(e) != 0 ? 1 : 0;   // fixed for the context
   if (plan_tb(ctx) != FDTD_OK) return bail(FDTD_ECUDA);
   if (cudaMalloc(&ctx->sims_d, sizeof(SimDev) * sdev.size()) != cudaSuccess ||
       cudaMalloc(&ctx->tiles_d, sizeof(TileWork) * ctx->tiles.size()) != cudaSuccess ||
