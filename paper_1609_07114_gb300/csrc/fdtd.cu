@@ -1080,13 +1080,17 @@ int plan_tb(fdtd_ctx* ctx) {
   ctx->tbm_zone_rng.clear();
   ctx->tbm_zones.clear();
   // FDTD_TB=0: off; 1: on wherever it applies; unset: the row-marching form
-  // where it applies, the model tiles take at most 1/8 of the slots of a
-  // wave, and the march over the cells outlasts the slowest model tile
-  // (otherwise the one-step kernels win: the 64-model lattice, with its
-  // sparse-material path, and small grids, where one CTA stepping a model
-  // twice takes longer than the whole march).  Time estimates measured on
-  // GB300: the march 6.6 ps per cell and pair of steps; a model tile
-  // 0.6 ns per element of [P | Q] plus 5 us.
+  // where it applies, unless (measured on GB300, against the one-step path)
+  //  - a model tile outlasts the march over the cells (small grids: one CTA
+  //    stepping a model twice takes longer than the whole march; estimates:
+  //    the march 6.6 ps per cell and pair of steps, a model tile 0.6 ns per
+  //    element of [P | Q] plus 5 us),
+  //  - fewer than half of the strip rows hold materials other than the
+  //    background (the one-step kernel's sparse-material path moves 24 B per
+  //    cell-step there: the 64-model lattice, 202.5 against 208.3),
+  //  - the model tiles alone would fill a wave.
+  // (4096^2 benchmark grid: 300.7 against 189.3 Gcell-steps/s; 256 uneven
+  // grids with 256 models: 203.1 against 182.3.)
   const int mode = ctx->tb_mode;
   if (mode == 0) return FDTD_OK;
   if (!ctx->pml_cells.empty()) return FDTD_OK;   // the layers' corrections need the one-step form
@@ -1097,11 +1101,18 @@ int plan_tb(fdtd_ctx* ctx) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, yee_tb2m_kernel<4>, 128, 0);
-    if (16 * (long long)ctx->insts.size() > (long long)nsm * std::max(occ, 1)) return FDTD_OK;
-    double cells = 0, zone_us = 0;
-    for (const SimHost& sh : ctx->sims) cells += (double)sh.nx * sh.ny;
+    if (2 * (long long)ctx->insts.size() > (long long)nsm * std::max(occ, 1)) return FDTD_OK;
+    double cells = 0, zone_us = 0, dense_rows = 0, strip_rows = 0;
+    for (const SimHost& sh : ctx->sims) {
+      cells += (double)sh.nx * sh.ny;
+      strip_rows += (double)sh.ny * sh.nstrip;
+      for (int j = 0; j < sh.ny; ++j)
+        for (int st = 0; st < sh.nstrip; ++st)
+          dense_rows += (sh.mbits[(size_t)(j >> 5) * sh.nstrip + st] >> (j & 31)) & 1u;
+    }
     for (const Instance& in : ctx->insts) zone_us = std::max(zone_us, 0.6e-3 * in.n * (double)in.map->ld + 5.0);
     if (cells * 6.6e-6 < 1.25 * zone_us) return FDTD_OK;
+    if (dense_rows < 0.5 * strip_rows) return FDTD_OK;
   }
   const int M = kTbZoneMargin;
   std::vector<int4> zone(ctx->insts.size());

@@ -36,6 +36,14 @@ def test_parity_case_through_two_step_path(tb_on, case):
     getattr(tp, case)()
 
 
+def test_full_batched_256_through_row_marching_form(monkeypatch):
+    """The 256-simulation batch in the benchmark's launch configuration
+    (two steps per launch, chosen automatically there), against the oracle."""
+    monkeypatch.setenv("FDTD_TB", "1")
+    monkeypatch.setenv("FDTD_TB_SMEM", "0")
+    tp.test_full_batched_256_sampled_simulations()
+
+
 def test_two_step_path_agrees_with_one_step_path(monkeypatch):
     monkeypatch.setenv("FDTD_TB_SMEM", "1")
     w = workloads.random_grid(7, 700, 150, 3, 6, 3, 40, 301, n_probes=12)
@@ -109,9 +117,9 @@ def test_row_marching_form_is_bit_identical_to_one_step(monkeypatch, rows):
 
 def test_default_choice_of_the_two_step_path(monkeypatch):
     """Unset FDTD_TB: the benchmark grid (4096^2, 8 models) steps in pairs;
-    the 64-model lattice and a 1024^2 grid with the same 8 models (whose
-    model tiles would outlast the march) singly; FDTD_TB=0 / 1 force the
-    choice."""
+    the 64-model lattice (mostly background material: the one-step kernel's
+    sparse path) and a 1024^2 grid with the same 8 models (whose model tiles
+    would outlast the march) singly; FDTD_TB=0 / 1 force the choice."""
     import test_gpu_lattice as tl
     monkeypatch.delenv("FDTD_TB", raising=False)
     w = workloads.grid_4096(10)
