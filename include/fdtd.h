@@ -392,9 +392,9 @@ int fdtd_get_kernel_times(fdtd_ctx* ctx, double* yee_ms, long long* yee_launches
  * tile; bit-identical to single steps), else 1.  Contexts with CPML layers
  * and runs with DFT monitors step singly.  FDTD_TB=0 / 1 in the environment
  * at context creation (kept for the context's life) forces one or the other
- * where the pair form applies; unset, pairs are used where the model tiles
- * take at most 1/8 of a wave and the pass over the cells outlasts the
- * slowest model tile (re-decided whenever a model is embedded).
+ * where the pair form applies; unset, pairs are used unless the slowest
+ * model tile outlasts the pass over the cells or most strip rows hold only
+ * the background material (re-decided whenever a model is embedded).
  * Returns FDTD_EINVAL for a null context. */
 int fdtd_steps_per_launch(const fdtd_ctx* ctx);
 

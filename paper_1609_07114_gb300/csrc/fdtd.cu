@@ -1087,21 +1087,16 @@ int plan_tb(fdtd_ctx* ctx) {
   //    element of [P | Q] plus 5 us),
   //  - fewer than half of the strip rows hold materials other than the
   //    background (the one-step kernel's sparse-material path moves 24 B per
-  //    cell-step there: the 64-model lattice, 202.5 against 208.3),
-  //  - the model tiles alone would fill a wave.
+  //    cell-step there: the 64-model lattice, 202.5 against 208.3).
   // (4096^2 benchmark grid: 300.7 against 189.3 Gcell-steps/s; 256 uneven
-  // grids with 256 models: 203.1 against 182.3.)
+  // grids with 1024 models, whose tiles take several waves beside the
+  // march: 203.1 against 182.3.)
   const int mode = ctx->tb_mode;
   if (mode == 0) return FDTD_OK;
   if (!ctx->pml_cells.empty()) return FDTD_OK;   // the layers' corrections need the one-step form
   const char* es = getenv("FDTD_TB_SMEM");
   const bool march = !(mode == 1 && es && atoi(es) == 1);
   if (mode != 1) {
-    int dev = 0, nsm = 1, occ = 1;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, yee_tb2m_kernel<4>, 128, 0);
-    if (2 * (long long)ctx->insts.size() > (long long)nsm * std::max(occ, 1)) return FDTD_OK;
     double cells = 0, zone_us = 0, dense_rows = 0, strip_rows = 0;
     for (const SimHost& sh : ctx->sims) {
       cells += (double)sh.nx * sh.ny;
