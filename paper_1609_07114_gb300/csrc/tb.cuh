@@ -60,23 +60,35 @@ __device__ __forceinline__ void cp_async_wait_all() {
 // bits.
 __device__ void tb_rom_step(const RomInstDev& ri, const float* v, float* sout) {
   const unsigned FULL = 0xffffffffu;
+  constexpr int R = 2;   // rows per warp at a time: their loads are in flight together
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   const float4* v4 = reinterpret_cast<const float4*>(v);
   const int l4 = ri.ld >> 2;
-  for (int r = warp; r < ri.n; r += nw) {
-    const float4* __restrict__ Mr = reinterpret_cast<const float4*>(ri.M + (size_t)r * ri.ld);
-    float acc = 0.f;
+  for (int r0 = R * warp; r0 < ri.n; r0 += R * nw) {
+    const float4* __restrict__ Mr[R];
+    float acc[R];
+#pragma unroll
+    for (int u = 0; u < R; ++u) {   // rows past the end repeat the last row; not stored
+      Mr[u] = reinterpret_cast<const float4*>(ri.M + (size_t)min(r0 + u, ri.n - 1) * ri.ld);
+      acc[u] = 0.f;
+    }
     for (int k = lane; k < l4; k += 32) {
-      const float4 m = Mr[k];
       const float4 x = v4[k];
-      acc = fmaf(m.x, x.x, acc);
-      acc = fmaf(m.y, x.y, acc);
-      acc = fmaf(m.z, x.z, acc);
-      acc = fmaf(m.w, x.w, acc);
+#pragma unroll
+      for (int u = 0; u < R; ++u) {
+        const float4 m = Mr[u][k];
+        acc[u] = fmaf(m.x, x.x, acc[u]);
+        acc[u] = fmaf(m.y, x.y, acc[u]);
+        acc[u] = fmaf(m.z, x.z, acc[u]);
+        acc[u] = fmaf(m.w, x.w, acc[u]);
+      }
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
-    if (lane == 0) sout[r] = acc;
+    for (int u = 0; u < R; ++u) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc[u] += __shfl_xor_sync(FULL, acc[u], o);
+      if (lane == 0 && r0 + u < ri.n) sout[r0 + u] = acc[u];
+    }
   }
 }
 
