@@ -142,12 +142,15 @@ def test_multi_strip_gradients_match_oracle():
     assert rel_l2(gw[0], gsrc[0]) < GTOL
 
 
-def test_full_size_gradient_properties():
+def test_full_size_gradient_properties(monkeypatch):
     """The gradient configuration at full batch size (16 x 1024^2, two shared
-    models each), in the benchmark's launch configuration, over 3000 steps
-    with checkpoints every 500: J is quadratic in the sources, so
-    J = 1/2 sum s . dJ/ds (Euler); and the eps gradient at the cell with the
-    largest sensitivity matches a central difference of two forward runs."""
+    models each), in the benchmark's launch configuration (the library's
+    default choice of one or two steps per launch for the forward and
+    checkpoint passes), over 3000 steps with checkpoints every 500: J is
+    quadratic in the sources, so J = 1/2 sum s . dJ/ds (Euler); and the eps
+    gradient at the cell with the largest sensitivity matches a central
+    difference of two forward runs."""
+    monkeypatch.delenv("FDTD_TB", raising=False)
     N = 3000
     w = workloads.adjoint_16(N)
     models = [pg.rom_build(md["a"], md["b"], md["r"], w["dx"], w["dy"], w["dt"], md["eps_r"],
