@@ -94,23 +94,32 @@ def profile_traffic(kernel="yee_step_kernel"):
     return None
 
 
+def _code_only(text):
+    """Source text without // comments and blank lines (so that a comment
+    edit does not void a profile taken on the same code)."""
+    lines = (re.sub(r"//.*", "", ln).rstrip() for ln in text.splitlines())
+    return "\n".join(ln for ln in lines if ln.strip())
+
+
 def stencil_source_sha():
-    """Hash of the stencil kernel's source: the grid and tile structures of
+    """Hash of the stencil kernel's code: the grid and tile structures of
     kernels.cuh (up to the reduced-model structures) plus the part of fdtd.cu
-    from the edge-coefficient helper up to the reduced-model kernel."""
+    from the edge-coefficient helper up to the reduced-model kernel, comments
+    removed."""
     d = os.path.join(ROOT, "paper_1609_07114_gb300", "csrc")
     cu = open(os.path.join(d, "fdtd.cu")).read()
     a = cu.index("// E-edge coefficients from the two adjacent cells")
     b = cu.index("// Eq. (23) for every embedded model")
     kh = open(os.path.join(d, "kernels.cuh")).read()
     kh = kh[:kh.index("struct RomInstDev")]
-    h = hashlib.sha256(kh.encode() + cu[a:b].encode())
+    h = hashlib.sha256(_code_only(kh).encode() + _code_only(cu[a:b]).encode())
     return h.hexdigest()[:16]
 
 
 def march_source_sha():
-    """Hash of the row-marching two-step kernel's source: the structures of
-    kernels.cuh, fdtd.cu's edge-coefficient helper and tb_march.cuh."""
+    """Hash of the row-marching two-step kernel's code: the structures of
+    kernels.cuh, fdtd.cu's edge-coefficient helper and tb_march.cuh,
+    comments removed."""
     d = os.path.join(ROOT, "paper_1609_07114_gb300", "csrc")
     cu = open(os.path.join(d, "fdtd.cu")).read()
     a = cu.index("// E-edge coefficients from the two adjacent cells")
@@ -118,7 +127,8 @@ def march_source_sha():
     kh = open(os.path.join(d, "kernels.cuh")).read()
     kh = kh[:kh.index("struct RomInstDev")]
     tm = open(os.path.join(d, "tb_march.cuh")).read()
-    return hashlib.sha256(kh.encode() + cu[a:b].encode() + tm.encode()).hexdigest()[:16]
+    return hashlib.sha256(_code_only(kh).encode() + _code_only(cu[a:b]).encode()
+                          + _code_only(tm).encode()).hexdigest()[:16]
 
 
 class ClockSampler:

@@ -15,9 +15,10 @@
 //      computed one row earlier,
 // holding everything in registers, and stores B's row when the tile owns it.
 // A starts two rows below the tile and B one row below, so the tile's first
-// stored row has all it needs.  The arithmetic of each update is the same
-// sequence of correctly rounded operations as stencil_row, so two passes of
-// this kernel give the bits of four launches of the one-step kernel.
+// stored row has all it needs.  Each update is the same sequence of explicit
+// operations as stencil_row (correctly rounded products and sums, the
+// hardware reciprocal of edge_coef), so two passes of this kernel give the
+// bits of four launches of the one-step kernel.
 //
 // Model regions: the cells of each model's zone (the region grown by three
 // cells, columns rounded out to multiples of 4) are stepped by the in-CTA
