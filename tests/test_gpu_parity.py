@@ -5,7 +5,8 @@ Tolerance: relative L2 error <= 1e-4 on probe waveforms and on final fields.
 The GPU steps FP32 fields with FP32 edge coefficients computed from FP32 cell
 materials; the oracle steps FP64.  The gap is FP32 rounding (about 1e-7 per
 operation, accumulated as a random walk over the steps) plus a phase drift
-from coefficient rounding (relative 6e-8 per wave speed, times the phase
+from coefficient rounding (FP32 materials and the hardware reciprocal in the
+edge coefficients, relative ~1e-7 per wave speed, times the phase
 travelled), both well below 1e-4 at these sizes and step counts.  Each side
 builds its own reduced models (the library in C++, the oracle in numpy);
 the two agree to 1e-12 on every input-output quantity (test_library_host).
