@@ -363,6 +363,9 @@ int fdtd_energy(fdtd_ctx* ctx, double* out);
  *     FDTD_EINVAL (use fdtd_energy).
  *   - The first call on a device looks up the array's device address once
  *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   - The array is chosen by the CUDA device current when the call is made,
+ *     so the context's device must be current (as for every call of this
+ *     library, whose kernels run on the current device).
  *   - All calls in the process share the one array: calls whose GPU work
  *     overlaps (different contexts on different streams) race.  Every entry
  *     used is written before it is read, so nothing needs clearing.

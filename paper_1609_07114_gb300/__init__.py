@@ -25,6 +25,7 @@ FDTD_RULE_DUAL = 0
 FDTD_RULE_PAPER = 1
 FDTD_SRC_JX = 0
 FDTD_SRC_JY = 1
+FDTD_ENERGY_STATIC_MAX = 32768   # capacity of fdtd_energy_noalloc (include/fdtd.h)
 
 _dp = C.POINTER(C.c_double)
 _fp = C.POINTER(C.c_float)

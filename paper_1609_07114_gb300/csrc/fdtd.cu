@@ -2340,6 +2340,7 @@ int fdtd_energy(fdtd_ctx* ctx, double* out) {
 }
 
 int fdtd_energy_noalloc(fdtd_ctx* ctx, double* out) {
+  NvtxRange nvtx_("fdtd_energy_noalloc");
   if (!ctx || !out) return fail(ctx, FDTD_EINVAL, "fdtd_energy_noalloc: bad argument");
   const int ntiles = (int)ctx->tiles.size(), ninst = (int)ctx->insts.size();
   const int nsim = (int)ctx->sims.size();

@@ -42,3 +42,20 @@ def test_noalloc_energy_matches_fdtd_energy_twice():
         got = ctx.energy_noalloc()
         assert np.all(ref > 0)
         np.testing.assert_allclose(got, ref, rtol=1e-12, atol=0)
+
+
+def test_noalloc_energy_rejects_contexts_beyond_its_capacity():
+    """A context with more stencil tiles + models + simulations than the
+    fixed array holds gets FDTD_EINVAL from the no-allocation entry point
+    (and nothing is written); fdtd_energy still serves it."""
+    n = pg.FDTD_ENERGY_STATIC_MAX // 2 + 16     # 2 x 2 simulations: one tile each
+    rng = np.random.default_rng(7)
+    sims = [(1.0 + rng.random((2, 2)), np.zeros((2, 2))) for _ in range(n)]
+    dx = 1e-3
+    ctx = pg.FdtdContext(dx, dx, 0.5 * pg.fdtd_cfl_limit(dx, dx), sims)
+    out = np.full(n, -7.0)
+    rc = pg.lib().fdtd_energy_noalloc(ctx._h, out.ctypes.data_as(pg._dp))
+    assert rc == -1                              # FDTD_EINVAL
+    assert b"static capacity" in pg.lib().fdtd_last_error(ctx._h)
+    assert np.all(out == -7.0)
+    assert np.all(ctx.energy() == 0.0)
