@@ -1,6 +1,9 @@
 """Discrete adjoint of the Yee + embedded-ROM time loop, FP64 oracle.
 
-Objective (probe energy):  J = sum_n sum_p (Hz^{n+1/2}(probe p))^2.
+Objective (probe energy):  J = sum_n sum_p (Hz^{n+1/2}(probe p))^2, or, given
+a cotangent c[n][p] of the probe samples o^n_p = Hz^{n+1/2}(probe p), the
+vector-Jacobian product of the probe series, i.e. the gradient of the linear
+functional L = sum_n sum_p c[n][p] o^n_p (c = 2 o gives J's gradient).
 Parameters: per-cell eps_r and sigma of the coarse grid and the source
 samples J^n.  The forward step n (``scheme.step``) is
 
@@ -18,7 +21,7 @@ transpose, run backwards over stored forward states, gives the gradient
   3. g_H' += curl^T(g_E / alpha);  dJ/dJ^n = -A g_E / alpha on source edges;
      dJ/deps_edge += g_E A (E - E') / (alpha dt);
      dJ/dsigma_edge -= g_E A (E + E') / (2 alpha);  g_E <- (beta/alpha) g_E
-  4. g_H'(probes) += 2 o^n
+  4. g_H'(probes) += dL/do^n   (2 o^n for J, c[n] for a given cotangent)
   5. g_E += (H update)^T g_H';  g_H <- g_H' on coarse cells
 Edge materials are cell means, so a cell receives half of each adjacent edge's
 eps/sigma gradient.  The coarse half cell of interface edge k (the cell just
@@ -54,14 +57,20 @@ def forward_store(grid, emb, nsteps, sources, probes):
     return states, out
 
 
-def gradients(w, nsteps=None, rule=None, order=None):
-    """J and dJ/d(eps_r, sigma, source samples) for workload w (FP64)."""
+def gradients(w, nsteps=None, rule=None, order=None, cotangent=None):
+    """J and dJ/d(eps_r, sigma, source samples) for workload w (FP64); with a
+    cotangent c ([nsteps][nprobe]), L = sum c o and dL/d(...) instead."""
     kw = {} if rule is None else {"rule": rule}
     grid, emb, built = problem.build(w, order=order, **kw)
     n_steps = w["nsteps"] if nsteps is None else nsteps
     sources, probes = w["sources"], w["probes"]
     states, out = forward_store(grid, emb, n_steps, sources, probes)
-    J = float(np.sum(out**2))
+    if cotangent is None:
+        J = float(np.sum(out**2))
+        seed = 2.0 * out
+    else:
+        seed = np.asarray(cotangent, dtype=np.float64).reshape(n_steps, len(probes))
+        J = float(np.sum(seed * out))
     nx, ny, dx, dy, dt = grid.nx, grid.ny, grid.dx, grid.dy, grid.dt
     area = dx * dy
     ch = dt / (dx * dy * MU0)
@@ -117,9 +126,8 @@ def gradients(w, nsteps=None, rule=None, order=None):
         gHp += -dy * muy[:, :-1] + dy * muy[:, 1:]
         gEx = np.where(grid.ex_upd, grid.bx / grid.ax * gEx, 0.0)
         gEy = np.where(grid.ey_upd, grid.by / grid.ay * gEy, 0.0)
-        # 4. probes
-        o = states[n + 1][2][pj, pi]
-        np.add.at(gHp, (pj, pi), 2.0 * o)
+        # 4. probes: o^n = H'(probes), dL/do^n = seed[n]
+        np.add.at(gHp, (pj, pi), seed[n])
         # 5. transposed H update (coarse cells only)
         gHp = np.where(grid.hz_active, gHp, 0.0)
         gEx[:-1, :] += -ch * dx * gHp
@@ -158,7 +166,10 @@ def gradients(w, nsteps=None, rule=None, order=None):
     return J, deps, dsig, gsrc
 
 
-def objective(w, nsteps=None, rule=None, order=None):
+def objective(w, nsteps=None, rule=None, order=None, cotangent=None):
+    """J (sum of probe Hz^2), or L = sum c o for a cotangent c."""
     kw = {} if rule is None else {"rule": rule}
     out, *_ = problem.run(w, nsteps, order=order, **kw)
-    return float(np.sum(out**2))
+    if cotangent is None:
+        return float(np.sum(out**2))
+    return float(np.sum(np.asarray(cotangent, dtype=np.float64).reshape(out.shape) * out))
