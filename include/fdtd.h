@@ -238,6 +238,22 @@ int fdtd_grad(fdtd_ctx* ctx, long long nsteps, const fdtd_source* src, int nsrc,
               const fdtd_probe* probes, int nprobe, int ckpt_every, float* dJ_deps,
               float* dJ_dsigma, float* dJ_dsrc, double* J_out);
 
+/* Vector-Jacobian product of the probe series (not in the paper): with the
+ * probe samples o[n][p] = Hz^{n+1/2}(probe p) of the next nsteps steps and a
+ * cotangent c = dL_dprobe (device FP32 [nsteps][nprobe], caller-owned),
+ * the gradient of L = sum_n sum_p c[n][p] o[n][p] by the same exact discrete
+ * adjoint as fdtd_grad (whose J is the case c = 2 o).  It runs the forward
+ * pass with checkpoints every ckpt_every steps and the reverse sweep seeded
+ * with c.  Outputs as for fdtd_grad (dL_deps, dL_dsigma per simulation
+ * [ny][nx] concatenated, dL_dsrc [nsrc][nsteps]; any may be NULL; device,
+ * caller-owned, overwritten); probe_out (device FP32 [nsteps][nprobe], may be
+ * NULL) receives the forward pass's probe samples.  The context ends in the
+ * state reached by the forward pass.  FDTD_EINVAL when nprobe > 0 and
+ * dL_dprobe is NULL.  Synchronises. */
+int fdtd_vjp(fdtd_ctx* ctx, long long nsteps, const fdtd_source* src, int nsrc,
+             const fdtd_probe* probes, int nprobe, int ckpt_every, const float* dL_dprobe,
+             float* dL_deps, float* dL_dsigma, float* dL_dsrc, float* probe_out);
+
 /* ---------------------------------------------------------- open boundaries */
 
 /* Convolutional PML layers (complex-frequency-shifted CPML of Roden and
@@ -388,6 +404,55 @@ int fdtd_set_timing(fdtd_ctx* ctx, int on);
  * model step counted in post_ms). */
 int fdtd_get_kernel_times(fdtd_ctx* ctx, double* yee_ms, long long* yee_launches,
                           double* post_ms, long long* post_launches);
+
+/* Device time (ms) of one launch of the context's stencil kernel alone, for
+ * roofline figures without per-kernel instrumentation: a CUDA graph of
+ * `launches` back-to-back launches of the kernel fdtd_run uses for the
+ * coarse update (the row-marching kernel when the context steps in pairs,
+ * else the one-step kernel), without sources, probes or reduced models, is
+ * replayed `reps` times between two CUDA events on the context's stream
+ * (after one untimed replay); *ms_per_launch = elapsed / (reps * launches).
+ * Every launch reads the current fields and writes the other copy of the
+ * ping-pong pair, so the current state and the step counter are unchanged
+ * (the other copy is overwritten by the next step anyway).  Synchronises.
+ * FDTD_EINVAL for a bad argument or while fdtd_set_timing is on. */
+int fdtd_time_stencil(fdtd_ctx* ctx, int launches, int reps, double* ms_per_launch);
+
+/* Launch configuration chosen by fdtd_autotune. */
+typedef struct {
+  int steps_per_launch;    /* 1, or 2 (two steps per pass over the fields) */
+  int tile_rows;           /* tile height of the one-step stencil */
+  int march_rows;          /* tile height of the row-marching two-step kernel (0: unused) */
+  int march_ring;          /* rows it stages ahead through shared memory (0: loads to registers) */
+  int gemm_min;            /* simulations sharing a map from which it steps as a GEMM (0: fixed rule, 20) */
+  int gemm_rows_per_warp;  /* GEMM CTA shape, 1 or 2 (0: fixed rule) */
+  int chain;               /* two-step path, maps outside the zone tiles: 1 every model, 0 none,
+                              -1 the maps shared by a GEMM group */
+  int chained_models;      /* models stepped that way in the chosen plan */
+  int candidates;          /* configurations timed (0: taken from the cache file) */
+  double ms_default;       /* device ms per time step of the fixed rule */
+  double ms_best;          /* ... and of the chosen configuration */
+} fdtd_tune_report;
+
+/* Autotuner of the launch configuration (no counterpart in the paper): times
+ * candidate configurations on the context itself and keeps the fastest for
+ * the context's life.  The candidates are the choices that leave every
+ * result bit-identical: one or two steps per launch, the tile heights of the
+ * one-step and two-step kernels, how many rows the two-step kernel stages
+ * ahead, where the models' maps run on the two-step path, and from how many
+ * sharing simulations (and with which CTA shape) a map runs as a GEMM.  Search: one pass of coordinate descent from the fixed
+ * rule, each candidate marched from the current state (no sources or probes,
+ * a few ms of steps timed with CUDA events on the context's stream); a
+ * candidate wins only if more than 1% faster.  The marching state (fields,
+ * model states, step count, PML auxiliaries, DFT sums) is restored after
+ * every candidate, so the context continues where it was.  cache_path (NULL:
+ * the FDTD_TUNE_CACHE environment variable; neither: no cache) names a text
+ * file holding one line per tuned problem, keyed by the device (name, SM
+ * count, clock), the grids and the embedded models: a key found there is
+ * applied without timing, a new result is appended.  report may be NULL.
+ * Synchronises.  Call it again after embedding more models or setting
+ * layers or monitors (those re-plan with the kept choices). */
+int fdtd_autotune(fdtd_ctx* ctx, const char* cache_path, fdtd_tune_report* report);
 
 /* Time steps one stencil launch of fdtd_run advances: 2 when the context
  * steps in pairs (temporal blocking: two steps of Eq. (5), Eq. (3) per pass

@@ -65,6 +65,17 @@ class fdtd_pml_desc(C.Structure):
 FDTD_PML_W, FDTD_PML_E, FDTD_PML_S, FDTD_PML_N = 1, 2, 4, 8
 
 
+class fdtd_tune_report(C.Structure):
+    _fields_ = [("steps_per_launch", C.c_int), ("tile_rows", C.c_int), ("march_rows", C.c_int),
+                ("march_ring", C.c_int),
+                ("gemm_min", C.c_int), ("gemm_rows_per_warp", C.c_int), ("chain", C.c_int),
+                ("chained_models", C.c_int), ("candidates", C.c_int), ("ms_default", C.c_double),
+                ("ms_best", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class fdtd_source(C.Structure):
     _fields_ = [("sim", C.c_int), ("comp", C.c_int), ("i", C.c_int), ("j", C.c_int),
                 ("len", C.c_int), ("wave", _fp)]
@@ -111,6 +122,8 @@ def lib() -> C.CDLL:
         "fdtd_grad": (i, [vp, ll, C.POINTER(fdtd_source), i, C.POINTER(fdtd_probe), i, i,
                           vp, vp, vp, _dp]),
         "fdtd_energy_noalloc": (i, [vp, _dp]),
+        "fdtd_vjp": (i, [vp, ll, C.POINTER(fdtd_source), i, C.POINTER(fdtd_probe), i, i,
+                         vp, vp, vp, vp, vp]),
         "fdtd_dft_set": (i, [vp, C.POINTER(fdtd_probe), i, _dp, i, _dp]),
         "fdtd_dft_get": (i, [vp, _dp]),
         "fdtd_fine_fields": (i, [vp, i, vp, vp, vp, vp]),
@@ -120,6 +133,8 @@ def lib() -> C.CDLL:
         "fdtd_set_timing": (i, [vp, i]),
         "fdtd_get_kernel_times": (i, [vp, _dp, C.POINTER(ll), _dp, C.POINTER(ll)]),
         "fdtd_steps_per_launch": (i, [vp]),
+        "fdtd_time_stencil": (i, [vp, i, i, _dp]),
+        "fdtd_autotune": (i, [vp, C.c_char_p, C.POINTER(fdtd_tune_report)]),
         "fdtd_last_error": (C.c_char_p, [vp]),
     }
     for name, (res, args) in sig.items():
@@ -436,6 +451,35 @@ class FdtdContext:
             off += ny * nx
         return J.value, out_e, out_s, gsrc[:len(sources)]
 
+    def fdtd_vjp(self, nsteps, sources, probes, cotangent, ckpt_every=500, need_src=True,
+                 probe_out=None):
+        """Vector-Jacobian product of the probe series (``fdtd_vjp``): the
+        gradient of L = sum cotangent * probes over the next nsteps steps.
+        cotangent: CUDA float32 [nsteps, nprobe]; probe_out: optional CUDA
+        float32 [nsteps, nprobe] for the forward samples.  Returns
+        (dL/deps_r per simulation [ny, nx], dL/dsigma likewise,
+        dL/dJ^n [nsrc, nsteps]) as CUDA float32 tensors."""
+        import torch
+        src, _ = self._sources(sources, host=False)
+        pr = self._probes(probes)
+        if len(probes):
+            assert (cotangent.is_cuda and cotangent.dtype == torch.float32 and cotangent.is_contiguous()
+                    and cotangent.numel() == nsteps * len(probes))
+        ncell = sum(ny * nx for ny, nx in self.shapes)
+        geps = torch.zeros(ncell, dtype=torch.float32, device="cuda")
+        gsig = torch.zeros(ncell, dtype=torch.float32, device="cuda")
+        gsrc = torch.zeros((max(len(sources), 1), nsteps), dtype=torch.float32, device="cuda")
+        ptr = lambda t: C.c_void_p(t.data_ptr()) if t is not None else C.c_void_p()
+        self._ck(lib().fdtd_vjp(self._h, nsteps, src, len(sources), pr, len(probes), ckpt_every,
+                                ptr(cotangent if len(probes) else None), ptr(geps), ptr(gsig),
+                                ptr(gsrc) if need_src else C.c_void_p(), ptr(probe_out)))
+        out_e, out_s, off = [], [], 0
+        for ny, nx in self.shapes:
+            out_e.append(geps[off:off + ny * nx].view(ny, nx))
+            out_s.append(gsig[off:off + ny * nx].view(ny, nx))
+            off += ny * nx
+        return out_e, out_s, gsrc[:len(sources)]
+
     def energy(self):
         """Storage function W of every simulation (``fdtd_energy``)."""
         out = np.zeros(len(self.shapes))
@@ -458,6 +502,21 @@ class FdtdContext:
         if r < 0:
             self._ck(r)
         return r
+
+    def autotune(self, cache_path=None):
+        """``fdtd_autotune``: time the bit-identical launch configurations on
+        this context and keep the fastest; returns the report as a dict."""
+        rep = fdtd_tune_report()
+        p = cache_path.encode() if cache_path else None
+        self._ck(lib().fdtd_autotune(self._h, p, C.byref(rep)))
+        return rep.as_dict()
+
+    def time_stencil(self, launches=16, reps=8):
+        """Device ms of one stencil launch alone, from graph replays without
+        per-kernel events (``fdtd_time_stencil``); the state is unchanged."""
+        ms = C.c_double()
+        self._ck(lib().fdtd_time_stencil(self._h, launches, reps, C.byref(ms)))
+        return ms.value
 
     def kernel_times(self):
         """(stencil ms, stencil launches, ROM/probe ms, ROM/probe launches);

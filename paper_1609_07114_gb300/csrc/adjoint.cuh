@@ -58,6 +58,7 @@ struct AdjWork {         // one CTA of adj_pre: columns [c0, c1) of one instance
 
 struct AdjRun {
   const float* probe_out;   // [nsteps][nprobe] of the forward pass
+  const float* seed;        // [nsteps][nprobe] dL/do^n (vector-Jacobian product), or null: 2 o^n (J)
   const int* probe_sim;
   const int* probe_cell;
   const SrcEdge* src_edges;
@@ -125,7 +126,8 @@ adj_pre_kernel(const AdjSimDev* __restrict__ sims, const AdjInstDev* __restrict_
   if (idx < ar->nprobe) {
     const AdjSimDev* sd = sims + ar->probe_sim[idx];
     float* ghza = par ? sd->ghz[1] : sd->ghz[0];
-    atomicAdd(ghza + ar->probe_cell[idx], 2.f * ar->probe_out[n * ar->nprobe + idx]);
+    const size_t k = (size_t)n * ar->nprobe + idx;
+    atomicAdd(ghza + ar->probe_cell[idx], ar->seed ? ar->seed[k] : 2.f * ar->probe_out[k]);
   } else if (idx - ar->nprobe < ar->nedges) {
     const SrcEdge se = ar->src_edges[idx - ar->nprobe];
     const AdjSimDev* sd = sims + se.sim;
@@ -579,9 +581,13 @@ struct GradArena {
   }
 };
 
+// vjp: seed the probe terms with the device cotangent `seed` ([nsteps][nprobe])
+// instead of 2 o^n (the probe energy J; J_out is then not formed);
+// probe_user: device buffer for the forward pass's probe samples (null: a
+// buffer of this call).
 int run_grad(fdtd_ctx* ctx, long long nsteps, const fdtd_source* src, int nsrc,
              const fdtd_probe* probes, int nprobe, int C, float* dJ_deps, float* dJ_dsig,
-             float* dJ_dsrc, double* J_out) {
+             float* dJ_dsrc, double* J_out, bool vjp, const float* seed, float* probe_user) {
   if (nsteps < 1 || C < 1 || nsrc < 0 || nprobe < 0 || (nsrc && !src) || (nprobe && !probes))
     return fail(ctx, FDTD_EINVAL, "fdtd_grad: bad argument");
   if (!ctx->pml_cells.empty()) return fail(ctx, FDTD_EINVAL, "fdtd_grad: not available with PML layers");
@@ -593,8 +599,8 @@ int run_grad(fdtd_ctx* ctx, long long nsteps, const fdtd_source* src, int nsrc,
   cudaStream_t st = ctx->stream;
   GradArena A;
   // --- forward pass with checkpoints
-  float* probe_d = nullptr;
-  CK(A.alloc(&probe_d, (size_t)nsteps * std::max(nprobe, 1)));
+  float* probe_d = probe_user;
+  if (!probe_d) CK(A.alloc(&probe_d, (size_t)nsteps * std::max(nprobe, 1)));
   std::vector<const float*> wv(std::max(nsrc, 1));
   for (int s = 0; s < nsrc; ++s) wv[s] = src[s].wave;
   int rc = prepare_run(ctx, nsteps, src, nsrc, wv.data(), probes, nprobe, probe_d);
@@ -628,7 +634,7 @@ int run_grad(fdtd_ctx* ctx, long long nsteps, const fdtd_source* src, int nsrc,
   }
   double* Jd = nullptr;
   CK(A.alloc(&Jd, 1));
-  if (nprobe > 0) sum_sq_kernel<<<1, 1024, 0, st>>>(probe_d, (size_t)nsteps * nprobe, Jd);
+  if (nprobe > 0 && !vjp) sum_sq_kernel<<<1, 1024, 0, st>>>(probe_d, (size_t)nsteps * nprobe, Jd);
   // --- adjoint state, frames and tables
   std::vector<AdjSimDev> asd(nsim);
   std::vector<double*> g64e(nsim), g64s(nsim);
@@ -718,7 +724,7 @@ int run_grad(fdtd_ctx* ctx, long long nsteps, const fdtd_source* src, int nsrc,
     if (!ctx->tiles.empty())
       CK(cudaMemcpy(&last, ctx->src_range.p + ctx->tiles.size() - 1, sizeof(int2), cudaMemcpyDeviceToHost));
     nedges = last.y;
-    AdjRun ar{probe_d, ctx->probe_sim.p, ctx->probe_cell.p, ctx->src_edges.p, dsrc, nsteps, nprobe, nedges};
+    AdjRun ar{probe_d, vjp ? seed : nullptr, ctx->probe_sim.p, ctx->probe_cell.p, ctx->src_edges.p, dsrc, nsteps, nprobe, nedges};
     CK(cudaMemcpy(ar_d, &ar, sizeof(AdjRun), cudaMemcpyHostToDevice));
   }
   // per-step tables of the recomputation (frame t -> t+1), the same for every segment

@@ -10,12 +10,14 @@
 #include <chrono>
 #include <cmath>
 #include <cstdlib>
+#include <cstdio>
 #include <cstring>
 #include <map>
 #include <memory>
 #include <mutex>
 #include <new>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include <nvtx3/nvToolsExt.h>
@@ -360,19 +362,23 @@ yee_step_kernel(const SimDev* __restrict__ sims, const TileWork* __restrict__ wo
 // Eq. (23) for every embedded model, then the probes.  A CTA takes
 // kRomRowsPerCta rows of one model, one row per warp: v = [y; x~; h] is staged
 // in shared memory and each warp forms one dot product with [P | Q] using
-// float4 loads (all of a row's loads are in flight together).
+// float4 loads (all of a row's loads are in flight together): lane l sums
+// the float4 chunks k4 = l, l + 32, ... with fused multiply-adds (x, y, z, w
+// in turn), and the 32 partial sums are added by a warp xor-butterfly
+// (offsets 16, 8, 4, 2, 1).
 // Batched form: the simulations sharing one coupled map step it as one
 // GEMM [S'] = [P | Q] [S; H], one column per simulation.  A CTA takes
-// 8 RPW rows (RPW per warp) and up to 32 columns (one per lane).  Its rows
-// of [P | Q] (row-major, stride ld + 4) and the input panel [S; H] of its
-// columns (ld x 32, stride 33) are staged in shared memory by cp.async with
-// every copy in flight at once; lane l then accumulates its rows . column l
-// in order k = 0, 1, ... (one memory latency per launch).  RPW = 1 gives
-// more, smaller CTAs (a map shared by a few tens of simulations); RPW = 4
-// re-stages the panel less often (large batches).
-__host__ __device__ constexpr size_t gemm_smem_floats(int ld, int rpw) {
-  return (size_t)ld * 33 + (size_t)rpw * kRomRowsPerCta * (ld + 4);
-}
+// 8 RPW rows (RPW per warp) and up to 32 columns; the input panel of its
+// columns is staged in shared memory column by column (ld floats each, by
+// cp.async with every copy in flight at once).  Each output is formed by the
+// operations of the one-row-per-warp form in the same order: lane l keeps,
+// for each of the 32 columns, the partial sum of the chunks k4 = l, l + 32, ...
+// of its row, and a reduce-scatter over the lanes (the butterfly's pairings,
+// offsets 16, 8, 4, 2, 1) leaves column l's sum in lane l.  So both forms,
+// and the two-step path's model tiles, give the same bits.  RPW = 1 gives
+// more, smaller CTAs (a map shared by a few tens of simulations); RPW = 2
+// reads each panel chunk for two rows (large batches).
+__host__ __device__ constexpr size_t gemm_smem_floats(int ld) { return (size_t)ld * 32; }
 
 // Asynchronous global -> shared copies (no register round trip, so every
 // copy of a staging loop is in flight at once).
@@ -390,6 +396,61 @@ __device__ __forceinline__ void async_wait_all() {
   asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
 
+// v[0..31]: this lane's partial sums of 32 columns.  Returns the total of
+// column `lane` over the 32 lanes, added pairwise in the order of an xor
+// butterfly with offsets 16, 8, 4, 2, 1 (floating-point addition is
+// commutative, so which lane holds a pair does not change the bits).
+__device__ __forceinline__ float reduce_scatter32(float (&v)[32], int lane) {
+  const unsigned FULL = 0xffffffffu;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int j = 0; j < o; ++j) {
+      const float lo = v[j], hi = v[j + o];
+      const float got = __shfl_xor_sync(FULL, up ? lo : hi, o);
+      v[j] = __fadd_rn(up ? hi : lo, got);
+    }
+  }
+  return v[0];
+}
+
+// RPW rows (row pointers Mr, ld floats each, 16-B aligned) against the 32
+// columns of the shared-memory panel (column c at panel + c ld); result of
+// row i for column `lane` in res[i].
+template <int RPW>
+__device__ __forceinline__ void gemm_exact_rows(const float4* const (&Mr)[RPW], int l4, const float* panel, int ld,
+                                                int lane, float (&res)[RPW]) {
+  float p[RPW][32];
+#pragma unroll
+  for (int i = 0; i < RPW; ++i)
+#pragma unroll
+    for (int c = 0; c < 32; ++c) p[i][c] = 0.f;
+  float4 mc[RPW];
+#pragma unroll
+  for (int i = 0; i < RPW; ++i) mc[i] = lane < l4 ? Mr[i][lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int k4 = lane; k4 < l4; k4 += 32) {
+    float4 mn[RPW];
+#pragma unroll
+    for (int i = 0; i < RPW; ++i) mn[i] = k4 + 32 < l4 ? Mr[i][k4 + 32] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int c = 0; c < 32; ++c) {
+      const float4 x = *reinterpret_cast<const float4*>(panel + (size_t)c * ld + 4 * k4);
+#pragma unroll
+      for (int i = 0; i < RPW; ++i) {
+        p[i][c] = fmaf(mc[i].x, x.x, p[i][c]);
+        p[i][c] = fmaf(mc[i].y, x.y, p[i][c]);
+        p[i][c] = fmaf(mc[i].z, x.z, p[i][c]);
+        p[i][c] = fmaf(mc[i].w, x.w, p[i][c]);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < RPW; ++i) mc[i] = mn[i];
+  }
+#pragma unroll
+  for (int i = 0; i < RPW; ++i) res[i] = reduce_scatter32(p[i], lane);
+}
+
 template <int RPW>
 __device__ __forceinline__ void rom_gemm_rows(const SimDev* __restrict__ sims,
                                               const RomInstDev* __restrict__ insts,
@@ -405,7 +466,7 @@ __device__ __forceinline__ void rom_gemm_rows(const SimDev* __restrict__ sims,
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   constexpr int nwarp = kRomRowsPerCta;
   const int nc = min(32, g.B - gw.c0);
-  const int ld = g.ld, ms = ld + 4;
+  const int ld = g.ld;
   if (tid < nc) {
     const RomInstDev ri = insts[ginst[g.inst_off + gw.c0 + tid]];
     const SimDev* sd = sims + ri.sim;
@@ -417,58 +478,45 @@ __device__ __forceinline__ void rom_gemm_rows(const SimDev* __restrict__ sims,
     s_hc[tid] = ri.h_cell;
     s_ye[tid] = ri.y_edge;
   }
-  float* panel = smem;                          // [k][col], stride 33
-  float* mrow = smem + (size_t)ld * 33;         // [row][k], stride ld + 4
-  const int nr = min(RPW * nwarp, g.n - gw.r0);
-  const int l4 = ld >> 2;
-  for (int e = tid; e < nr * l4; e += blockDim.x) {
-    const int r = e / l4, k4 = e - r * l4;
-    async_copy16(mrow + (size_t)r * ms + 4 * k4, g.M + (size_t)(gw.r0 + r) * ld + 4 * k4);
-  }
+  const int rb = gw.r0 + RPW * warp;
+  const float4* Mr[RPW];
+#pragma unroll
+  for (int i = 0; i < RPW; ++i)   // rows past the end repeat the last row; not stored
+    Mr[i] = reinterpret_cast<const float4*>(g.M + (size_t)min(rb + i, g.n - 1) * ld);
   pdl_wait();        // model states and Hz^{n+1/2}: written by the previous kernels
   __syncthreads();   // column pointers
-  for (int col = warp; col < nc; col += nwarp) {
-    const float* __restrict__ sp = s_in[col];
-    const float* __restrict__ hp = s_hz[col];
-    const int* __restrict__ hc = s_hc[col];
-    for (int k = lane; k < g.n; k += 32) async_copy4(panel + k * 33 + col, sp + k);
-#pragma unroll 4
-    for (int k = g.n + lane; k < g.n + g.ny; k += 32) async_copy4(panel + k * 33 + col, hp + hc[k - g.n]);
-    for (int k = g.n + g.ny + lane; k < ld; k += 32) panel[k * 33 + col] = 0.f;
+  float* panel = smem;   // [col][k], ld floats per column
+  for (int col = warp; col < 32; col += nwarp) {
+    float* pc = panel + (size_t)col * ld;
+    if (col < nc) {
+      const float* __restrict__ sp = s_in[col];
+      const float* __restrict__ hp = s_hz[col];
+      const int* __restrict__ hc = s_hc[col];
+      for (int k = lane; k < g.n; k += 32) async_copy4(pc + k, sp + k);
+      for (int k = g.n + lane; k < g.n + g.ny; k += 32) async_copy4(pc + k, hp + hc[k - g.n]);
+      for (int k = g.n + g.ny + lane; k < ld; k += 32) pc[k] = 0.f;
+    } else {
+      for (int k = lane; k < ld; k += 32) pc[k] = 0.f;
+    }
   }
   async_wait_all();
   __syncthreads();
-  const int rb = RPW * warp;
-  if (gw.r0 + rb >= g.n || lane >= nc) return;
-  const float* m0 = mrow + (size_t)rb * ms;
-  const float* pc = panel + lane;
-  float acc[RPW];
-#pragma unroll
-  for (int i = 0; i < RPW; ++i) acc[i] = 0.f;
-#pragma unroll 2
-  for (int k = 0; k < ld; k += 4) {
-    const float p0 = pc[k * 33], p1 = pc[(k + 1) * 33], p2 = pc[(k + 2) * 33], p3 = pc[(k + 3) * 33];
-#pragma unroll
-    for (int i = 0; i < RPW; ++i) {
-      const float4 w = *reinterpret_cast<const float4*>(m0 + i * ms + k);
-      acc[i] = fmaf(w.x, p0, acc[i]);
-      acc[i] = fmaf(w.y, p1, acc[i]);
-      acc[i] = fmaf(w.z, p2, acc[i]);
-      acc[i] = fmaf(w.w, p3, acc[i]);
-    }
-  }
+  if (rb >= g.n) return;
+  float res[RPW];
+  gemm_exact_rows<RPW>(Mr, ld >> 2, panel, ld, lane, res);
+  if (lane >= nc) return;
   float* __restrict__ so = s_out[lane];
   const int* __restrict__ ye = s_ye[lane];
   float* __restrict__ bx = s_ex[lane];
   float* __restrict__ by = s_ey[lane];
 #pragma unroll
   for (int i = 0; i < RPW; ++i) {
-    const int r = gw.r0 + rb + i;
+    const int r = rb + i;
     if (r < g.n) {
-      so[r] = acc[i];
+      so[r] = res[i];
       if (r < g.ny) {
         const int code = ye[r];
-        ((code >> 30) ? by : bx)[code & 0x3fffffff] = acc[i];
+        ((code >> 30) ? by : bx)[code & 0x3fffffff] = res[i];
       }
     }
   }
@@ -485,8 +533,8 @@ rom_post_kernel(const SimDev* __restrict__ sims, const RomInstDev* __restrict__ 
   if ((int)blockIdx.x >= nwork && (int)blockIdx.x < nwork + ngwork) {
     const GemmWork gw = gwork[blockIdx.x - nwork];
     const GemmGroupDev g = groups[gw.group];
-    if (g.rpw == 4)
-      rom_gemm_rows<4>(sims, insts, g, gw, ginst, par, reinterpret_cast<float*>(smem4));
+    if (g.rpw == 2)
+      rom_gemm_rows<2>(sims, insts, g, gw, ginst, par, reinterpret_cast<float*>(smem4));
     else
       rom_gemm_rows<1>(sims, insts, g, gw, ginst, par, reinterpret_cast<float*>(smem4));
     return;
@@ -894,7 +942,7 @@ struct Instance {
   int sim = 0, i0 = 0, j0 = 0, a = 0, b = 0, q = 0, ny = 0, n = 0;
   InterfaceDesc itf;
   std::shared_ptr<CoupledMap> map;
-  float* state_d[2] = {nullptr, nullptr};
+  float* state_d[3] = {nullptr, nullptr, nullptr};   // ping-pong pair, mid-step vector (ld floats each)
   int* y_edge_d = nullptr;
   int* h_cell_d = nullptr;
   std::vector<int> y_edge, h_cell;
@@ -992,6 +1040,18 @@ struct fdtd_ctx {
   DevBuf<int> tb_prb;
   cudaGraphExec_t tb_graph[2] = {nullptr, nullptr};
   int tb_graph_nprobe[2] = {-1, -1};
+  // zone chain (tb.cuh zone_step_kernel / rom_chain_kernel): the last
+  // tb_nchain model tiles step their maps outside the tile, on a side stream
+  // of the highest priority forked from the context's stream per pair
+  int tb_chain_mode = -1;          // FDTD_TB_CHAIN at creation: 0 never, 1 every model, -1 shared maps
+  std::vector<char> in_gemm;       // per instance: stepped in a GEMM group (upload_instances)
+  int tb_nchain = 0;
+  int chain_nrow = 0;              // rom_chain_kernel blocks stepping single models (romwork prefix)
+  size_t zone_smem = 0, chain_smem = 0;
+  DevBuf<float> zone_scratch;
+  cudaStream_t side_stream = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  int prio_hi = 0;
   // row-marching form of the two-step path (tb_march.cuh): ordinary areas in
   // yee_tb2m_kernel, tb_tiles then holds only the model tiles
   int tb_mode = -1;                // FDTD_TB at creation: 0 off, 1 on where it applies, -1 automatic
@@ -1010,6 +1070,11 @@ struct fdtd_ctx {
   int tbm_th = 0;
   int tbm_pf = 0;                  // rows prefetched into L2 ahead of the loads (FDTD_TB_PF)
   int tbm_mb = 4;                  // resident CTAs per SM the kernel is compiled for (FDTD_TB_MB)
+  int tbm_ring = 0;                // rows staged ahead through shared memory (FDTD_TB_RING; 0: registers)
+  // configuration chosen by fdtd_autotune (0: the fixed rule or the
+  // environment): one-step tile rows, row-marching tile rows, simulations per
+  // shared map from which it steps as a GEMM, GEMM rows per warp
+  int ov_th1 = 0, ov_thm = 0, ov_gemm_min = 0, ov_rpw = 0, ov_ring = -1;
   // measurement mode (fdtd_set_timing)
   bool timing = false;
   std::vector<cudaEvent_t> ev;
@@ -1074,6 +1139,7 @@ void drop_graphs(fdtd_ctx* ctx) {
 int plan_tb(fdtd_ctx* ctx) {
   ctx->tb = false;
   ctx->tb_march = false;
+  ctx->tb_nchain = 0;
   ctx->tb_tiles.clear();
   ctx->tb_zones.clear();
   ctx->tbm_tiles.clear();
@@ -1096,8 +1162,16 @@ int plan_tb(fdtd_ctx* ctx) {
   if (!ctx->pml_cells.empty()) return FDTD_OK;   // the layers' corrections need the one-step form
   const char* es = getenv("FDTD_TB_SMEM");
   const bool march = !(mode == 1 && es && atoi(es) == 1);
+  // Models whose map is stepped outside their zone tile (zone chain):
+  // FDTD_TB_CHAIN=1 every model, 0 none, unset those whose map is shared by
+  // a GEMM group (one [P | Q] panel applied to many simulations' vectors).
+  const size_t ninst = ctx->insts.size();
+  std::vector<char> chain(ninst, 0);
+  for (size_t k = 0; k < ninst; ++k)
+    chain[k] = ctx->tb_chain_mode == 1 ||
+               (ctx->tb_chain_mode < 0 && k < ctx->in_gemm.size() && ctx->in_gemm[k]);
   if (mode != 1) {
-    double cells = 0, zone_us = 0, dense_rows = 0, strip_rows = 0;
+    double cells = 0, zone_us = 0, chain_nld = 0, dense_rows = 0, strip_rows = 0;
     for (const SimHost& sh : ctx->sims) {
       cells += (double)sh.nx * sh.ny;
       strip_rows += (double)sh.ny * sh.nstrip;
@@ -1105,16 +1179,22 @@ int plan_tb(fdtd_ctx* ctx) {
         for (int st = 0; st < sh.nstrip; ++st)
           dense_rows += (sh.mbits[(size_t)(j >> 5) * sh.nstrip + st] >> (j & 31)) & 1u;
     }
-    for (const Instance& in : ctx->insts) zone_us = std::max(zone_us, 0.6e-3 * in.n * (double)in.map->ld + 5.0);
+    for (size_t k = 0; k < ninst; ++k) {
+      const Instance& in = ctx->insts[k];
+      if (chain[k]) chain_nld += (double)in.n * in.map->ld;
+      else zone_us = std::max(zone_us, 0.6e-3 * in.n * (double)in.map->ld + 5.0);
+    }
+    // the chain: four dependent launches (~6 us each) and two map products
+    if (chain_nld > 0) zone_us = std::max(zone_us, 24.0 + 1.33e-7 * chain_nld);
     if (cells * 6.6e-6 < 1.25 * zone_us) return FDTD_OK;
     if (dense_rows < 0.5 * strip_rows) return FDTD_OK;
   }
   const int M = kTbZoneMargin;
-  std::vector<int4> zone(ctx->insts.size());
-  for (size_t k = 0; k < ctx->insts.size(); ++k) {
+  std::vector<int4> zone(ninst);
+  for (size_t k = 0; k < ninst; ++k) {
     const Instance& in = ctx->insts[k];
     const SimHost& sh = ctx->sims[in.sim];
-    if (in.map->ld > kTbMaxRomN) return FDTD_OK;
+    if (in.map->ld > kTbMaxRomN && !chain[k]) return FDTD_OK;
     // columns rounded out to multiples of 4 (whole float4 groups of the march)
     int4 z{std::max(in.i0 - M, 0) & ~3, std::max(in.j0 - M, 0), std::min((in.i0 + in.a + M + 3) & ~3, sh.nx),
            std::min(in.j0 + in.b + M, sh.ny)};
@@ -1142,12 +1222,20 @@ int plan_tb(fdtd_ctx* ctx) {
     // against 280.1 Gcell-steps/s for 3 CTAs at 162 registers, 4096^2)
     ctx->tbm_mb = 4;
     if (const char* em = getenv("FDTD_TB_MB")) ctx->tbm_mb = atoi(em) == 3 ? 3 : 4;
-    if (ctx->tbm_mb == 4)
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, yee_tb2m_kernel<4>, 128, 0);
-    else
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, yee_tb2m_kernel<3>, 128, 0);
-    const long long slots =
-        std::max((long long)nsm, (long long)nsm * std::max(occ, 1) - 2 * (long long)ctx->insts.size());
+    ctx->tbm_ring = 0;
+    if (const char* eg = getenv("FDTD_TB_RING")) ctx->tbm_ring = std::min(4, std::max(0, atoi(eg)));
+    if (ctx->ov_ring >= 0) ctx->tbm_ring = ctx->ov_ring;
+    if (ctx->tbm_ring == 1 || ctx->tbm_mb == 3) ctx->tbm_ring = 0;
+    if (ctx->tbm_ring > 0)
+      CK(cudaFuncSetAttribute(march_fn(4, ctx->tbm_ring), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)march_smem(ctx->tbm_ring)));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, march_fn(ctx->tbm_mb, ctx->tbm_ring), 128,
+                                                  march_smem(ctx->tbm_ring));
+    // (a zone chain takes one slot per SM while its kernels run)
+    long long nfused = 0;
+    for (size_t k = 0; k < ninst; ++k) nfused += chain[k] ? 0 : 1;
+    const long long slots = std::max((long long)nsm, (long long)nsm * std::max(occ, 1) - 2 * nfused -
+                                                         (nfused < (long long)ninst ? (long long)nsm : 0));
     auto tiles_for = [&](int th) {
       long long t = 0;
       for (const SimHost& sh : ctx->sims)
@@ -1161,6 +1249,7 @@ int plan_tb(fdtd_ctx* ctx) {
       if (best < 0 || cost < best) best = cost, th = h;
     }
     if (const char* er = getenv("FDTD_TB_ROWS")) th = std::min(4096, std::max(4, atoi(er)));
+    if (ctx->ov_thm) th = ctx->ov_thm;
     ctx->tbm_pf = 0;
     if (const char* ep = getenv("FDTD_TB_PF")) ctx->tbm_pf = std::min(16, std::max(0, atoi(ep)));
     ctx->tbm_th = th;
@@ -1216,9 +1305,48 @@ int plan_tb(fdtd_ctx* ctx) {
         }
     }
   }
-  for (size_t k = 0; k < ctx->insts.size(); ++k) {
-    const int4 z = zone[k];
-    ctx->tb_tiles.push_back({ctx->insts[k].sim, z.x, z.z, z.y, z.w, (int)k, 0, 0, 0, 0, 0, 0});
+  // model tiles: the fused ones first, then the zone chain's (each with its
+  // window's scratch: Ex, Ey, Hz after the first sub-step)
+  size_t scr = 0, zsm = 0, csm = 0;
+  ctx->tb_nchain = 0;
+  for (int pass = 0; pass < 2; ++pass)
+    for (size_t k = 0; k < ninst; ++k) {
+      if ((int)chain[k] != pass) continue;
+      const int4 z = zone[k];
+      TbTile t{ctx->insts[k].sim, z.x, z.z, z.y, z.w, (int)k, 0, 0, 0, 0, 0, 0, 0};
+      if (pass == 1) {
+        const size_t nf = (size_t)zone_rows(z.y, z.w) * 4 * zone_sw4(z.x, z.z);
+        t.scr = (int)(scr / 4);
+        scr += 3 * nf;
+        zsm = std::max(zsm, sizeof(float) * 5 * nf);
+        const int ld = ctx->insts[k].map->ld;
+        csm = std::max(csm, sizeof(float) * (k < ctx->in_gemm.size() && ctx->in_gemm[k] ? gemm_smem_floats(ld)
+                                                                                          : (size_t)ld));
+        ++ctx->tb_nchain;
+      }
+      ctx->tb_tiles.push_back(t);
+    }
+  ctx->chain_nrow = 0;
+  if (ctx->tb_nchain > 0) {
+    if (scr > (size_t)INT32_MAX * 4) return fail(ctx, FDTD_EINVAL, "zone scratch too large");
+    CK(ctx->zone_scratch.reserve(scr));
+    // single models of the chain are the one-step path's row-per-warp work
+    // (every model outside a GEMM group); shared maps its GEMM tiles
+    if (ctx->tb_chain_mode == 1) ctx->chain_nrow = ctx->nromwork;
+    ctx->zone_smem = zsm;
+    ctx->chain_smem = csm;
+    if (zsm > 200 * 1024 || csm > 200 * 1024) return fail(ctx, FDTD_EINVAL, "zone chain too large for shared memory");
+    CK(cudaFuncSetAttribute(zone_step_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zsm));
+    CK(cudaFuncSetAttribute(zone_step_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zsm));
+    CK(cudaFuncSetAttribute(rom_chain_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max(csm, (size_t)16)));
+    if (!ctx->side_stream) {
+      int lo = 0, hi = 0;
+      CK(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+      ctx->prio_hi = hi;
+      CK(cudaStreamCreateWithPriority(&ctx->side_stream, cudaStreamNonBlocking, hi));
+      CK(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
+      CK(cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming));
+    }
   }
   cudaFree(ctx->tb_zones_d);
   ctx->tb_zones_d = nullptr;
@@ -1236,18 +1364,21 @@ int plan_tb(fdtd_ctx* ctx) {
 // Instances are stepped either one row per warp (rom_post_kernel's first
 // block range) or, when at least FDTD_ROM_GEMM_MIN (default 20) of them share
 // one coupled map, as one GEMM over the shared [P | Q] (second range; 8 or
-// 32 rows x up to 32 simulations per CTA, FDTD_GEMM_RPW = 1 or 4).
+// 16 rows x up to 32 simulations per CTA, FDTD_GEMM_RPW = 1 or 2).  Both
+// forms give the same bits.
 int upload_instances(fdtd_ctx* ctx) {
   std::vector<RomInstDev> h(ctx->insts.size());
   std::vector<RomWork> wk;
   size_t smem = 0;
   int gemm_min = 20;   // measured: below ~20 simulations per map one row per warp is as fast or faster
   if (const char* e = getenv("FDTD_ROM_GEMM_MIN")) gemm_min = std::max(1, atoi(e));
-  // rows per warp of the GEMM form: 4 when the map is shared by >= 32
+  if (ctx->ov_gemm_min) gemm_min = ctx->ov_gemm_min;
+  // rows per warp of the GEMM form: 2 when the map is shared by >= 32
   // simulations (the panel is re-staged less often), else 1 (more CTAs);
-  // FDTD_GEMM_RPW = 1 or 4 overrides (same results, speed only)
+  // FDTD_GEMM_RPW = 1 or 2 overrides (same results, speed only)
   int rpw_env = 0;
-  if (const char* e = getenv("FDTD_GEMM_RPW")) rpw_env = atoi(e) == 4 ? 4 : 1;
+  if (const char* e = getenv("FDTD_GEMM_RPW")) rpw_env = atoi(e) == 2 ? 2 : 1;
+  if (ctx->ov_rpw) rpw_env = ctx->ov_rpw;
   std::vector<const CoupledMap*> maps;
   std::vector<std::vector<int>> members;
   for (size_t k = 0; k < ctx->insts.size(); ++k) {
@@ -1263,22 +1394,22 @@ int upload_instances(fdtd_ctx* ctx) {
   std::vector<char> in_gemm(ctx->insts.size(), 0);
   for (size_t g = 0; g < maps.size(); ++g) {
     if ((int)members[g].size() < gemm_min) continue;
-    const int gemm_rpw = rpw_env ? rpw_env : ((int)members[g].size() >= 32 ? 4 : 1);
+    const int gemm_rpw = rpw_env ? rpw_env : ((int)members[g].size() >= 32 ? 2 : 1);
     // the GEMM's shared-memory panel must fit one CTA; else row per warp
-    if (sizeof(float) * gemm_smem_floats(maps[g]->ld, gemm_rpw) > 200 * 1024) continue;
+    if (sizeof(float) * gemm_smem_floats(maps[g]->ld) > 200 * 1024) continue;
     const Instance& in0 = ctx->insts[members[g][0]];
     GemmGroupDev gd{maps[g]->M_d, in0.n, in0.ny, maps[g]->ld, (int)members[g].size(), (int)ginst.size(), gemm_rpw, 0, 0};
     for (int k : members[g]) ginst.push_back(k), in_gemm[k] = 1;
     for (int r0 = 0; r0 < gd.n; r0 += gemm_rpw * kRomRowsPerCta)
       for (int c0 = 0; c0 < gd.B; c0 += 32) gwork.push_back({(int)groups.size(), r0, c0, 0});
     groups.push_back(gd);
-    smem = std::max(smem, sizeof(float) * gemm_smem_floats(gd.ld, gemm_rpw));
+    smem = std::max(smem, sizeof(float) * gemm_smem_floats(gd.ld));
   }
   for (size_t k = 0; k < ctx->insts.size(); ++k) {
     const Instance& in = ctx->insts[k];
     RomInstDev& d = h[k];
     d.M = in.map->M_d;
-    d.state[0] = in.state_d[0], d.state[1] = in.state_d[1];
+    d.state[0] = in.state_d[0], d.state[1] = in.state_d[1], d.state_mid = in.state_d[2];
     d.y_edge = in.y_edge_d, d.h_cell = in.h_cell_d;
     d.n = in.n, d.ny = in.ny, d.ld = in.map->ld, d.sim = in.sim;
     if (in_gemm[k]) continue;
@@ -1323,6 +1454,7 @@ int upload_instances(fdtd_ctx* ctx) {
     }
   }
   ctx->nromwork = (int)wk.size();
+  ctx->in_gemm = in_gemm;
   ctx->post_smem = smem;
   if (smem > 48 * 1024) {
     if (smem > 200 * 1024) return fail(ctx, FDTD_EINVAL, "reduced model too large for one CTA's shared memory");
@@ -1334,20 +1466,36 @@ int upload_instances(fdtd_ctx* ctx) {
 
 // Launch with the programmatic-serialisation attribute when pdl is set (the
 // kernel's prologue may overlap the previous kernel's tail; see pdl_wait).
+// The priority form sets the launch's scheduling priority (kept by a graph
+// node captured from it).
 template <typename... KArgs, typename... Args>
 void launch_k(void (*k)(KArgs...), unsigned grid, unsigned block, size_t smem, cudaStream_t s, bool pdl,
-              Args... args) {
+              int prio, Args... args) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(block);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchAttribute at[2];
+  int na = 0;
+  if (pdl) {
+    at[na].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[na].val.programmaticStreamSerializationAllowed = 1;
+    ++na;
+  }
+  if (prio != 0) {
+    at[na].id = cudaLaunchAttributePriority;
+    at[na].val.priority = prio;
+    ++na;
+  }
   cfg.attrs = at;
-  cfg.numAttrs = pdl ? 1 : 0;
+  cfg.numAttrs = na;
   cudaLaunchKernelEx(&cfg, k, args...);
+}
+template <typename... KArgs, typename... Args>
+void launch_k(void (*k)(KArgs...), unsigned grid, unsigned block, size_t smem, cudaStream_t s, bool pdl,
+              Args... args) {
+  launch_k(k, grid, block, smem, s, pdl, 0, args...);
 }
 
 void launch_yee(fdtd_ctx* ctx, cudaStream_t s, int par, int c) {
@@ -1715,15 +1863,44 @@ int march_timed(fdtd_ctx* ctx, long long nsteps, int nprobe) {
   return FDTD_OK;
 }
 
+// The zone chain of one pair of steps on the side stream (highest priority,
+// so that its blocks are scheduled ahead of the march's pending ones),
+// forked from and joined back into s: half 0, map, half 1, map.
+void launch_chain(fdtd_ctx* ctx, cudaStream_t s, int par, int c) {
+  const unsigned nz = (unsigned)ctx->tb_nchain;
+  const TbTile* zt = ctx->tb_tiles_d + (ctx->tb_tiles.size() - nz);
+  cudaStream_t q = ctx->side_stream;
+  cudaEventRecord(ctx->ev_fork, s);
+  cudaStreamWaitEvent(q, ctx->ev_fork, 0);
+  const unsigned nmap = (unsigned)(ctx->chain_nrow + ctx->ngwork);
+  launch_k(zone_step_kernel<0>, nz, kTbThreads, ctx->zone_smem, q, false, ctx->prio_hi, (const SimDev*)ctx->sims_d,
+           zt, (const RomInstDev*)ctx->insts_d, (const RunDev*)ctx->run_d, (const TbRun*)ctx->tb_run_d,
+           ctx->zone_scratch.p, par, c);
+  launch_k(rom_chain_kernel, nmap, kRomRowsPerCta * 32, ctx->chain_smem, q, false, ctx->prio_hi,
+           (const SimDev*)ctx->sims_d, (const RomInstDev*)ctx->insts_d, (const RomWork*)ctx->romwork_d,
+           ctx->chain_nrow, (const GemmGroupDev*)ctx->groups_d, (const GemmWork*)ctx->gwork_d,
+           (const int*)ctx->ginst_d, par, 0);
+  launch_k(zone_step_kernel<1>, nz, kTbThreads, ctx->zone_smem, q, false, ctx->prio_hi, (const SimDev*)ctx->sims_d,
+           zt, (const RomInstDev*)ctx->insts_d, (const RunDev*)ctx->run_d, (const TbRun*)ctx->tb_run_d,
+           ctx->zone_scratch.p, par, c);
+  launch_k(rom_chain_kernel, nmap, kRomRowsPerCta * 32, ctx->chain_smem, q, false, ctx->prio_hi,
+           (const SimDev*)ctx->sims_d, (const RomInstDev*)ctx->insts_d, (const RomWork*)ctx->romwork_d,
+           ctx->chain_nrow, (const GemmGroupDev*)ctx->groups_d, (const GemmWork*)ctx->gwork_d,
+           (const int*)ctx->ginst_d, par, 1);
+  cudaEventRecord(ctx->ev_join, q);
+}
+
 void launch_tb(fdtd_ctx* ctx, cudaStream_t s, int par, int c) {
-  const unsigned ntb = (unsigned)ctx->tb_tiles.size();
+  const unsigned ntb = (unsigned)(ctx->tb_tiles.size() - ctx->tb_nchain);   // ordinary and fused model tiles
+  if (ctx->tb_nchain > 0) launch_chain(ctx, s, par, c);
   if (ntb > 0)
     yee_tb2_kernel<<<ntb, kTbThreads, kTbSmemFields, s>>>(ctx->sims_d, ctx->tb_tiles_d, ctx->insts_d, ctx->run_d,
                                                           ctx->tb_run_d, par, c);
   if (ctx->tb_march)   // overlaps the model tiles (programmatic serialisation) when there are any
-    launch_k(ctx->tbm_mb == 4 ? yee_tb2m_kernel<4> : yee_tb2m_kernel<3>, (unsigned)ctx->tbm_tiles.size(), 128, 0, s,
+    launch_k(march_fn(ctx->tbm_mb, ctx->tbm_ring), (unsigned)ctx->tbm_tiles.size(), 128, march_smem(ctx->tbm_ring), s,
              ctx->pdl && ntb > 0, (const SimDev*)ctx->sims_d, (const TileWork*)ctx->tbm_tiles_d,
              (const RunDev*)ctx->run_d, (const TbMarchDev*)ctx->tbm_d, par, c, ctx->tbm_pf);
+  if (ctx->tb_nchain > 0) cudaStreamWaitEvent(s, ctx->ev_join, 0);
 }
 
 int ensure_tb_graph(fdtd_ctx* ctx, int par, int nprobe) {
@@ -1843,6 +2020,7 @@ void plan_tiles(fdtd_ctx* ctx) {
   int best = best_tile_rows(ctx->sims, slots);
   if (const char* e = getenv("FDTD_TILE_ROWS"))
     best = std::min(512, std::max(4, atoi(e)));   // <= 512: one warp's 32 bit words cover a tile
+  if (ctx->ov_th1) best = ctx->ov_th1;
   ctx->tiles.clear();
   for (int s = 0; s < (int)ctx->sims.size(); ++s) {
     SimHost& sh = ctx->sims[s];
@@ -1881,6 +2059,7 @@ int static_energy_scratch(fdtd_ctx* ctx, double** ptr) {
 }  // namespace
 
 #include "adjoint.cuh"
+#include "tune.cuh"
 
 // ============================================================== C ABI
 
@@ -1914,8 +2093,7 @@ void fdtd_destroy(fdtd_ctx* ctx) {
     cudaFree(s.mbits_d);
   }
   for (Instance& in : ctx->insts) {
-    cudaFree(in.state_d[0]);
-    cudaFree(in.state_d[1]);
+    for (float* p : in.state_d) cudaFree(p);
     cudaFree(in.y_edge_d);
     cudaFree(in.h_cell_d);
   }
@@ -1967,6 +2145,10 @@ void fdtd_destroy(fdtd_ctx* ctx) {
     cudaFree(b.V2);
   }
   for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
+  ctx->zone_scratch.release();
+  if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+  if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+  if (ctx->side_stream) cudaStreamDestroy(ctx->side_stream);
   if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
   delete ctx;
 }
@@ -2057,6 +2239,7 @@ int fdtd_create(const fdtd_grid_desc* g, void* cuda_stream, fdtd_ctx** out) {
   }
   plan_tiles(ctx);
   if (const char* e = getenv("FDTD_TB")) ctx->tb_mode = atoi(e) != 0 ? 1 : 0;   // fixed for the context
+  if (const char* e = getenv("FDTD_TB_CHAIN")) ctx->tb_chain_mode = atoi(e) != 0 ? 1 : 0;
   if (plan_tb(ctx) != FDTD_OK) return bail(FDTD_ECUDA);
   if (cudaMalloc(&ctx->sims_d, sizeof(SimDev) * sdev.size()) != cudaSuccess ||
       cudaMalloc(&ctx->tiles_d, sizeof(TileWork) * ctx->tiles.size()) != cudaSuccess ||
@@ -2160,12 +2343,14 @@ int rom_embed(fdtd_ctx* ctx, const rom_model* m, int sim, int i0, int j0, int* i
     in.y_edge.push_back((in.itf.comp[k] << 30) | (in.itf.ej[k] * sh.pitch + in.itf.ei[k]));
     in.h_cell.push_back(in.itf.hj[k] * sh.pitch + in.itf.hi[k]);
   }
-  CK(cudaMalloc(&in.state_d[0], sizeof(float) * in.n));
-  CK(cudaMalloc(&in.state_d[1], sizeof(float) * in.n));
+  // [y; x~] padded to ld floats: the two-step path's maps outside the tile
+  // read the whole input vector [y; x~; h; 0] from it (the padding stays 0)
+  for (int p = 0; p < 3; ++p) {
+    CK(cudaMalloc(&in.state_d[p], sizeof(float) * in.map->ld));
+    CK(cudaMemset(in.state_d[p], 0, sizeof(float) * in.map->ld));
+  }
   CK(cudaMalloc(&in.y_edge_d, sizeof(int) * in.ny));
   CK(cudaMalloc(&in.h_cell_d, sizeof(int) * in.ny));
-  CK(cudaMemset(in.state_d[0], 0, sizeof(float) * in.n));
-  CK(cudaMemset(in.state_d[1], 0, sizeof(float) * in.n));
   CK(cudaMemcpy(in.y_edge_d, in.y_edge.data(), sizeof(int) * in.ny, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(in.h_cell_d, in.h_cell.data(), sizeof(int) * in.ny, cudaMemcpyHostToDevice));
   // Mark the covered cells and zero every field on and inside the region.
@@ -2374,7 +2559,26 @@ int fdtd_grad(fdtd_ctx* ctx, long long nsteps, const fdtd_source* src, int nsrc,
   NvtxRange nvtx_("fdtd_grad");
   if (!ctx) return fail(ctx, FDTD_EINVAL, "fdtd_grad: null context");
   if (ctx->timing) return fail(ctx, FDTD_EINVAL, "fdtd_grad: switch timing off first");
-  return run_grad(ctx, nsteps, src, nsrc, probes, nprobe, ckpt_every, dJ_deps, dJ_dsigma, dJ_dsrc, J_out);
+  return run_grad(ctx, nsteps, src, nsrc, probes, nprobe, ckpt_every, dJ_deps, dJ_dsigma, dJ_dsrc, J_out,
+                  false, nullptr, nullptr);
+}
+
+int fdtd_vjp(fdtd_ctx* ctx, long long nsteps, const fdtd_source* src, int nsrc, const fdtd_probe* probes,
+             int nprobe, int ckpt_every, const float* dL_dprobe, float* dL_deps, float* dL_dsigma,
+             float* dL_dsrc, float* probe_out) {
+  NvtxRange nvtx_("fdtd_vjp");
+  if (!ctx) return fail(ctx, FDTD_EINVAL, "fdtd_vjp: null context");
+  if (ctx->timing) return fail(ctx, FDTD_EINVAL, "fdtd_vjp: switch timing off first");
+  if (nprobe > 0 && !dL_dprobe) return fail(ctx, FDTD_EINVAL, "fdtd_vjp: null cotangent");
+  return run_grad(ctx, nsteps, src, nsrc, probes, nprobe, ckpt_every, dL_deps, dL_dsigma, dL_dsrc, nullptr,
+                  true, dL_dprobe, probe_out);
+}
+
+int fdtd_autotune(fdtd_ctx* ctx, const char* cache_path, fdtd_tune_report* report) {
+  NvtxRange nvtx_("fdtd_autotune");
+  if (!ctx) return set_global_error(FDTD_EINVAL, "fdtd_autotune: null context");
+  if (ctx->timing) return fail(ctx, FDTD_EINVAL, "fdtd_autotune: switch timing off first");
+  return run_autotune(ctx, cache_path, report);
 }
 
 int fdtd_set_timing(fdtd_ctx* ctx, int on) {
@@ -2405,6 +2609,68 @@ int fdtd_get_kernel_times(fdtd_ctx* ctx, double* yee_ms, long long* yee_launches
   if (post_ms) *post_ms = ctx->t_post;
   if (post_launches) *post_launches = ctx->n_post;
   return FDTD_OK;
+}
+
+// Device time of the stencil kernel alone: a graph of back-to-back launches
+// (no per-kernel events, no programmatic overlap between them) that read the
+// current fields and write the other ping-pong copy, replayed reps times
+// between two events.  The current fields and the step counter are not
+// changed; the other copy is scratch until the next step overwrites it.
+int fdtd_time_stencil(fdtd_ctx* ctx, int launches, int reps, double* ms_per_launch) {
+  NvtxRange nvtx_("fdtd_time_stencil");
+  if (!ctx || launches < 1 || reps < 1 || !ms_per_launch)
+    return fail(ctx, FDTD_EINVAL, "fdtd_time_stencil: bad argument");
+  if (ctx->timing) return fail(ctx, FDTD_EINVAL, "fdtd_time_stencil: switch timing off first");
+  // run tables without sources or probes (all the stencil reads of a run)
+  int rc = prepare_run(ctx, 2, nullptr, 0, nullptr, nullptr, 0, nullptr);
+  if (rc) return rc;
+  const int par = ctx->cur;
+  const int nord = (int)ctx->tb_tiles.size() - (int)ctx->insts.size();   // shared-memory two-step: ordinary tiles
+  struct Res {
+    cudaGraphExec_t ge = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    ~Res() {
+      if (ge) cudaGraphExecDestroy(ge);
+      if (e0) cudaEventDestroy(e0);
+      if (e1) cudaEventDestroy(e1);
+    }
+  } r;
+  cudaStream_t cs = ctx->capture_stream;
+  cudaGraph_t g = nullptr;
+  CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+  for (int k = 0; k < launches; ++k) {
+    if (ctx->tb && ctx->tb_march)
+      launch_k(march_fn(ctx->tbm_mb, ctx->tbm_ring), (unsigned)ctx->tbm_tiles.size(), 128,
+               march_smem(ctx->tbm_ring), cs, false, (const SimDev*)ctx->sims_d, (const TileWork*)ctx->tbm_tiles_d, (const RunDev*)ctx->run_d,
+               (const TbMarchDev*)ctx->tbm_d, par, 0, ctx->tbm_pf);
+    else if (ctx->tb && nord > 0)
+      yee_tb2_kernel<<<nord, kTbThreads, kTbSmemFields, cs>>>(ctx->sims_d, ctx->tb_tiles_d, ctx->insts_d, ctx->run_d,
+                                                              ctx->tb_run_d, par, 0);
+    else if (ctx->stencil_tma)
+      yee_step_tma_kernel<<<(unsigned)ctx->tiles.size(), kCtaCols / 4, kTmaSmem, cs>>>(ctx->sims_d, ctx->tiles_d,
+                                                                                      ctx->run_d, par, 0);
+    else if (ctx->vec == 2)
+      launch_k(yee_step_kernel<2>, (unsigned)ctx->tiles.size(), kCtaCols / 2, 0, cs, false, (const SimDev*)ctx->sims_d,
+               (const TileWork*)ctx->tiles_d, (const RunDev*)ctx->run_d, par, 0);
+    else
+      launch_k(yee_step_kernel<4>, (unsigned)ctx->tiles.size(), kCtaCols / 4, 0, cs, false, (const SimDev*)ctx->sims_d,
+               (const TileWork*)ctx->tiles_d, (const RunDev*)ctx->run_d, par, 0);
+  }
+  CK(cudaStreamEndCapture(cs, &g));
+  const cudaError_t ei = cudaGraphInstantiate(&r.ge, g, 0);
+  cudaGraphDestroy(g);
+  if (ei != cudaSuccess) return fail(ctx, FDTD_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(ei));
+  CK(cudaEventCreate(&r.e0));
+  CK(cudaEventCreate(&r.e1));
+  CK(cudaGraphLaunch(r.ge, ctx->stream));   // warm-up replay
+  CK(cudaEventRecord(r.e0, ctx->stream));
+  for (int k = 0; k < reps; ++k) CK(cudaGraphLaunch(r.ge, ctx->stream));
+  CK(cudaEventRecord(r.e1, ctx->stream));
+  CK(cudaEventSynchronize(r.e1));
+  float ms = 0.f;
+  CK(cudaEventElapsedTime(&ms, r.e0, r.e1));
+  *ms_per_launch = (double)ms / ((double)reps * launches);
+  return check_status(ctx);
 }
 
 // State buffer: magic, step, cur-independent field copies (Ex, Ey, Hz per

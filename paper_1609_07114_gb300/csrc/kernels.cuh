@@ -56,7 +56,8 @@ struct SrcEdge {    // one driven edge
 
 struct RomInstDev {
   const float* M;     // n x ld row-major: [P | Q | 0], ld = roundup(n + ny, 4)
-  float* state[2];    // [y; x~], ping-ponged with the fields
+  float* state[2];    // [y; x~] (ld floats: [y; x~; h; 0]), ping-ponged with the fields
+  float* state_mid;   // two-step path, maps outside the tile: [y; x~; h]^{n+1} between the sub-steps
   const int* y_edge;  // ny: (comp << 30) | (j * pitch + i)
   const int* h_cell;  // ny: j * pitch + i
   int n, ny, ld, sim;
@@ -70,7 +71,7 @@ constexpr int kRomRowsPerCta = 8;   // one row per warp
 struct GemmGroupDev {
   const float* M;       // [P | Q | 0], n x ld
   int n, ny, ld, B;     // B instances, listed at ginst[inst_off ...]
-  int inst_off, rpw;    // rpw: rows per warp of the CTA tiles (1 or 4)
+  int inst_off, rpw;    // rpw: rows per warp of the CTA tiles (1 or 2)
   int pad1, pad2;
 };
 

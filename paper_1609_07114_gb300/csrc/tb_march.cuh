@@ -131,10 +131,51 @@ __device__ __forceinline__ float pick4(const float (&v)[4], int t) {
   return t == 0 ? v[0] : (t == 1 ? v[1] : (t == 2 ? v[2] : v[3]));
 }
 
-template <int kMinBlocks>
+// Staged form of the loads (kRing >= 2 rows): each lane copies its own five
+// float4 of a row into its warp's ring in shared memory with cp.async, kRing - 1
+// rows ahead of the row it computes, one commit group per row; the copies in
+// flight hold no registers and the compiler cannot sink them.  A lane reads
+// back only what it copied itself, so waiting on its own groups suffices.
+// Ring layout: [warp][slot][5 values][32 lanes] float4.
+constexpr int kMarchRingBytesPerRow = 4 * 5 * 32 * 16;   // four warps
+
+__device__ __forceinline__ void march_issue(float4* slot, const float* __restrict__ ex, const float* __restrict__ ey,
+                                            const float* __restrict__ hz, const float2* __restrict__ mat, int j, int ny,
+                                            int P, int cl, bool inb, int lane) {
+  asm volatile("" ::: "memory");   // after the reads of the slot's previous row
+  const bool ok = inb && j < ny;
+  const size_t row = ok ? (size_t)j * P + cl : 0;
+  cp_async16(slot + 0 * 32 + lane, ok ? ex + row + P : ex, ok);
+  cp_async16(slot + 1 * 32 + lane, ey + row, ok);
+  cp_async16(slot + 2 * 32 + lane, hz + row, ok);
+  cp_async16(slot + 3 * 32 + lane, mat + row, ok);
+  cp_async16(slot + 4 * 32 + lane, mat + row + 2, ok);
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+
+__device__ __forceinline__ void march_fetch(MarchIn& r, const float4* slot, int j, int ny, bool inb, int lane) {
+  if (inb && j < ny) {
+    r.exn = slot[0 * 32 + lane];
+    r.eyv = slot[1 * 32 + lane];
+    r.hzv = slot[2 * 32 + lane];
+    r.ma = slot[3 * 32 + lane];
+    r.mb = slot[4 * 32 + lane];
+  } else {
+    r.exn = r.eyv = r.hzv = make_float4(0.f, 0.f, 0.f, 0.f);
+    r.ma = r.mb = make_float4(-1.f, 0.f, -1.f, 0.f);
+  }
+}
+
+template <int N>
+__device__ __forceinline__ void cp_async_wait_n() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+template <int kMinBlocks, int kRing>
 __global__ void __launch_bounds__(128, kMinBlocks)
 yee_tb2m_kernel(const SimDev* __restrict__ sims, const TileWork* __restrict__ tiles,
                 const RunDev* __restrict__ run, const TbMarchDev* __restrict__ tm, int par, int c, int pf) {
+  extern __shared__ float4 march_ring[];
   const unsigned FULL = 0xffffffffu;
   const TileWork tw = tiles[blockIdx.x];
   const SimDev sd = sims[tw.sim];
@@ -191,10 +232,28 @@ yee_tb2m_kernel(const SimDev* __restrict__ sims, const TileWork* __restrict__ ti
     }
   }
   MarchIn cur, nxt;
-  march_load(cur, ex, ey, hz, mat, jA0, ny, P, cl, inb);
+  float4* ring = march_ring + (size_t)warp * (kRing > 0 ? kRing : 1) * 5 * 32;
+  int slot = 0;
+  if constexpr (kRing > 0) {
+#pragma unroll
+    for (int d = 0; d < kRing - 1; ++d) march_issue(ring + d * 5 * 32, ex, ey, hz, mat, jA0 + d, ny, P, cl, inb, lane);
+  } else {
+    march_load(cur, ex, ey, hz, mat, jA0, ny, P, cl, inb);
+  }
   for (int j = jA0; j <= jAe; ++j) {
-    if (pf > 0 && j + pf <= jAe && j + pf < ny) march_prefetch(ex, ey, hz, mat, j + pf, P, c0, lane);
-    if (j + 1 <= jAe) march_load(nxt, ex, ey, hz, mat, j + 1, ny, P, cl, inb);
+    if constexpr (kRing > 0) {
+      int ahead = slot + kRing - 1;
+      ahead -= ahead >= kRing ? kRing : 0;
+      // row j + kRing - 1 (past the tile: an empty group, so the count stays uniform)
+      if (j + kRing - 1 <= jAe) march_issue(ring + ahead * 5 * 32, ex, ey, hz, mat, j + kRing - 1, ny, P, cl, inb, lane);
+      else asm volatile("cp.async.commit_group;\n" ::: "memory");
+      cp_async_wait_n<kRing - 1>();
+      march_fetch(cur, ring + slot * 5 * 32, j, ny, inb, lane);
+      slot = slot + 1 == kRing ? 0 : slot + 1;
+    } else {
+      if (pf > 0 && j + pf <= jAe && j + pf < ny) march_prefetch(ex, ey, hz, mat, j + pf, P, c0, lane);
+      if (j + 1 <= jAe) march_load(nxt, ex, ey, hz, mat, j + 1, ny, P, cl, inb);
+    }
     const float2 m[4] = {make_float2(cur.ma.x, cur.ma.y), make_float2(cur.ma.z, cur.ma.w),
                          make_float2(cur.mb.x, cur.mb.y), make_float2(cur.mb.z, cur.mb.w)};
     // ---- A.H: Hz^{n+1/2}(j) (Eq. (5))
@@ -320,12 +379,27 @@ yee_tb2m_kernel(const SimDev* __restrict__ sims, const TileWork* __restrict__ ti
       cyr[t] = nyr[t];
     }
     lmask = nmask;
-    cur = nxt;
+    if constexpr (kRing == 0) cur = nxt;
   }
   // Launched after the model tiles of the same two steps (which it does not
   // read) with programmatic serialisation: it may start while they run, and
   // it does not complete before them, so the next launch sees both.
   pdl_wait();
 }
+
+using MarchFn = void (*)(const SimDev*, const TileWork*, const RunDev*, const TbMarchDev*, int, int, int);
+
+// The row-marching kernel compiled for mb resident CTAs per SM, with loads
+// in registers (ring 0) or staged through a ring of 2-4 rows.
+MarchFn march_fn(int mb, int ring) {
+  if (mb == 3) return yee_tb2m_kernel<3, 0>;
+  switch (ring) {
+    case 2: return yee_tb2m_kernel<4, 2>;
+    case 3: return yee_tb2m_kernel<4, 3>;
+    case 4: return yee_tb2m_kernel<4, 4>;
+    default: return yee_tb2m_kernel<4, 0>;
+  }
+}
+size_t march_smem(int ring) { return ring > 0 ? (size_t)ring * kMarchRingBytesPerRow : 0; }
 
 }  // namespace

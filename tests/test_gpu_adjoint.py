@@ -12,7 +12,7 @@ if not torch.cuda.is_available():
     pytest.skip("no CUDA device", allow_module_level=True)
 
 import paper_1609_07114_gb300 as pg
-from paper_1609_07114_gb300.autograd import ProbeEnergy, ProbeEnergySpec
+from paper_1609_07114_gb300.autograd import FdtdFn, FdtdSpec, probe_energy
 import workloads
 from oracle import adjoint
 
@@ -95,23 +95,123 @@ def test_batch_gradients_are_per_simulation():
     assert abs(J - Jt) < 1e-4 * Jt
 
 
-def test_autograd_function():
+def _autograd_case(ws, nsteps, ckpt=40):
+    """FdtdSpec and leaf tensors (eps, sigma, waves) of a batch of workloads
+    with one grid size; models are built per simulation."""
+    w0 = ws[0]
+    roms = [[(pg.rom_build(rd["a"], rd["b"], rd["r"], w["dx"], w["dy"], w["dt"], rd["eps_r"], rd["sigma"],
+                           rd["q"], f0=rd["f0"]), rd["i0"], rd["j0"]) for rd in w["roms"]] for w in ws]
+    spec = FdtdSpec(w0["dx"], w0["dy"], w0["dt"], nsteps,
+                    [[{k: v for k, v in so.items() if k != "wave"} for so in w["sources"]] for w in ws],
+                    [list(w["probes"]) for w in ws], roms, ckpt_every=ckpt)
+    eps = torch.tensor(np.stack([w["eps_r"] for w in ws]), requires_grad=True)
+    sig = torch.tensor(np.stack([w["sigma"] for w in ws]), requires_grad=True)
+    wav = torch.tensor(np.stack([np.stack([so["wave"][:nsteps] for so in w["sources"]]) for w in ws])
+                       .astype(np.float32), requires_grad=True)
+    return spec, eps, sig, wav
+
+
+def test_autograd_probe_energy():
+    """J = sum of probe Hz^2 through FdtdFn (forward: the probe series) and
+    autograd (backward: fdtd_vjp seeded with dJ/dprobes = 2 o), against the
+    FP64 oracle adjoint."""
     w = grad_case(seed=64, nx=60, ny=50, nsteps=120)
-    models = [(pg.rom_build(rd["a"], rd["b"], rd["r"], w["dx"], w["dy"], w["dt"], rd["eps_r"], rd["sigma"],
-                            rd["q"], f0=rd["f0"]), rd["i0"], rd["j0"]) for rd in w["roms"]]
-    spec = ProbeEnergySpec(w["dx"], w["dy"], w["dt"], 120,
-                           [{k: v for k, v in s.items() if k != "wave"} for s in w["sources"]],
-                           w["probes"], models, ckpt_every=40)
-    eps = torch.tensor(w["eps_r"], requires_grad=True)
-    sig = torch.tensor(w["sigma"], requires_grad=True)
-    wav = torch.tensor(np.stack([s["wave"][:120] for s in w["sources"]]).astype(np.float32), requires_grad=True)
-    J = ProbeEnergy.apply(eps, sig, wav, spec)
+    spec, eps, sig, wav = _autograd_case([w], 120)
+    J = probe_energy(eps, sig, wav, spec)
     (3.0 * J).backward()
     Jo, deps, dsig, gsrc = adjoint.gradients(w, 120)
     assert abs(float(J) - Jo) < 1e-4 * Jo
-    assert rel_l2(eps.grad.numpy() / 3.0, deps) < GTOL
-    assert rel_l2(sig.grad.numpy() / 3.0, dsig) < GTOL
-    assert rel_l2(wav.grad.numpy()[0] / 3.0, gsrc[0]) < GTOL
+    assert rel_l2(eps.grad.numpy()[0] / 3.0, deps) < GTOL
+    assert rel_l2(sig.grad.numpy()[0] / 3.0, dsig) < GTOL
+    assert rel_l2(wav.grad.numpy()[0, 0] / 3.0, gsrc[0]) < GTOL
+
+
+def test_autograd_linear_functional_of_probes():
+    """L = sum c * probes with a random cotangent c: torch.autograd.grad
+    through fdtd_vjp against the oracle adjoint seeded with the same c
+    (pinned by central differences)."""
+    N = 150
+    w = grad_case(seed=66, nx=90, ny=70, nsteps=N)
+    spec, eps, sig, wav = _autograd_case([w], N)
+    c = np.random.default_rng(3).standard_normal((N, len(w["probes"])))
+    probes = FdtdFn.apply(eps, sig, wav, spec)
+    assert probes.shape == (1, N, len(w["probes"]))
+    L = (torch.tensor(c[None], device="cuda") * probes.double()).sum()
+    ge, gs, gw = torch.autograd.grad(L, (eps, sig, wav))
+    Lo, deps, dsig, gsrc = adjoint.gradients(w, N, cotangent=c)
+    scale = float((np.abs(c)[None] * probes.detach().cpu().double().abs().numpy()).sum())
+    assert abs(float(L) - Lo) < 1e-4 * scale
+    assert rel_l2(ge.numpy()[0], deps) < GTOL
+    assert rel_l2(gs.numpy()[0], dsig) < GTOL
+    assert rel_l2(gw.numpy()[0, 0], gsrc[0]) < GTOL
+
+
+def test_autograd_forward_runs_no_reverse_sweep():
+    """The forward pass alone is one fdtd_run: the same probe series bit for
+    bit, and no reverse sweep until backward is called."""
+    N = 80
+    w = grad_case(seed=65, nx=60, ny=50, nsteps=N)
+    spec, eps, sig, wav = _autograd_case([w], N)
+    before = FdtdFn.vjp_calls
+    probes = FdtdFn.apply(eps, sig, wav, spec)
+    assert FdtdFn.vjp_calls == before
+    ctx = pg.FdtdContext(w["dx"], w["dy"], w["dt"], [(w["eps_r"], w["sigma"])])
+    for (m, i0, j0) in spec.roms[0]:
+        ctx.rom_embed(m, 0, i0, j0)
+    ref = torch.zeros((N, len(w["probes"])), dtype=torch.float32, device="cuda")
+    ctx.fdtd_run(N, [dict(s, sim=0, wave=wav.detach()[0, k].cuda()) for k, s in enumerate(spec.sources[0])],
+                 [(0, i, j) for (i, j) in w["probes"]], ref)
+    assert torch.equal(probes[0], ref)
+    (probes.double() ** 2).sum().backward()
+    assert FdtdFn.vjp_calls == before + 1
+    assert eps.grad is not None and float(eps.grad.abs().max()) > 0
+
+
+def test_autograd_batch_is_per_simulation():
+    """Two simulations of one grid size in one call (models, sources and
+    probes per simulation): each simulation's gradient of the summed probe
+    energy matches its own oracle adjoint."""
+    N = 120
+    ws = [grad_case(seed=67, nx=80, ny=64, nsteps=N), grad_case(seed=68, nx=80, ny=64, nsteps=N)]
+    spec, eps, sig, wav = _autograd_case(ws, N)
+    J = probe_energy(eps, sig, wav, spec)
+    J.backward()
+    Jt = 0.0
+    for b, w in enumerate(ws):
+        Jo, deps, dsig, gsrc = adjoint.gradients(w, N)
+        Jt += Jo
+        assert rel_l2(eps.grad.numpy()[b], deps) < GTOL
+        assert rel_l2(sig.grad.numpy()[b], dsig) < GTOL
+        assert rel_l2(wav.grad.numpy()[b, 0], gsrc[0]) < GTOL
+    assert abs(float(J) - Jt) < 1e-4 * Jt
+
+
+def test_vjp_with_twice_the_probes_equals_grad():
+    """fdtd_vjp seeded with 2 o equals fdtd_grad (the probe energy)."""
+    w = grad_case(seed=69, nx=70, ny=60, nsteps=100)
+    J, ge, gs, gw, ctx = gpu_grad([w], 100, 30)
+    ctx2 = pg.FdtdContext(w["dx"], w["dy"], w["dt"], [(w["eps_r"], w["sigma"])])
+    for rd in w["roms"]:
+        m = pg.rom_build(rd["a"], rd["b"], rd["r"], w["dx"], w["dy"], w["dt"], rd["eps_r"], rd["sigma"],
+                         rd["q"], f0=rd["f0"])
+        ctx2.rom_embed(m, 0, rd["i0"], rd["j0"])
+    srcs = [dict(so, sim=0, wave=torch.tensor(so["wave"][:100].astype(np.float32), device="cuda"))
+            for so in w["sources"]]
+    probes = [(0, i, j) for (i, j) in w["probes"]]
+    out = torch.zeros((100, len(probes)), dtype=torch.float32, device="cuda")
+    ctx2.fdtd_run(100, srcs, probes, out)
+    ctx3 = pg.FdtdContext(w["dx"], w["dy"], w["dt"], [(w["eps_r"], w["sigma"])])
+    for rd in w["roms"]:
+        m = pg.rom_build(rd["a"], rd["b"], rd["r"], w["dx"], w["dy"], w["dt"], rd["eps_r"], rd["sigma"],
+                         rd["q"], f0=rd["f0"])
+        ctx3.rom_embed(m, 0, rd["i0"], rd["j0"])
+    fwd = torch.zeros_like(out)
+    ve, vs, vw = ctx3.fdtd_vjp(100, srcs, probes, (2.0 * out).contiguous(), 30, probe_out=fwd)
+    assert torch.equal(fwd, out)
+    assert ctx3.step_count() == 100
+    assert rel_l2(ve[0].cpu().numpy(), ge[0]) < 1e-6
+    assert rel_l2(vs[0].cpu().numpy(), gs[0]) < 1e-6
+    assert rel_l2(vw.cpu().numpy(), gw) < 1e-6
 
 
 @pytest.mark.parametrize("nx,ny", [(100, 80), (300, 230)])
@@ -189,3 +289,34 @@ def test_full_size_gradient_properties(monkeypatch):
 
     fd = (J_at(h) - J_at(-h)) / (2 * h)
     assert abs(fd - gk[j, i]) < 2e-2 * abs(gk[j, i])
+
+
+def _adjoint16_case(wb, k, N):
+    """Workload record of simulation k of the gradient configuration (for the
+    oracle)."""
+    s = wb["sims"][k]
+    return dict(nx=s["nx"], ny=s["ny"], dx=wb["dx"], dy=wb["dy"], dt=wb["dt"], eps_r=s["eps_r"],
+                sigma=s["sigma"], roms=[dict(wb["models"][mi], i0=i0, j0=j0) for (mi, i0, j0) in s["place"]],
+                sources=[s["source"]], probes=list(s["probes"]), nsteps=N)
+
+
+def test_scaled_gradient_configuration_matches_oracle_fields(monkeypatch):
+    """The gradient configuration's recipe (two shared q = 120 models per
+    simulation, vacuum rings, 8 probes, J = sum Hz^2, checkpoints every 500
+    steps) on a scaled copy, 2 x 192^2 over 1500 steps, in the library's
+    default launch configuration: the whole dJ/deps, dJ/dsigma fields and the
+    source gradients against the FP64 oracle adjoint."""
+    monkeypatch.delenv("FDTD_TB", raising=False)
+    N = 1500
+    wb = workloads.adjoint_16(N, nsim=2, n=192)
+    ws = [_adjoint16_case(wb, k, N) for k in range(2)]
+    J, ge, gs, gw, _ = gpu_grad(ws, N, 500)
+    Jt = 0.0
+    for k, w in enumerate(ws):
+        Jo, deps, dsig, gsrc = adjoint.gradients(w, N)
+        Jt += Jo
+        assert np.abs(deps).max() > 0
+        assert rel_l2(ge[k], deps) < GTOL
+        assert rel_l2(gs[k], dsig) < GTOL
+        assert rel_l2(gw[k], gsrc[0]) < GTOL
+    assert abs(J - Jt) < 1e-4 * Jt

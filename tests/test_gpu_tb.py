@@ -3,7 +3,12 @@ model tiles take a small share of a wave) in both forms (the
 row-marching kernel with model tiles, and FDTD_TB_SMEM=1 shared-memory
 tiles): the parity cases of the one-step path rerun through it against the
 FP64 oracle, and the paths against each other on the same inputs (the
-row-marching form bit for bit: it uses the one-step kernel's operations)."""
+row-marching form bit for bit: it uses the one-step kernel's operations).
+The models' maps are stepped either inside their zone tiles (fused) or by the
+zone chain (tile halves around a map launch: the default for maps shared by a
+GEMM group, FDTD_TB_CHAIN=1 for every model); the map itself one row per warp
+or as a GEMM over the simulations sharing it.  Every choice gives the same
+bits."""
 import numpy as np
 import pytest
 
@@ -11,6 +16,7 @@ torch = pytest.importorskip("torch")
 if not torch.cuda.is_available():
     pytest.skip("no CUDA device", allow_module_level=True)
 
+import paper_1609_07114_gb300 as pg
 import workloads
 import test_gpu_parity as tp
 
@@ -136,3 +142,134 @@ def test_default_choice_of_the_two_step_path(monkeypatch):
     monkeypatch.setenv("FDTD_TB", "1")
     assert tl.lattice_context(wl)[0].steps_per_launch() == 2
 
+
+
+_BATCHED_MODELS = {}
+
+
+def batched_context(ws):
+    """Context of _batched_small workloads: the four shared models are built
+    once per process and embedded in every simulation."""
+    w0 = ws[0]
+    if not _BATCHED_MODELS:
+        for k, md in enumerate(w0["models"]):
+            _BATCHED_MODELS[k] = pg.rom_build(md["a"], md["b"], md["r"], w0["dx"], w0["dy"], w0["dt"], md["eps_r"],
+                                              md["sigma"], md["q"], f0=md["f0"])
+    ctx = pg.FdtdContext(w0["dx"], w0["dy"], w0["dt"], [(w["eps_r"], w["sigma"]) for w in ws])
+    for s, w in enumerate(ws):
+        for (k, i0, j0) in w["place"]:
+            ctx.rom_embed(_BATCHED_MODELS[k], s, i0, j0)
+    return ctx, list(_BATCHED_MODELS.values())
+
+
+def _batched_small(N, per_size=40):
+    """40 grids of 128^2 sharing the four batched-layout models (vacuum
+    rings): two GEMM column blocks per map (32 + 8 columns)."""
+    wb = workloads.batched_256(N, per_size=per_size, sizes=(128,))
+    ws = []
+    for s in wb["sims"]:
+        probes = [s["probe"]] + [(i0 - 1, j0 + 2) for (_, i0, j0) in s["place"]]   # some inside zones
+        ws.append(dict(nx=s["nx"], ny=s["ny"], dx=wb["dx"], dy=wb["dy"], dt=wb["dt"], eps_r=s["eps_r"],
+                       sigma=s["sigma"], roms=[dict(wb["models"][k], i0=i0, j0=j0) for (k, i0, j0) in s["place"]],
+                       sources=[s["source"]], probes=probes, nsteps=N, place=s["place"], models=wb["models"],
+                       make=batched_context))
+    return ws
+
+
+def context_for(ws):
+    """The workloads' own context builder (shared models) or one model per
+    region."""
+    return ws[0]["make"](ws) if "make" in ws[0] else tp.gpu_context(ws)
+
+
+def _run_forms(monkeypatch, ws, n, settings):
+    res = {}
+    for name, env in settings.items():
+        for k, v in env.items():
+            monkeypatch.setenv(k, v)
+        ctx, _ = context_for(ws)
+        out = tp.gpu_run(ctx, ws, n)
+        res[name] = (out, [ctx.get_fields(s) for s in range(len(ws))], ctx.steps_per_launch())
+        ctx.close()
+    return res
+
+
+def _assert_same_bits(res, ref):
+    assert np.abs(res[ref][0]).max() > 0
+    for name, (out, fields, _) in res.items():
+        assert np.array_equal(out, res[ref][0]), name
+        for fa, fb in zip(fields, res[ref][1]):
+            for a, b in zip(fa, fb):
+                assert np.array_equal(a, b), name
+
+
+def test_gemm_and_row_forms_are_bit_identical(monkeypatch):
+    """One step per launch: the shared maps stepped one row per warp, or as a
+    GEMM over the 40 simulations sharing each (both CTA shapes)."""
+    ws = _batched_small(121)
+    res = _run_forms(monkeypatch, ws, 121, {
+        "row": {"FDTD_TB": "0", "FDTD_ROM_GEMM_MIN": "1000"},
+        "gemm1": {"FDTD_TB": "0", "FDTD_ROM_GEMM_MIN": "1", "FDTD_GEMM_RPW": "1"},
+        "gemm2": {"FDTD_TB": "0", "FDTD_ROM_GEMM_MIN": "1", "FDTD_GEMM_RPW": "2"},
+    })
+    _assert_same_bits(res, "row")
+
+
+def test_zone_chain_is_bit_identical(monkeypatch):
+    """Two steps per launch with the shared maps as GEMMs in the zone chain
+    (the default for shared maps), with every model in the chain one row per
+    warp, and with the maps inside fused model tiles, against one step per
+    launch; odd step count (a trailing single step)."""
+    ws = _batched_small(121)
+    monkeypatch.setenv("FDTD_TB_SMEM", "0")
+    res = _run_forms(monkeypatch, ws, 121, {
+        "one": {"FDTD_TB": "0", "FDTD_ROM_GEMM_MIN": "1"},
+        "chain_gemm": {"FDTD_TB": "1", "FDTD_ROM_GEMM_MIN": "1", "FDTD_TB_CHAIN": "1"},
+        "chain_rows": {"FDTD_TB": "1", "FDTD_ROM_GEMM_MIN": "1000", "FDTD_TB_CHAIN": "1"},
+        "fused": {"FDTD_TB": "1", "FDTD_ROM_GEMM_MIN": "1", "FDTD_TB_CHAIN": "0"},
+    })
+    assert [res[k][2] for k in ("one", "chain_gemm", "chain_rows", "fused")] == [1, 2, 2, 2]
+    _assert_same_bits(res, "one")
+
+
+@pytest.mark.parametrize("rows", ["17", "auto"])
+def test_zone_chain_on_tile_boundaries_is_bit_identical(monkeypatch, rows):
+    """Every model (their maps not shared) in the zone chain, with probes and
+    sources on strip and tile boundaries and inside zones, against one step
+    per launch."""
+    n = 203
+    ws = _boundary_workloads(n)
+    for w in ws:
+        for rd in w["roms"]:
+            w["probes"] += [(rd["i0"] - 2, rd["j0"] + 1), (rd["i0"] + rd["a"] + 1, rd["j0"])]
+    monkeypatch.setenv("FDTD_TB_SMEM", "0")
+    if rows == "auto":
+        monkeypatch.delenv("FDTD_TB_ROWS", raising=False)
+    else:
+        monkeypatch.setenv("FDTD_TB_ROWS", rows)
+    res = _run_forms(monkeypatch, ws, n, {
+        "one": {"FDTD_TB": "0"},
+        "chain": {"FDTD_TB": "1", "FDTD_TB_CHAIN": "1"},
+    })
+    assert res["chain"][2] == 2
+    _assert_same_bits(res, "one")
+
+
+@pytest.mark.parametrize("ring", ["2", "3", "4"])
+def test_staged_rows_are_bit_identical(monkeypatch, ring):
+    """The row-marching kernel with its loads staged 1-3 rows ahead through
+    shared memory (FDTD_TB_RING) against its register form, 17-row tiles
+    (many tile starts and ends) and the automatic plan's."""
+    n = 203
+    ws = _boundary_workloads(n)
+    monkeypatch.setenv("FDTD_TB_SMEM", "0")
+    for rows in ("17", None):
+        if rows:
+            monkeypatch.setenv("FDTD_TB_ROWS", rows)
+        else:
+            monkeypatch.delenv("FDTD_TB_ROWS", raising=False)
+        res = _run_forms(monkeypatch, ws, n, {
+            "regs": {"FDTD_TB": "1", "FDTD_TB_RING": "0"},
+            "ring": {"FDTD_TB": "1", "FDTD_TB_RING": ring},
+        })
+        _assert_same_bits(res, "regs")
