@@ -58,6 +58,11 @@ WORKLOAD = ("grid_4096: 4096x4096 coarse cells (dx=1mm, eps_r~U[1,4], sigma~U[0,
             "16 Hz probes, dt=0.95 fine CFL")
 # autotuner results of this run (contexts of the same shape reuse them)
 TUNE_CACHE = os.path.join("/tmp", f"fdtd_tune_{os.getpid()}.txt")
+TUNE = [True]   # --no-tune: the fixed rule (and the FDTD_* environment) instead
+
+
+def autotune(ctx):
+    return ctx.autotune(TUNE_CACHE) if TUNE[0] else dict(ctx.plan(), fixed_rule=True)
 atexit.register(lambda: os.path.exists(TUNE_CACHE) and os.remove(TUNE_CACHE))
 CONFIG = {"workload": WORKLOAD, "nx": 4096, "ny": 4096, "roms": 8, "rom_q": 200,
           "l2": "inputs larger than L2: 0.47 GB of fields+materials per time step (L2 129 MB)"}
@@ -400,7 +405,7 @@ def measure_batched(K, W, T, plain_per_size=16, per_size=64):
 
     cells = sum(s["nx"] * s["ny"] for s in sims)
     ctx, waves, probes = make_ctx(sims)
-    tune = ctx.autotune(TUNE_CACHE)
+    tune = autotune(ctx)
     spl = ctx.steps_per_launch()
     out = torch.zeros((T, len(probes)), dtype=torch.float32, device="cuda")
     for k in range(W):
@@ -427,7 +432,7 @@ def measure_batched(K, W, T, plain_per_size=16, per_size=64):
     for group in by_size.values():
         for s in group[:plain_per_size]:
             c1, wv, pr = make_ctx([s])
-            c1.autotune(TUNE_CACHE)                         # the first of each size is timed, the rest cached
+            autotune(c1)                                    # the first of each size is timed, the rest cached
             step(c1, [s], wv, pr, 0, Tp, outp)              # warm (graph capture)
             torch.cuda.synchronize()
             e0.record(stream)
@@ -473,7 +478,7 @@ def measure_adjoint(K, W, N, nsim=16):
         for k, s in enumerate(w["sims"]):
             for (mi, i0, j0) in s["place"]:
                 ctx.rom_embed(models[mi], k, i0, j0)
-        tunes.append(ctx.autotune(TUNE_CACHE))
+        tunes.append(autotune(ctx))
         return ctx
 
     waves = [torch.tensor(s["source"]["wave"].astype(np.float32), device="cuda") for s in w["sims"]]
@@ -541,7 +546,7 @@ def measure_lattice(K, W, T, n=8192, lossless=False, energy_every=0):
                                       rd["sigma"], rd["q"], f0=rd["f0"])
         ctx.rom_embed(built[key], 0, rd["i0"], rd["j0"])
     rom_seconds = time.perf_counter() - t0
-    tune = ctx.autotune(TUNE_CACHE)
+    tune = autotune(ctx)
     t0 = time.perf_counter()   # the same three models built on the device (not used below)
     for rd in {id(rd["eps_r"]): rd for rd in w["roms"]}.values():
         pg.rom_build_gpu(rd["a"], rd["b"], rd["r"], w["dx"], w["dy"], w["dt"], rd["eps_r"], rd["sigma"],
@@ -595,9 +600,9 @@ def measure_lattice(K, W, T, n=8192, lossless=False, energy_every=0):
     spl = ctx.steps_per_launch()
     kms = ctx.time_stencil(8, 4)
     f_nb = float(np.mean((w["eps_r"] != 1.0) | (w["sigma"] != 0.0)))
-    # fields + the materials of non-background cells (the two-step kernel
-    # reads every material)
-    bpc = 32.0 if spl == 2 else 24.0 + 8.0 * f_nb
+    # per launch (one or two steps): the fields and the materials of the
+    # non-background cells (both kernels skip background-only strip rows)
+    bpc = 24.0 + 8.0 * f_nb
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "steps": K, "warmup": W,
         "ms_per_step": el_s / max(nsteps_timed // T, 1) * 1e3, "time_steps_per_step": T,
@@ -652,7 +657,7 @@ def measure_grid(args, ws, rank, local, dist):
         models.append(m)
     rom_seconds = time.perf_counter() - t0
     t0 = time.perf_counter()
-    tune = ctx.autotune(TUNE_CACHE)
+    tune = autotune(ctx)
     tune["seconds"] = round(time.perf_counter() - t0, 3)
     wave = torch.tensor(w["sources"][0]["wave"].astype(np.float32), device="cuda")
     probes = [(0, i, j) for (i, j) in w["probes"]]
@@ -751,7 +756,9 @@ def main():
                     help="batched: simulations of each size run one at a time for the plain rate")
     ap.add_argument("--batch-per-size", type=int, default=64,
                     help="batched: simulations of each size in the batch (64 = the configuration)")
+    ap.add_argument("--no-tune", action="store_true", help="the fixed rule instead of the autotuner's choice")
     args = ap.parse_args()
+    TUNE[0] = not args.no_tune
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

@@ -454,6 +454,10 @@ typedef struct {
  * layers or monitors (those re-plan with the kept choices). */
 int fdtd_autotune(fdtd_ctx* ctx, const char* cache_path, fdtd_tune_report* report);
 
+/* The context's current launch configuration in the same form (candidates,
+ * ms_default and ms_best are 0); no device work. */
+int fdtd_get_plan(const fdtd_ctx* ctx, fdtd_tune_report* report);
+
 /* Time steps one stencil launch of fdtd_run advances: 2 when the context
  * steps in pairs (temporal blocking: two steps of Eq. (5), Eq. (3) per pass
  * over the fields, each model's Eq. (23) evaluated between them in its own

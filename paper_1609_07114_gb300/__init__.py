@@ -135,6 +135,7 @@ def lib() -> C.CDLL:
         "fdtd_steps_per_launch": (i, [vp]),
         "fdtd_time_stencil": (i, [vp, i, i, _dp]),
         "fdtd_autotune": (i, [vp, C.c_char_p, C.POINTER(fdtd_tune_report)]),
+        "fdtd_get_plan": (i, [vp, C.POINTER(fdtd_tune_report)]),
         "fdtd_last_error": (C.c_char_p, [vp]),
     }
     for name, (res, args) in sig.items():
@@ -509,6 +510,12 @@ class FdtdContext:
         rep = fdtd_tune_report()
         p = cache_path.encode() if cache_path else None
         self._ck(lib().fdtd_autotune(self._h, p, C.byref(rep)))
+        return rep.as_dict()
+
+    def plan(self):
+        """The current launch configuration (``fdtd_get_plan``) as a dict."""
+        rep = fdtd_tune_report()
+        self._ck(lib().fdtd_get_plan(self._h, C.byref(rep)))
         return rep.as_dict()
 
     def time_stencil(self, launches=16, reps=8):

@@ -1071,6 +1071,7 @@ struct fdtd_ctx {
   int tbm_pf = 0;                  // rows prefetched into L2 ahead of the loads (FDTD_TB_PF)
   int tbm_mb = 4;                  // resident CTAs per SM the kernel is compiled for (FDTD_TB_MB)
   int tbm_ring = 0;                // rows staged ahead through shared memory (FDTD_TB_RING; 0: registers)
+  bool tbm_sparse = false;         // some simulation has a background material (sparse-material form)
   // configuration chosen by fdtd_autotune (0: the fixed rule or the
   // environment): one-step tile rows, row-marching tile rows, simulations per
   // shared map from which it steps as a GEMM, GEMM rows per warp
@@ -1147,16 +1148,14 @@ int plan_tb(fdtd_ctx* ctx) {
   ctx->tbm_zones.clear();
   // FDTD_TB=0: off; 1: on wherever it applies; unset: the row-marching form
   // where it applies, unless (measured on GB300, against the one-step path)
-  //  - a model tile outlasts the march over the cells (small grids: one CTA
-  //    stepping a model twice takes longer than the whole march; estimates:
-  //    the march 6.6 ps per cell and pair of steps, a model tile 0.6 ns per
-  //    element of [P | Q] plus 5 us),
-  //  - fewer than half of the strip rows hold materials other than the
-  //    background (the one-step kernel's sparse-material path moves 24 B per
-  //    cell-step there: the 64-model lattice, 202.5 against 208.3).
-  // (4096^2 benchmark grid: 300.7 against 189.3 Gcell-steps/s; 256 uneven
-  // grids with 1024 models, whose tiles take several waves beside the
-  // march: 203.1 against 182.3.)
+  // a model's work outlasts the march over the cells (small grids: one CTA
+  // stepping a model twice takes longer than the whole march; estimates:
+  // the march 6.6 ps per cell and pair of steps, a fused model tile 0.6 ns
+  // per element of [P | Q] plus 5 us, the zone chain 24 us plus its maps).
+  // (4096^2 benchmark grid: 300.7 against 189.3 Gcell-steps/s.)  The march
+  // reads the materials of background-only strip rows as the one-step kernel
+  // does, so grids of sparse scatterers take it too.  fdtd_autotune times
+  // both choices.
   const int mode = ctx->tb_mode;
   if (mode == 0) return FDTD_OK;
   if (!ctx->pml_cells.empty()) return FDTD_OK;   // the layers' corrections need the one-step form
@@ -1171,14 +1170,8 @@ int plan_tb(fdtd_ctx* ctx) {
     chain[k] = ctx->tb_chain_mode == 1 ||
                (ctx->tb_chain_mode < 0 && k < ctx->in_gemm.size() && ctx->in_gemm[k]);
   if (mode != 1) {
-    double cells = 0, zone_us = 0, chain_nld = 0, dense_rows = 0, strip_rows = 0;
-    for (const SimHost& sh : ctx->sims) {
-      cells += (double)sh.nx * sh.ny;
-      strip_rows += (double)sh.ny * sh.nstrip;
-      for (int j = 0; j < sh.ny; ++j)
-        for (int st = 0; st < sh.nstrip; ++st)
-          dense_rows += (sh.mbits[(size_t)(j >> 5) * sh.nstrip + st] >> (j & 31)) & 1u;
-    }
+    double cells = 0, zone_us = 0, chain_nld = 0;
+    for (const SimHost& sh : ctx->sims) cells += (double)sh.nx * sh.ny;
     for (size_t k = 0; k < ninst; ++k) {
       const Instance& in = ctx->insts[k];
       if (chain[k]) chain_nld += (double)in.n * in.map->ld;
@@ -1187,7 +1180,6 @@ int plan_tb(fdtd_ctx* ctx) {
     // the chain: four dependent launches (~6 us each) and two map products
     if (chain_nld > 0) zone_us = std::max(zone_us, 24.0 + 1.33e-7 * chain_nld);
     if (cells * 6.6e-6 < 1.25 * zone_us) return FDTD_OK;
-    if (dense_rows < 0.5 * strip_rows) return FDTD_OK;
   }
   const int M = kTbZoneMargin;
   std::vector<int4> zone(ninst);
@@ -1226,10 +1218,12 @@ int plan_tb(fdtd_ctx* ctx) {
     if (const char* eg = getenv("FDTD_TB_RING")) ctx->tbm_ring = std::min(4, std::max(0, atoi(eg)));
     if (ctx->ov_ring >= 0) ctx->tbm_ring = ctx->ov_ring;
     if (ctx->tbm_ring == 1 || ctx->tbm_mb == 3) ctx->tbm_ring = 0;
+    ctx->tbm_sparse = false;
+    for (const SimHost& sh : ctx->sims) ctx->tbm_sparse = ctx->tbm_sparse || !sh.all_dense;
     if (ctx->tbm_ring > 0)
-      CK(cudaFuncSetAttribute(march_fn(4, ctx->tbm_ring), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)march_smem(ctx->tbm_ring)));
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, march_fn(ctx->tbm_mb, ctx->tbm_ring), 128,
+      CK(cudaFuncSetAttribute(march_fn(4, ctx->tbm_ring, ctx->tbm_sparse),
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)march_smem(ctx->tbm_ring)));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, march_fn(ctx->tbm_mb, ctx->tbm_ring, ctx->tbm_sparse), 128,
                                                   march_smem(ctx->tbm_ring));
     // (a zone chain takes one slot per SM while its kernels run)
     long long nfused = 0;
@@ -1897,7 +1891,8 @@ void launch_tb(fdtd_ctx* ctx, cudaStream_t s, int par, int c) {
     yee_tb2_kernel<<<ntb, kTbThreads, kTbSmemFields, s>>>(ctx->sims_d, ctx->tb_tiles_d, ctx->insts_d, ctx->run_d,
                                                           ctx->tb_run_d, par, c);
   if (ctx->tb_march)   // overlaps the model tiles (programmatic serialisation) when there are any
-    launch_k(march_fn(ctx->tbm_mb, ctx->tbm_ring), (unsigned)ctx->tbm_tiles.size(), 128, march_smem(ctx->tbm_ring), s,
+    launch_k(march_fn(ctx->tbm_mb, ctx->tbm_ring, ctx->tbm_sparse), (unsigned)ctx->tbm_tiles.size(), 128,
+             march_smem(ctx->tbm_ring), s,
              ctx->pdl && ntb > 0, (const SimDev*)ctx->sims_d, (const TileWork*)ctx->tbm_tiles_d,
              (const RunDev*)ctx->run_d, (const TbMarchDev*)ctx->tbm_d, par, c, ctx->tbm_pf);
   if (ctx->tb_nchain > 0) cudaStreamWaitEvent(s, ctx->ev_join, 0);
@@ -2581,6 +2576,13 @@ int fdtd_autotune(fdtd_ctx* ctx, const char* cache_path, fdtd_tune_report* repor
   return run_autotune(ctx, cache_path, report);
 }
 
+int fdtd_get_plan(const fdtd_ctx* ctx, fdtd_tune_report* report) {
+  if (!ctx || !report) return set_global_error(FDTD_EINVAL, "fdtd_get_plan: bad argument");
+  *report = fdtd_tune_report{};
+  fill_report(ctx, report);
+  return FDTD_OK;
+}
+
 int fdtd_set_timing(fdtd_ctx* ctx, int on) {
   if (!ctx) return set_global_error(FDTD_EINVAL, "fdtd_set_timing: null context");
   if (ctx->timing) {
@@ -2640,7 +2642,7 @@ int fdtd_time_stencil(fdtd_ctx* ctx, int launches, int reps, double* ms_per_laun
   CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
   for (int k = 0; k < launches; ++k) {
     if (ctx->tb && ctx->tb_march)
-      launch_k(march_fn(ctx->tbm_mb, ctx->tbm_ring), (unsigned)ctx->tbm_tiles.size(), 128,
+      launch_k(march_fn(ctx->tbm_mb, ctx->tbm_ring, ctx->tbm_sparse), (unsigned)ctx->tbm_tiles.size(), 128,
                march_smem(ctx->tbm_ring), cs, false, (const SimDev*)ctx->sims_d, (const TileWork*)ctx->tbm_tiles_d, (const RunDev*)ctx->run_d,
                (const TbMarchDev*)ctx->tbm_d, par, 0, ctx->tbm_pf);
     else if (ctx->tb && nord > 0)

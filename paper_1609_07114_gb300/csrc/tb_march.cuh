@@ -57,18 +57,41 @@ struct MarchIn {        // the loads of row j for sub-step A
   float4 ma, mb;        // mat(j) of the lane's 4 cells
 };
 
-// Lanes outside the pitched row and rows >= ny read nothing (dead cells).
+// Sparse materials: whether row j of the warp's 128 columns [c0 - 4, c0 + 124),
+// which lie in at most two of the 128-column strips of the simulation's bits,
+// holds a cell other than the background (or the cell left of a strip does).
+// Rows are asked in ascending order; the word of 32 rows is fetched at the
+// first row asked and at every multiple of 32.  Warp-uniform.
+__device__ __forceinline__ bool march_dense(const SimDev& sd, int j, int c0, bool first, uint32_t& wbits) {
+  if (first || (j & 31) == 0) {
+    wbits = 0xffffffffu;   // rows past the grid are not loaded anyway
+    if ((j >> 5) <= ((sd.ny - 1) >> 5)) {
+      const uint32_t* w = sd.mbits + (size_t)(j >> 5) * sd.nstrip;
+      wbits = w[max(c0 - 4, 0) >> 7] | w[min(c0 + 123, sd.pitch - 1) >> 7];
+    }
+  }
+  return ((wbits >> (j & 31)) & 1u) != 0u;
+}
+
+// Lanes outside the pitched row and rows >= ny read nothing (dead cells);
+// rows of background cells only (dense false) take the background material
+// without reading it.
 __device__ __forceinline__ void march_load(MarchIn& r, const float* __restrict__ ex,
                                            const float* __restrict__ ey, const float* __restrict__ hz,
                                            const float2* __restrict__ mat, int j, int ny, int P, int cl,
-                                           bool inb) {
+                                           bool inb, bool dense, const float2* __restrict__ bgp) {
   if (inb && j < ny) {
     const size_t row = (size_t)j * P + cl;
     r.exn = ld4(ex + row + P);
     r.eyv = ld4(ey + row);
     r.hzv = ld4(hz + row);
-    r.ma = ld4(reinterpret_cast<const float*>(mat + row));
-    r.mb = ld4(reinterpret_cast<const float*>(mat + row + 2));
+    if (dense) {
+      r.ma = ld4(reinterpret_cast<const float*>(mat + row));
+      r.mb = ld4(reinterpret_cast<const float*>(mat + row + 2));
+    } else {
+      const float2 bg = *bgp;
+      r.ma = r.mb = make_float4(bg.x, bg.y, bg.x, bg.y);
+    }
   } else {
     r.exn = r.eyv = r.hzv = make_float4(0.f, 0.f, 0.f, 0.f);
     r.ma = r.mb = make_float4(-1.f, 0.f, -1.f, 0.f);
@@ -141,25 +164,33 @@ constexpr int kMarchRingBytesPerRow = 4 * 5 * 32 * 16;   // four warps
 
 __device__ __forceinline__ void march_issue(float4* slot, const float* __restrict__ ex, const float* __restrict__ ey,
                                             const float* __restrict__ hz, const float2* __restrict__ mat, int j, int ny,
-                                            int P, int cl, bool inb, int lane) {
+                                            int P, int cl, bool inb, int lane, bool dense) {
   asm volatile("" ::: "memory");   // after the reads of the slot's previous row
   const bool ok = inb && j < ny;
   const size_t row = ok ? (size_t)j * P + cl : 0;
   cp_async16(slot + 0 * 32 + lane, ok ? ex + row + P : ex, ok);
   cp_async16(slot + 1 * 32 + lane, ey + row, ok);
   cp_async16(slot + 2 * 32 + lane, hz + row, ok);
-  cp_async16(slot + 3 * 32 + lane, mat + row, ok);
-  cp_async16(slot + 4 * 32 + lane, mat + row + 2, ok);
+  if (dense) {
+    cp_async16(slot + 3 * 32 + lane, mat + row, ok);
+    cp_async16(slot + 4 * 32 + lane, mat + row + 2, ok);
+  }
   asm volatile("cp.async.commit_group;\n" ::: "memory");
 }
 
-__device__ __forceinline__ void march_fetch(MarchIn& r, const float4* slot, int j, int ny, bool inb, int lane) {
+__device__ __forceinline__ void march_fetch(MarchIn& r, const float4* slot, int j, int ny, bool inb, int lane,
+                                            bool dense, const float2* __restrict__ bgp) {
   if (inb && j < ny) {
     r.exn = slot[0 * 32 + lane];
     r.eyv = slot[1 * 32 + lane];
     r.hzv = slot[2 * 32 + lane];
-    r.ma = slot[3 * 32 + lane];
-    r.mb = slot[4 * 32 + lane];
+    if (dense) {
+      r.ma = slot[3 * 32 + lane];
+      r.mb = slot[4 * 32 + lane];
+    } else {
+      const float2 bg = *bgp;
+      r.ma = r.mb = make_float4(bg.x, bg.y, bg.x, bg.y);
+    }
   } else {
     r.exn = r.eyv = r.hzv = make_float4(0.f, 0.f, 0.f, 0.f);
     r.ma = r.mb = make_float4(-1.f, 0.f, -1.f, 0.f);
@@ -171,7 +202,7 @@ __device__ __forceinline__ void cp_async_wait_n() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-template <int kMinBlocks, int kRing>
+template <int kMinBlocks, int kRing, bool kSparse>
 __global__ void __launch_bounds__(128, kMinBlocks)
 yee_tb2m_kernel(const SimDev* __restrict__ sims, const TileWork* __restrict__ tiles,
                 const RunDev* __restrict__ run, const TbMarchDev* __restrict__ tm, int par, int c, int pf) {
@@ -232,27 +263,42 @@ yee_tb2m_kernel(const SimDev* __restrict__ sims, const TileWork* __restrict__ ti
     }
   }
   MarchIn cur, nxt;
+  // sparse-material bits of the row being loaded; the background material
+  const float2* __restrict__ bg = &sims[tw.sim].mbg;
+  uint32_t wbits = 0;
   float4* ring = march_ring + (size_t)warp * (kRing > 0 ? kRing : 1) * 5 * 32;
   int slot = 0;
+  unsigned dslots = 0;   // ring: slot k holds a row whose materials were read
   if constexpr (kRing > 0) {
 #pragma unroll
-    for (int d = 0; d < kRing - 1; ++d) march_issue(ring + d * 5 * 32, ex, ey, hz, mat, jA0 + d, ny, P, cl, inb, lane);
+    for (int d = 0; d < kRing - 1; ++d) {
+      const bool dn = !kSparse || march_dense(sd, jA0 + d, c0, d == 0, wbits);
+      dslots = dn ? dslots | (1u << d) : dslots & ~(1u << d);
+      march_issue(ring + d * 5 * 32, ex, ey, hz, mat, jA0 + d, ny, P, cl, inb, lane, dn);
+    }
   } else {
-    march_load(cur, ex, ey, hz, mat, jA0, ny, P, cl, inb);
+    march_load(cur, ex, ey, hz, mat, jA0, ny, P, cl, inb, !kSparse || march_dense(sd, jA0, c0, true, wbits), bg);
   }
   for (int j = jA0; j <= jAe; ++j) {
     if constexpr (kRing > 0) {
       int ahead = slot + kRing - 1;
       ahead -= ahead >= kRing ? kRing : 0;
       // row j + kRing - 1 (past the tile: an empty group, so the count stays uniform)
-      if (j + kRing - 1 <= jAe) march_issue(ring + ahead * 5 * 32, ex, ey, hz, mat, j + kRing - 1, ny, P, cl, inb, lane);
-      else asm volatile("cp.async.commit_group;\n" ::: "memory");
+      if (j + kRing - 1 <= jAe) {
+        const bool dn = !kSparse || march_dense(sd, j + kRing - 1, c0, false, wbits);
+        dslots = dn ? dslots | (1u << ahead) : dslots & ~(1u << ahead);
+        march_issue(ring + ahead * 5 * 32, ex, ey, hz, mat, j + kRing - 1, ny, P, cl, inb, lane, dn);
+      } else {
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+      }
       cp_async_wait_n<kRing - 1>();
-      march_fetch(cur, ring + slot * 5 * 32, j, ny, inb, lane);
+      march_fetch(cur, ring + slot * 5 * 32, j, ny, inb, lane, ((dslots >> slot) & 1u) != 0u, bg);
       slot = slot + 1 == kRing ? 0 : slot + 1;
     } else {
       if (pf > 0 && j + pf <= jAe && j + pf < ny) march_prefetch(ex, ey, hz, mat, j + pf, P, c0, lane);
-      if (j + 1 <= jAe) march_load(nxt, ex, ey, hz, mat, j + 1, ny, P, cl, inb);
+      if (j + 1 <= jAe)
+        march_load(nxt, ex, ey, hz, mat, j + 1, ny, P, cl, inb, !kSparse || march_dense(sd, j + 1, c0, false, wbits),
+                   bg);
     }
     const float2 m[4] = {make_float2(cur.ma.x, cur.ma.y), make_float2(cur.ma.z, cur.ma.w),
                          make_float2(cur.mb.x, cur.mb.y), make_float2(cur.mb.z, cur.mb.w)};
@@ -390,14 +436,16 @@ yee_tb2m_kernel(const SimDev* __restrict__ sims, const TileWork* __restrict__ ti
 using MarchFn = void (*)(const SimDev*, const TileWork*, const RunDev*, const TbMarchDev*, int, int, int);
 
 // The row-marching kernel compiled for mb resident CTAs per SM, with loads
-// in registers (ring 0) or staged through a ring of 2-4 rows.
-MarchFn march_fn(int mb, int ring) {
-  if (mb == 3) return yee_tb2m_kernel<3, 0>;
+// in registers (ring 0) or staged through a ring of 2-4 rows, and with the
+// background rows' materials taken without reading them (sparse: some
+// simulation of the launch has a background material).
+MarchFn march_fn(int mb, int ring, bool sparse) {
+  if (mb == 3) return sparse ? yee_tb2m_kernel<3, 0, true> : yee_tb2m_kernel<3, 0, false>;
   switch (ring) {
-    case 2: return yee_tb2m_kernel<4, 2>;
-    case 3: return yee_tb2m_kernel<4, 3>;
-    case 4: return yee_tb2m_kernel<4, 4>;
-    default: return yee_tb2m_kernel<4, 0>;
+    case 2: return sparse ? yee_tb2m_kernel<4, 2, true> : yee_tb2m_kernel<4, 2, false>;
+    case 3: return sparse ? yee_tb2m_kernel<4, 3, true> : yee_tb2m_kernel<4, 3, false>;
+    case 4: return sparse ? yee_tb2m_kernel<4, 4, true> : yee_tb2m_kernel<4, 4, false>;
+    default: return sparse ? yee_tb2m_kernel<4, 0, true> : yee_tb2m_kernel<4, 0, false>;
   }
 }
 size_t march_smem(int ring) { return ring > 0 ? (size_t)ring * kMarchRingBytesPerRow : 0; }

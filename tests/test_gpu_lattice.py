@@ -64,11 +64,42 @@ def test_sparse_material_path_equals_dense_path(monkeypatch):
         np.testing.assert_array_equal(a, b)
 
 
-def test_full_size_lattice_sampled_windows():
+def test_two_step_sparse_march_equals_one_step(monkeypatch):
+    """The two-step march skips the materials of background-only strip rows
+    as the one-step kernel does: two steps per launch (register loads, staged
+    rows, the models' maps in their tiles or in the zone chain) against one
+    step per launch and against the dense-material form, bit for bit."""
+    N = 201
+    w = small_lattice(N)
+    settings = {
+        "one": {"FDTD_TB": "0"},
+        "two": {"FDTD_TB": "1", "FDTD_TB_RING": "0", "FDTD_TB_CHAIN": "0"},
+        "two_ring": {"FDTD_TB": "1", "FDTD_TB_RING": "3", "FDTD_TB_CHAIN": "0"},
+        "two_chain": {"FDTD_TB": "1", "FDTD_TB_RING": "0", "FDTD_TB_CHAIN": "1"},
+        "two_dense": {"FDTD_TB": "1", "FDTD_TB_RING": "0", "FDTD_TB_CHAIN": "0", "FDTD_MAT_DENSE": "1"},
+    }
+    res = {}
+    for name, env in settings.items():
+        for k, v in env.items():
+            monkeypatch.setenv(k, v)
+        ctx, _ = lattice_context(w)
+        assert ctx.steps_per_launch() == (1 if name == "one" else 2)
+        res[name] = (tp.gpu_run(ctx, [w], N), ctx.get_fields(0))
+        monkeypatch.delenv("FDTD_MAT_DENSE", raising=False)
+    assert np.abs(res["one"][0]).max() > 0
+    for name in settings:
+        np.testing.assert_array_equal(res[name][0], res["one"][0])
+        for a, b in zip(res[name][1], res["one"][1]):
+            np.testing.assert_array_equal(a, b)
+
+
+def test_full_size_lattice_sampled_windows(monkeypatch):
     """8192^2 with 64 models, in the launch configuration the benchmark
-    times.  After N steps from rest only columns within N of a line source
-    can be nonzero; the oracle recomputes each full-height band (with every
-    model inside it) and probes and band fields are compared."""
+    times (the library's default choice).  After N steps from rest only
+    columns within N of a line source can be nonzero; the oracle recomputes
+    each full-height band (with every model inside it) and probes and band
+    fields are compared."""
+    monkeypatch.delenv("FDTD_TB", raising=False)
     N = 40
     w = workloads.lattice_8192(N)
     # A model couples its whole interface within one step, so a band that

@@ -123,9 +123,9 @@ def test_row_marching_form_is_bit_identical_to_one_step(monkeypatch, rows):
 
 def test_default_choice_of_the_two_step_path(monkeypatch):
     """Unset FDTD_TB: the benchmark grid (4096^2, 8 models) steps in pairs;
-    the 64-model lattice (mostly background material: the one-step kernel's
-    sparse path) and a 1024^2 grid with the same 8 models (whose model tiles
-    would outlast the march) singly; FDTD_TB=0 / 1 force the choice."""
+    a 1024^2 grid with the same 8 models and the 64-model lattice at 2048^2
+    (whose model tiles would outlast the march over so few cells) singly;
+    FDTD_TB=0 / 1 force the choice."""
     import test_gpu_lattice as tl
     monkeypatch.delenv("FDTD_TB", raising=False)
     w = workloads.grid_4096(10)
