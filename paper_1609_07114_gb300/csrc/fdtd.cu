@@ -1218,8 +1218,16 @@ int plan_tb(fdtd_ctx* ctx) {
     if (const char* eg = getenv("FDTD_TB_RING")) ctx->tbm_ring = std::min(4, std::max(0, atoi(eg)));
     if (ctx->ov_ring >= 0) ctx->tbm_ring = ctx->ov_ring;
     if (ctx->tbm_ring == 1 || ctx->tbm_mb == 3) ctx->tbm_ring = 0;
+    // the sparse-material form where some strip row holds only background
+    // material (a background alone, e.g. the vacuum rings of random grids,
+    // saves nothing: every strip row is read)
     ctx->tbm_sparse = false;
-    for (const SimHost& sh : ctx->sims) ctx->tbm_sparse = ctx->tbm_sparse || !sh.all_dense;
+    for (const SimHost& sh : ctx->sims) {
+      if (sh.all_dense || ctx->tbm_sparse) continue;
+      for (int j = 0; j < sh.ny && !ctx->tbm_sparse; ++j)
+        for (int st = 0; st < sh.nstrip && !ctx->tbm_sparse; ++st)
+          ctx->tbm_sparse = ((sh.mbits[(size_t)(j >> 5) * sh.nstrip + st] >> (j & 31)) & 1u) == 0u;
+    }
     if (ctx->tbm_ring > 0)
       CK(cudaFuncSetAttribute(march_fn(4, ctx->tbm_ring, ctx->tbm_sparse),
                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)march_smem(ctx->tbm_ring)));

@@ -242,22 +242,37 @@ def test_multi_strip_gradients_match_oracle():
     assert rel_l2(gw[0], gsrc[0]) < GTOL
 
 
-def test_full_size_gradient_properties(monkeypatch):
-    """The gradient configuration at full batch size (16 x 1024^2, two shared
-    models each), in the benchmark's launch configuration (the library's
-    default choice of one or two steps per launch for the forward and
-    checkpoint passes), over 3000 steps with checkpoints every 500: J is
-    quadratic in the sources, so J = 1/2 sum s . dJ/ds (Euler); and the eps
-    gradient at the cell with the largest sensitivity matches a central
-    difference of two forward runs."""
+def test_full_size_gradients_against_finite_differences(monkeypatch):
+    """The gradient configuration at full size (16 x 1024^2, two shared
+    q = 120 models per simulation, 8 probes each, J = sum Hz^2 over 10^4
+    steps, checkpoints every 500) in the library's default launch
+    configuration.  fdtd_grad against finite differences through the GPU
+    forward (an FP64 forward of this size exists only in the oracle, hours
+    per run), J split per simulation by its own probes so that every pair of
+    runs checks one cell in each of the 16 simulations:
+      - eps_r at 32 seeded random coarse cells and at 16 cells beside a model
+        (their material also enters the coupling of Eq. (19)): central
+        differences, h = 10% of eps_r;
+      - sigma at the same cells: one-sided second-order differences
+        (-3 J(s) + 4 J(s + h) - J(s + 2h)) / 2h, h = 0.04 S/m;
+      - the sources: J is quadratic in them, so J = 1/2 s . dJ/ds (Euler).
+    Tolerance |D - g| <= t_rel |g| + t_abs max|g| (per simulation and
+    parameter): the FP32 forward leaves a noise floor in the difference
+    quotients of at most 5e-6 (eps) and 3.1e-5 (sigma) of the simulation's
+    largest gradient (measured on GB300 at these step sizes), taken with a
+    margin of 4 and 3; t_rel = 2% (eps) and 5% (sigma) covers the truncation
+    error (0.6% and 4.7% at most where the noise is small).  At least 24 of
+    the 32 random cells must agree to 1% (eps) and 20 to 5% (sigma), so
+    that the floor does not carry the test."""
     monkeypatch.delenv("FDTD_TB", raising=False)
-    N = 3000
+    N = 10000
     w = workloads.adjoint_16(N)
+    S = len(w["sims"])
     models = [pg.rom_build(md["a"], md["b"], md["r"], w["dx"], w["dy"], w["dt"], md["eps_r"],
                            md["sigma"], md["q"], f0=md["f0"]) for md in w["models"]]
 
-    def ctx_for(eps_list):
-        ctx = pg.FdtdContext(w["dx"], w["dy"], w["dt"], [(e, s["sigma"]) for e, s in zip(eps_list, w["sims"])])
+    def ctx_for(eps, sig):
+        ctx = pg.FdtdContext(w["dx"], w["dy"], w["dt"], [(e, x) for e, x in zip(eps, sig)])
         for k, s in enumerate(w["sims"]):
             for (mi, i0, j0) in s["place"]:
                 ctx.rom_embed(models[mi], k, i0, j0)
@@ -267,28 +282,61 @@ def test_full_size_gradient_properties(monkeypatch):
     src = [dict(s["source"], sim=k, wave=waves[k]) for k, s in enumerate(w["sims"])]
     probes = [(k, i, j) for k, s in enumerate(w["sims"]) for (i, j) in s["probes"]]
     eps0 = [s["eps_r"] for s in w["sims"]]
-    J, ge, gs, gw = ctx_for(eps0).fdtd_grad(N, src, probes, 500)
-    assert J > 0
+    sig0 = [s["sigma"] for s in w["sims"]]
+    J, ge, gs, gw = ctx_for(eps0, sig0).fdtd_grad(N, src, probes, 500)
+    ge = [g.cpu().numpy() for g in ge]
+    gs = [g.cpu().numpy() for g in gs]
     gw = gw.cpu().numpy()
     euler = 0.5 * sum(float(np.dot(np.asarray(s["source"]["wave"][:N], np.float64), gw[k]))
                       for k, s in enumerate(w["sims"]))
     assert abs(euler - J) < 1e-3 * J
-    gmax = [float(g.abs().max()) for g in ge]
-    k = int(np.argmax(gmax))
-    gk = ge[k].cpu().numpy()
-    j, i = np.unravel_index(np.argmax(np.abs(gk)), gk.shape)
-    h = 1e-3 * eps0[k][j, i]
 
-    def J_at(delta):
-        eps = [e.copy() for e in eps0]
-        eps[k][j, i] += delta
-        ctx = ctx_for(eps)
+    def J_sims(eps, sig):
+        ctx = ctx_for(eps, sig)
         out = torch.zeros((N, len(probes)), dtype=torch.float32, device="cuda")
         ctx.fdtd_run(N, src, probes, out)
-        return float((out.double() ** 2).sum())
+        o = out.double().cpu().numpy()
+        ctx.close()
+        return np.array([(o[:, 8 * k:8 * k + 8] ** 2).sum() for k in range(S)])
 
-    fd = (J_at(h) - J_at(-h)) / (2 * h)
-    assert abs(fd - gk[j, i]) < 2e-2 * abs(gk[j, i])
+    def perturbed(cells, eps_d, sig_d):
+        eps = [e.copy() for e in eps0]
+        sig = [x.copy() for x in sig0]
+        for k, (i, j) in enumerate(cells):
+            eps[k][j, i] += eps_d[k]
+            sig[k][j, i] += sig_d[k]
+        return J_sims(eps, sig)
+
+    rng = np.random.default_rng(1609071145)
+
+    def random_cell(k):
+        s = w["sims"][k]
+        near = np.zeros((s["ny"], s["nx"]), bool)
+        for (mi, i0, j0) in s["place"]:
+            near[j0 - 2:j0 + 18, i0 - 2:i0 + 18] = True
+        while True:
+            i, j = int(rng.integers(2, s["nx"] - 2)), int(rng.integers(2, s["ny"] - 2))
+            if not near[j, i]:
+                return i, j
+
+    rounds = {"random0": [random_cell(k) for k in range(S)], "random1": [random_cell(k) for k in range(S)],
+              "ring": [(s["place"][k % 2][1] - 1, s["place"][k % 2][2] + 3 + k % 7) for k, s in enumerate(w["sims"])]}
+    J0 = J_sims(eps0, sig0)
+    hs = 0.04
+    zero = [0.0] * S
+    good_e = good_s = 0
+    for name, cells in rounds.items():
+        he = [0.1 * eps0[k][j, i] for k, (i, j) in enumerate(cells)]
+        De = (perturbed(cells, he, zero) - perturbed(cells, [-h for h in he], zero)) / (2 * np.array(he))
+        Ds = (-3 * J0 + 4 * perturbed(cells, zero, [hs] * S) - perturbed(cells, zero, [2 * hs] * S)) / (2 * hs)
+        for k, (i, j) in enumerate(cells):
+            g_e, g_s = ge[k][j, i], gs[k][j, i]
+            assert abs(De[k] - g_e) <= 0.02 * abs(g_e) + 2e-5 * np.abs(ge[k]).max(), (name, k, De[k], g_e)
+            assert abs(Ds[k] - g_s) <= 0.05 * abs(g_s) + 1e-4 * np.abs(gs[k]).max(), (name, k, Ds[k], g_s)
+            if name != "ring":
+                good_e += abs(De[k] - g_e) <= 0.01 * abs(g_e)
+                good_s += abs(Ds[k] - g_s) <= 0.05 * abs(g_s)
+    assert good_e >= 24 and good_s >= 20, (good_e, good_s)
 
 
 def _adjoint16_case(wb, k, N):
