@@ -50,24 +50,32 @@ __device__ __forceinline__ float comp(const float4& v, int t) {
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
-// E-edge coefficients from the two adjacent cells {eps/dt, sigma/2}
-// (edge material = mean of the two cells, Sec. II-A).
-// ca = (A - S)/(A + S) is formed as 1 - 2 S cb: exactly 1 on a lossless
-// edge (A cb rounded can fall one unit below 1, which would damp lossless
-// media by ~1e-7 per step).  cb is the hardware reciprocal (one MUFU op,
-// relative error ~1e-7: the same as a relative change of the edge's
-// material below FP32 resolution, and the same value in every kernel).
+// E-edge coefficients from the two adjacent cells, each stored as
+// {p, q} = {eps0 eps_r / dt + sigma / 2, sigma} (edge material = mean of the
+// two cells, Sec. II-A): with A = eps / dt and S = sigma / 2 of the edge,
+//   cb = 1 / (A + S) = 2 / (p1 + p2),   ca = (A - S) / (A + S) = 1 - (q1 + q2) / (p1 + p2),
+// so r = 1 / (p1 + p2) gives both: cb = 2 r, ca = 1 - (q1 + q2) r.  On a
+// lossless edge ca is exactly 1 and cb the reciprocal of A (the factor 2 and
+// the halving are exact).  The reciprocal is the hardware one (one MUFU op,
+// relative error ~1e-7: the same as a relative change of the edge's material
+// below FP32 resolution, and the same value in every kernel).
 __device__ __forceinline__ float rcp_hw(float x) {
   float r;
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
   return r;
 }
 
+// ca and r = cb / 2; the stencils multiply r by 2/dy or 2/dx (the same bits
+// as cb times 1/dy or 1/dx).
+__device__ __forceinline__ void edge_coef_r(float2 m1, float2 m2, float& ca, float& r) {
+  r = rcp_hw(__fadd_rn(m1.x, m2.x));
+  ca = __fmaf_rn(-__fadd_rn(m1.y, m2.y), r, 1.f);
+}
+
 __device__ __forceinline__ void edge_coef(float2 m1, float2 m2, float& ca, float& cb) {
-  const float A = 0.5f * (m1.x + m2.x);
-  const float S = 0.5f * (m1.y + m2.y);
-  cb = rcp_hw(A + S);
-  ca = __fmaf_rn(-2.f * S, cb, 1.f);
+  float r;
+  edge_coef_r(m1, m2, ca, r);
+  cb = __fmul_rn(2.f, r);
 }
 
 // Fused coarse H and E half steps over one tile (module header).
@@ -199,9 +207,9 @@ __device__ __forceinline__ void stencil_row(const SimDev& sd, const RowIn<V>& cu
       for (int t = 0; t < V; ++t) {
         float v = cy.exc[t];
         if (j >= 1 && cl + t < nx && cy.mp[t].x >= 0.f && m[t].x >= 0.f) {
-          float ca, cb;
-          edge_coef(cy.mp[t], m[t], ca, cb);
-          v = __fmaf_rn(ca, v, __fmul_rn(__fmul_rn(cb, sd.rdy), __fsub_rn(hn[t], cy.hzp[t])));
+          float ca, r;
+          edge_coef_r(cy.mp[t], m[t], ca, r);
+          v = __fmaf_rn(ca, v, __fmul_rn(__fmul_rn(r, sd.rdy2), __fsub_rn(hn[t], cy.hzp[t])));
         }
         exw[t] = v;
       }
@@ -224,9 +232,9 @@ __device__ __forceinline__ void stencil_row(const SimDev& sd, const RowIn<V>& cu
         const float hl = t == 0 ? hnL : hn[t - 1];
         float v = eyA[t];
         if (i >= 1 && i < nx && ml.x >= 0.f && m[t].x >= 0.f) {
-          float ca, cb;
-          edge_coef(ml, m[t], ca, cb);
-          v = __fmaf_rn(ca, v, -__fmul_rn(__fmul_rn(cb, sd.rdx), __fsub_rn(hn[t], hl)));
+          float ca, r;
+          edge_coef_r(ml, m[t], ca, r);
+          v = __fmaf_rn(ca, v, -__fmul_rn(__fmul_rn(r, sd.rdx2), __fsub_rn(hn[t], hl)));
         }
         eyw[t] = v;
       }
@@ -750,6 +758,9 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   return v;  // valid in thread 0
 }
 
+// eps0 eps_r / dt of a cell from its stored {eps0 eps_r / dt + sigma / 2, sigma}.
+__device__ __forceinline__ double cell_a(float2 m) { return (double)m.x - 0.5 * (double)m.y; }
+
 // Coarse part over one stencil tile: 1/2 eps A E^2 - dt/2 E (K H) on every
 // updated edge, 1/2 mu0 A H^2 on every coarse cell.
 __global__ void __launch_bounds__(256)
@@ -777,7 +788,7 @@ energy_cells_kernel(const SimDev* __restrict__ sims, const TileWork* __restrict_
       const float2 mb = mat[off - P];
       if (mb.x >= 0.f) {
         const double e = ex[off];
-        const double eps = 0.5 * ((double)m.x + (double)mb.x) * dt;
+        const double eps = 0.5 * (cell_a(m) + cell_a(mb)) * dt;
         acc += 0.5 * area * eps * e * e - 0.5 * dt * e * dx * (h - (double)hz[off - P]);
       }
     }
@@ -785,7 +796,7 @@ energy_cells_kernel(const SimDev* __restrict__ sims, const TileWork* __restrict_
       const float2 ml = mat[off - 1];
       if (ml.x >= 0.f) {
         const double e = ey[off];
-        const double eps = 0.5 * ((double)m.x + (double)ml.x) * dt;
+        const double eps = 0.5 * (cell_a(m) + cell_a(ml)) * dt;
         acc += 0.5 * area * eps * e * e + 0.5 * dt * e * dy * (h - (double)hz[off - 1]);
       }
     }
@@ -2203,7 +2214,7 @@ int fdtd_create(const fdtd_grid_desc* g, void* cuda_stream, fdtd_ctx** out) {
       for (int i = 0; i < d.nx; ++i) {
         const size_t k = (size_t)j * d.nx + i;
         sh.mat[(size_t)j * sh.pitch + i] =
-            make_float2((float)(kEps0 * d.eps_r[k] / g->dt), (float)(0.5 * d.sigma[k]));
+            make_float2((float)(kEps0 * d.eps_r[k] / g->dt + 0.5 * d.sigma[k]), (float)d.sigma[k]);
       }
     const size_t bytes = sizeof(float) * (size_t)(d.ny + 1) * sh.pitch;
     for (int p = 0; p < 2; ++p) {
@@ -2239,6 +2250,8 @@ int fdtd_create(const fdtd_grid_desc* g, void* cuda_stream, fdtd_ctx** out) {
     sd.chy = (float)(g->dt / (kMu0 * g->dx));
     sd.rdy = (float)(1.0 / g->dy);
     sd.rdx = (float)(1.0 / g->dx);
+    sd.rdy2 = 2.f * sd.rdy;   // exact
+    sd.rdx2 = 2.f * sd.rdx;
   }
   plan_tiles(ctx);
   if (const char* e = getenv("FDTD_TB")) ctx->tb_mode = atoi(e) != 0 ? 1 : 0;   // fixed for the context

@@ -10,8 +10,8 @@
 //
 // Memory layout per simulation: Ex, Ey, Hz each (ny+1) rows x pitch floats,
 // row-major, pitch a multiple of 128 floats (512 B) and > nx; cell materials
-// as float2 {eps0 eps_r / dt, sigma/2}, the first component set to -1 for
-// cells covered by a reduced model.  An E edge is updated only if both its
+// as float2 {eps0 eps_r / dt + sigma / 2, sigma}, the first component set to
+// -1 for cells covered by a reduced model.  An E edge is updated only if both its
 // cells are coarse cells and it is not on the PEC wall.
 //
 // Sparse materials: a simulation's most frequent cell material is its
@@ -42,6 +42,8 @@ struct SimDev {
   float chy;   // dt / (mu0 dx):  Hz -= chy (Ey_{i+1} - Ey_i)
   float rdy;   // 1/dy: Ex += cb (Hz_j - Hz_{j-1}) / dy
   float rdx;   // 1/dx: Ey -= cb (Hz_i - Hz_{i-1}) / dx
+  float rdy2;  // 2/dy, 2/dx: the same products from r = cb / 2
+  float rdx2;
 };
 
 struct TileWork {   // one CTA of yee_step: columns [x0, x0 + kCtaCols), rows [y0, y1)

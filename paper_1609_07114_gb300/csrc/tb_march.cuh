@@ -326,10 +326,10 @@ yee_tb2m_kernel(const SimDev* __restrict__ sims, const TileWork* __restrict__ ti
     unsigned nmask = 0;
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
-      float ca, cb;
-      edge_coef(mp[t], m[t], ca, cb);
+      float ca, r;
+      edge_coef_r(mp[t], m[t], ca, r);
       nxa[t] = ca;
-      nxr[t] = __fmul_rn(cb, sd.rdy);
+      nxr[t] = __fmul_rn(r, sd.rdy2);
       const float v = __fmaf_rn(ca, exc[t], __fmul_rn(nxr[t], __fsub_rn(hn[t], hzp[t])));
       const bool upd = j >= 1 && cl + t < nx && mp[t].x >= 0.f && m[t].x >= 0.f;
       xa[t] = upd ? v : exc[t];
@@ -397,10 +397,10 @@ yee_tb2m_kernel(const SimDev* __restrict__ sims, const TileWork* __restrict__ ti
       const int i = cl + t;
       const float2 ml = t == 0 ? mL : m[t - 1];
       const float hl = t == 0 ? hl0 : hn[t - 1];
-      float ca, cb;
-      edge_coef(ml, m[t], ca, cb);
+      float ca, r;
+      edge_coef_r(ml, m[t], ca, r);
       nya[t] = ca;
-      nyr[t] = __fmul_rn(cb, sd.rdx);
+      nyr[t] = __fmul_rn(r, sd.rdx2);
       const float v = __fmaf_rn(ca, eyA[t], -__fmul_rn(nyr[t], __fsub_rn(hn[t], hl)));
       const bool upd = i >= 1 && i < nx && ml.x >= 0.f && m[t].x >= 0.f;
       ya[t] = upd ? v : eyA[t];
