@@ -424,6 +424,7 @@ typedef struct {
   int tile_rows;           /* tile height of the one-step stencil */
   int march_rows;          /* tile height of the row-marching two-step kernel (0: unused) */
   int march_ring;          /* rows it stages ahead through shared memory (0: loads to registers) */
+  int march_prefetch;      /* register loads: rows prefetched ahead, < 0 into L1, > 0 into L2 */
   int gemm_min;            /* simulations sharing a map from which it steps as a GEMM (0: fixed rule, 20) */
   int gemm_rows_per_warp;  /* GEMM CTA shape, 1 or 2 (0: fixed rule) */
   int chain;               /* two-step path, maps outside the zone tiles: 1 every model, 0 none,
@@ -439,7 +440,7 @@ typedef struct {
  * the context's life.  The candidates are the choices that leave every
  * result bit-identical: one or two steps per launch, the tile heights of the
  * one-step and two-step kernels, how many rows the two-step kernel stages
- * ahead, where the models' maps run on the two-step path, and from how many
+ * ahead or prefetches, where the models' maps run on the two-step path, and from how many
  * sharing simulations (and with which CTA shape) a map runs as a GEMM.  Search: one pass of coordinate descent from the fixed
  * rule, each candidate marched from the current state (no sources or probes,
  * a few ms of steps timed with CUDA events on the context's stream); a

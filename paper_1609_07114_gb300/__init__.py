@@ -67,7 +67,7 @@ FDTD_PML_W, FDTD_PML_E, FDTD_PML_S, FDTD_PML_N = 1, 2, 4, 8
 
 class fdtd_tune_report(C.Structure):
     _fields_ = [("steps_per_launch", C.c_int), ("tile_rows", C.c_int), ("march_rows", C.c_int),
-                ("march_ring", C.c_int),
+                ("march_ring", C.c_int), ("march_prefetch", C.c_int),
                 ("gemm_min", C.c_int), ("gemm_rows_per_warp", C.c_int), ("chain", C.c_int),
                 ("chained_models", C.c_int), ("candidates", C.c_int), ("ms_default", C.c_double),
                 ("ms_best", C.c_double)]

@@ -352,9 +352,20 @@ yee_step_kernel(const SimDev* __restrict__ sims, const TileWork* __restrict__ wo
     bool dcur = strip_dense(fw, js, js), dprev = true;   // row j's bit, row j-1's bit
     RowIn<V> cur, nxt;
     load_row<V>(cur, ex, ey, hz, mat, (size_t)js * P, P, cl, c0, nx, lane, halo, dcur, sd.mbg);
+    const int pf1 = run->pf1;
     for (int j = js; j < j1; ++j) {
       const size_t row = (size_t)j * P;
       const bool dn = strip_dense(fw, js, j + 1 < j1 ? j + 1 : j);
+      if (pf1 > 0 && j + 1 + pf1 < j1) {   // L1 prefetch of the lane's part of a later row
+        const size_t rp = row + (size_t)(1 + pf1) * P + cl;
+        asm volatile("prefetch.global.L1 [%0];" ::"l"(ex + rp + P));
+        asm volatile("prefetch.global.L1 [%0];" ::"l"(ey + rp));
+        asm volatile("prefetch.global.L1 [%0];" ::"l"(hz + rp));
+        if (strip_dense(fw, js, j + 1 + pf1)) {
+          asm volatile("prefetch.global.L1 [%0];" ::"l"(mat + rp));
+          if (V == 4) asm volatile("prefetch.global.L1 [%0];" ::"l"(mat + rp + 2));
+        }
+      }
       if (j + 1 < j1) load_row<V>(nxt, ex, ey, hz, mat, row + P, P, cl, c0, nx, lane, halo, dn, sd.mbg);
       stencil_row<V>(sd, cur, cy, j, j0, cl, nx, lane, halo, dcur, dprev, bc, row, hzo, exo, eyo);
       cur = nxt;
@@ -875,6 +886,7 @@ int set_global_error(int code, const std::string& msg) {
 namespace {
 
 constexpr int kChunk = 16;  // steps per captured graph (even: parity repeats)
+constexpr int kNoOverride = -1000;   // a tuner override not set
 
 struct SimHost {
   int nx = 0, ny = 0, pitch = 0;
@@ -990,6 +1002,7 @@ struct fdtd_ctx {
   int vec = 4;                     // columns per lane of the stencil kernel (2 or 4)
   bool stencil_tma = false;        // bulk-copy (TMA) ring form of the stencil (V = 4)
   bool pdl = true;                 // programmatic dependent launch of the step kernels (FDTD_PDL=0: off)
+  int pf1 = 0;                     // one-step stencil: rows prefetched into L1 ahead (FDTD_PF1)
   unsigned* status_d = nullptr;    // kernels' status word (RunDev::status)
   SimDev* sims_d = nullptr;
   TileWork* tiles_d = nullptr;
@@ -1079,14 +1092,14 @@ struct fdtd_ctx {
   DevBuf<MarchSrc> tbm_src;
   DevBuf<MarchPrb> tbm_prb;
   int tbm_th = 0;
-  int tbm_pf = 0;                  // rows prefetched into L2 ahead of the loads (FDTD_TB_PF)
+  int tbm_pf = 0;                  // rows prefetched ahead of the loads (FDTD_TB_PF: > 0 into L2, < 0 into L1)
   int tbm_mb = 4;                  // resident CTAs per SM the kernel is compiled for (FDTD_TB_MB)
   int tbm_ring = 0;                // rows staged ahead through shared memory (FDTD_TB_RING; 0: registers)
   bool tbm_sparse = false;         // some simulation has a background material (sparse-material form)
   // configuration chosen by fdtd_autotune (0: the fixed rule or the
   // environment): one-step tile rows, row-marching tile rows, simulations per
   // shared map from which it steps as a GEMM, GEMM rows per warp
-  int ov_th1 = 0, ov_thm = 0, ov_gemm_min = 0, ov_rpw = 0, ov_ring = -1;
+  int ov_th1 = 0, ov_thm = 0, ov_gemm_min = 0, ov_rpw = 0, ov_ring = -1, ov_pf = kNoOverride;
   // measurement mode (fdtd_set_timing)
   bool timing = false;
   std::vector<cudaEvent_t> ev;
@@ -1225,10 +1238,6 @@ int plan_tb(fdtd_ctx* ctx) {
     // against 280.1 Gcell-steps/s for 3 CTAs at 162 registers, 4096^2)
     ctx->tbm_mb = 4;
     if (const char* em = getenv("FDTD_TB_MB")) ctx->tbm_mb = atoi(em) == 3 ? 3 : 4;
-    ctx->tbm_ring = 0;
-    if (const char* eg = getenv("FDTD_TB_RING")) ctx->tbm_ring = std::min(4, std::max(0, atoi(eg)));
-    if (ctx->ov_ring >= 0) ctx->tbm_ring = ctx->ov_ring;
-    if (ctx->tbm_ring == 1 || ctx->tbm_mb == 3) ctx->tbm_ring = 0;
     // the sparse-material form where some strip row holds only background
     // material (a background alone, e.g. the vacuum rings of random grids,
     // saves nothing: every strip row is read)
@@ -1239,6 +1248,14 @@ int plan_tb(fdtd_ctx* ctx) {
         for (int st = 0; st < sh.nstrip && !ctx->tbm_sparse; ++st)
           ctx->tbm_sparse = ((sh.mbits[(size_t)(j >> 5) * sh.nstrip + st] >> (j & 31)) & 1u) == 0u;
     }
+    // loads through a ring of rows in shared memory: by default for the
+    // sparse form (its register form needs more than the 128 registers of
+    // 4 CTAs per SM; 8192^2 lattice: 0.342 ms per launch with a ring of 2
+    // against 0.459 with registers)
+    ctx->tbm_ring = ctx->tbm_sparse ? 2 : 0;
+    if (const char* eg = getenv("FDTD_TB_RING")) ctx->tbm_ring = std::min(4, std::max(0, atoi(eg)));
+    if (ctx->ov_ring >= 0) ctx->tbm_ring = ctx->ov_ring;
+    if (ctx->tbm_ring == 1 || ctx->tbm_mb == 3) ctx->tbm_ring = 0;
     if (ctx->tbm_ring > 0)
       CK(cudaFuncSetAttribute(march_fn(4, ctx->tbm_ring, ctx->tbm_sparse),
                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)march_smem(ctx->tbm_ring)));
@@ -1263,8 +1280,13 @@ int plan_tb(fdtd_ctx* ctx) {
     }
     if (const char* er = getenv("FDTD_TB_ROWS")) th = std::min(4096, std::max(4, atoi(er)));
     if (ctx->ov_thm) th = ctx->ov_thm;
-    ctx->tbm_pf = 0;
-    if (const char* ep = getenv("FDTD_TB_PF")) ctx->tbm_pf = std::min(16, std::max(0, atoi(ep)));
+    // Rows prefetched ahead of the register loads: FDTD_TB_PF = d > 0 into L2
+    // (a bulk prefetch), d < 0 into L1 (per lane), 0 none.  Default: L1, two
+    // rows ahead (measured on GB300, 4096^2: 0.0961 ms per launch against
+    // 0.1065 without, 0.1063 / 0.1014 / 0.1047 one / three / four rows ahead).
+    ctx->tbm_pf = -2;
+    if (const char* ep = getenv("FDTD_TB_PF")) ctx->tbm_pf = std::min(16, std::max(-8, atoi(ep)));
+    if (ctx->ov_pf != kNoOverride) ctx->tbm_pf = ctx->ov_pf;
     ctx->tbm_th = th;
     for (int s = 0; s < (int)ctx->sims.size(); ++s) {
       const SimHost& sh = ctx->sims[s];
@@ -1792,6 +1814,7 @@ int prepare_run(fdtd_ctx* ctx, long long nsteps, const fdtd_source* src, int nsr
   rd.dft_cell = ctx->dft_cell.p;
   rd.dft_acc = ctx->dft_acc.p;
   rd.nfreq = ctx->dft_nfreq;
+  rd.pf1 = ctx->pf1;
   rd.status = ctx->status_d;
   // Pageable host sources: cudaMemcpyAsync returns once the data are staged,
   // so the host vectors may go out of scope; the copies stay stream-ordered.
@@ -2021,6 +2044,8 @@ void plan_tiles(fdtd_ctx* ctx) {
   if (const char* e = getenv("FDTD_STENCIL")) ctx->stencil_tma = (vec == 4) && std::string(e) == "tma";
   ctx->pdl = true;
   if (const char* e = getenv("FDTD_PDL")) ctx->pdl = atoi(e) != 0;
+  ctx->pf1 = 0;
+  if (const char* e = getenv("FDTD_PF1")) ctx->pf1 = std::min(8, std::max(0, atoi(e)));
   int dev = 0, nsm = 1, occ = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);

@@ -128,7 +128,7 @@ struct RunDev {
   const int* dft_cell;
   double2* dft_acc;
   int nfreq;
-  int pad;
+  int pf1;                   // one-step stencil: rows prefetched into L1 ahead of its loads (0: none)
   unsigned* status;          // device word: bit 0 = a bounded wait in a kernel gave up
 };
 

@@ -150,6 +150,18 @@ __device__ __forceinline__ void march_prefetch(const float* ex, const float* ey,
   if (p && bytes) asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
+// L1 prefetch of the lane's part of row j (each lane its own 16-byte pieces;
+// no registers held).
+__device__ __forceinline__ void march_prefetch_l1(const float* ex, const float* ey, const float* hz,
+                                                  const float2* mat, int j, int P, int cl) {
+  const size_t row = (size_t)j * P + cl;
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(ex + row + P));
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(ey + row));
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(hz + row));
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(mat + row));
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(mat + row + 2));
+}
+
 __device__ __forceinline__ float pick4(const float (&v)[4], int t) {
   return t == 0 ? v[0] : (t == 1 ? v[1] : (t == 2 ? v[2] : v[3]));
 }
@@ -296,6 +308,7 @@ yee_tb2m_kernel(const SimDev* __restrict__ sims, const TileWork* __restrict__ ti
       slot = slot + 1 == kRing ? 0 : slot + 1;
     } else {
       if (pf > 0 && j + pf <= jAe && j + pf < ny) march_prefetch(ex, ey, hz, mat, j + pf, P, c0, lane);
+      if (pf < 0 && j - pf <= jAe && j - pf < ny && inb) march_prefetch_l1(ex, ey, hz, mat, j - pf, P, cl);
       if (j + 1 <= jAe)
         march_load(nxt, ex, ey, hz, mat, j + 1, ny, P, cl, inb, !kSparse || march_dense(sd, j + 1, c0, false, wbits),
                    bg);

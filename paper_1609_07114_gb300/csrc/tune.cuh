@@ -5,8 +5,8 @@
 // share one operation sequence per update; the model map's row and GEMM forms
 // add in the same order), so only time is at stake:
 //   - one or two steps per launch (FDTD_TB),
-//   - the one-step tile height, or the row-marching tile height and how many
-//     rows it stages ahead through shared memory,
+//   - the one-step tile height, or the row-marching tile height, how many
+//     rows it stages ahead through shared memory or prefetches into L1,
 //   - where the models' maps run on the two-step path (fused in the zone
 //     tiles, or in the zone chain: every model, or the shared maps),
 //   - from how many sharing simulations a map runs as a GEMM, and the GEMM
@@ -24,7 +24,7 @@
 namespace {
 
 struct TuneCfg {
-  int tb_mode, chain, th1, thm, gmin, rpw, ring;
+  int tb_mode, chain, th1, thm, gmin, rpw, ring, pf;
 };
 
 // The one-step tile table and per-simulation tile offsets on the device.
@@ -48,6 +48,7 @@ int apply_cfg(fdtd_ctx* ctx, const TuneCfg& c) {
   ctx->ov_gemm_min = c.gmin;
   ctx->ov_rpw = c.rpw;
   ctx->ov_ring = c.ring;
+  ctx->ov_pf = c.pf;
   drop_graphs(ctx);
   plan_tiles(ctx);
   int rc = upload_tiles(ctx);
@@ -165,8 +166,8 @@ bool cache_lookup(const char* path, const std::string& key, TuneCfg* c) {
   while (fgets(line, sizeof(line), f)) {
     char k[64];
     TuneCfg t{};
-    if (sscanf(line, "%63s tb=%d chain=%d th1=%d thm=%d gmin=%d rpw=%d ring=%d", k, &t.tb_mode, &t.chain, &t.th1,
-               &t.thm, &t.gmin, &t.rpw, &t.ring) == 8 &&
+    if (sscanf(line, "%63s tb=%d chain=%d th1=%d thm=%d gmin=%d rpw=%d ring=%d pf=%d", k, &t.tb_mode, &t.chain,
+               &t.th1, &t.thm, &t.gmin, &t.rpw, &t.ring, &t.pf) == 9 &&
         key == k) {
       *c = t;   // the last entry of a key wins
       found = true;
@@ -179,8 +180,8 @@ bool cache_lookup(const char* path, const std::string& key, TuneCfg* c) {
 void cache_store(const char* path, const std::string& key, const TuneCfg& c, double ms) {
   FILE* f = path ? fopen(path, "a") : nullptr;
   if (!f) return;
-  fprintf(f, "%s tb=%d chain=%d th1=%d thm=%d gmin=%d rpw=%d ring=%d ms_per_step=%.6f\n", key.c_str(), c.tb_mode,
-          c.chain, c.th1, c.thm, c.gmin, c.rpw, c.ring, ms);
+  fprintf(f, "%s tb=%d chain=%d th1=%d thm=%d gmin=%d rpw=%d ring=%d pf=%d ms_per_step=%.6f\n", key.c_str(),
+          c.tb_mode, c.chain, c.th1, c.thm, c.gmin, c.rpw, c.ring, c.pf, ms);
   fclose(f);
 }
 
@@ -193,6 +194,7 @@ void fill_report(const fdtd_ctx* ctx, fdtd_tune_report* rep) {
   rep->gemm_rows_per_warp = ctx->ov_rpw;
   rep->chain = ctx->tb_chain_mode;
   rep->march_ring = ctx->tb && ctx->tb_march ? ctx->tbm_ring : 0;
+  rep->march_prefetch = ctx->tb && ctx->tb_march && ctx->tbm_ring == 0 ? ctx->tbm_pf : 0;
   rep->chained_models = ctx->tb ? ctx->tb_nchain : 0;
 }
 
@@ -217,7 +219,7 @@ int run_autotune(fdtd_ctx* ctx, const char* cache_path, fdtd_tune_report* rep) {
   for (size_t a = 0; a < ctx->insts.size() && !shared; ++a)
     for (size_t b = a + 1; b < ctx->insts.size() && !shared; ++b)
       shared = ctx->insts[a].map == ctx->insts[b].map;
-  TuneCfg best{ctx->tb_mode, ctx->tb_chain_mode, 0, 0, 0, 0, -1};
+  TuneCfg best{ctx->tb_mode, ctx->tb_chain_mode, 0, 0, 0, 0, -1, kNoOverride};
   rc = apply_cfg(ctx, best);
   if (rc) return rc;
   double t_def = 0;
@@ -244,9 +246,19 @@ int run_autotune(fdtd_ctx* ctx, const char* cache_path, fdtd_tune_report* rep) {
   if (rc) return rc;
   best.tb_mode = ctx->tb ? 1 : 0;   // the fixed rule's choice (timed above), pinned
   {
+    // the other path; two steps also with every model in the zone chain
+    // (a large map on a small grid needs many CTAs to keep up with the march)
     TuneCfg c = best;
     c.tb_mode = 1 - best.tb_mode;
     if ((rc = tryc(c))) return rc;
+    if (!ctx->insts.empty())
+      for (int ch : {0, 1}) {
+        TuneCfg d = best;
+        d.tb_mode = 1;
+        d.chain = ch;
+        if (d.tb_mode == best.tb_mode && d.chain == best.chain) continue;
+        if ((rc = tryc(d))) return rc;
+      }
   }
   {
     rc = apply_cfg(ctx, best);
@@ -263,6 +275,11 @@ int run_autotune(fdtd_ctx* ctx, const char* cache_path, fdtd_tune_report* rep) {
       for (int rg : {0, 2, 3, 4}) {
         TuneCfg c = best;
         c.ring = rg;
+        if ((rc = tryc(c))) return rc;
+      }
+      for (int p : {0, -1, -2, -3}) {   // rows prefetched into L1 ahead of the register loads
+        TuneCfg c = best;
+        c.pf = p;
         if ((rc = tryc(c))) return rc;
       }
       if (!ctx->insts.empty())
