@@ -323,8 +323,97 @@ __device__ __forceinline__ void adj_load_row(AdjRowIn& r, const AdjSimDev& sd, c
   }
 }
 
-__global__ void __launch_bounds__(128, 3)
+// Staged form of the row loads (kRing >= 2): each lane copies its own eleven
+// float4 of a row (and lanes 0 and 31 their halo scalars) into its warp's ring
+// in shared memory with cp.async, kRing - 1 rows ahead of the row it computes,
+// one commit group per row; the copies in flight hold no registers, so the
+// kernel fits 128 registers (4 CTAs per SM) and keeps more bytes in flight.
+// A lane reads back only what it copied itself.  Slot layout per warp:
+// [11 values][32 lanes] float4, then 16 floats of halo scalars.
+constexpr int kAdjSlot4 = 11 * 32 + 4;   // float4 per warp and ring slot
+
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem));
+}
+
+// The loads of adj_load_row, issued into a ring slot (then one commit group).
+__device__ __forceinline__ void adj_issue_row(float4* slot, const AdjSimDev& sd, const float* __restrict__ gexa,
+                                              const float* __restrict__ geya, const float* __restrict__ gha,
+                                              const float* __restrict__ ex0, const float* __restrict__ ex1,
+                                              const float* __restrict__ ey0, const float* __restrict__ ey1,
+                                              size_t row, int P, int cl, int c0, int lane, bool halo, bool right) {
+  asm volatile("" ::: "memory");   // after the reads of the slot's previous row
+  cp_async16(slot + 0 * 32 + lane, gexa + row + P + cl, true);
+  cp_async16(slot + 1 * 32 + lane, geya + row + cl, true);
+  cp_async16(slot + 2 * 32 + lane, gha + row + cl, true);
+  cp_async16(slot + 3 * 32 + lane, sd.mat + row + P + cl, true);
+  cp_async16(slot + 4 * 32 + lane, sd.mat + row + P + cl + 2, true);
+  cp_async16(slot + 5 * 32 + lane, ex0 + row + P + cl, true);
+  cp_async16(slot + 6 * 32 + lane, ex1 + row + P + cl, true);
+  cp_async16(slot + 7 * 32 + lane, ey0 + row + cl, true);
+  cp_async16(slot + 8 * 32 + lane, ey1 + row + cl, true);
+  cp_async16(slot + 9 * 32 + lane, sd.geps + row + cl, true);
+  cp_async16(slot + 10 * 32 + lane, sd.gsig + row + cl, true);
+  float* e = reinterpret_cast<float*>(slot + 11 * 32);
+  if (halo) {
+    cp_async4(e + 0, gexa + row + P + c0 - 1);
+    cp_async4(e + 1, geya + row + c0 - 1);
+    cp_async4(e + 2, gha + row + c0 - 1);
+    cp_async8(e + 4, sd.mat + row + P + c0 - 1);
+    cp_async8(e + 6, sd.mat + row + c0 - 2);
+  }
+  if (right) {
+    cp_async4(e + 8, geya + row + c0 + 128);
+    cp_async4(e + 9, ey0 + row + c0 + 128);
+    cp_async4(e + 10, ey1 + row + c0 + 128);
+    cp_async8(e + 12, sd.mat + row + c0 + 128);
+  }
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+
+__device__ __forceinline__ void adj_fetch_row(AdjRowIn& r, const float4* slot, int lane, bool halo, bool right) {
+  r.gx1 = slot[0 * 32 + lane];
+  r.gy = slot[1 * 32 + lane];
+  r.gh = slot[2 * 32 + lane];
+  r.m1a = slot[3 * 32 + lane];
+  r.m1b = slot[4 * 32 + lane];
+  r.x0 = slot[5 * 32 + lane];
+  r.x1 = slot[6 * 32 + lane];
+  r.y0 = slot[7 * 32 + lane];
+  r.y1 = slot[8 * 32 + lane];
+  r.ae = slot[9 * 32 + lane];
+  r.as = slot[10 * 32 + lane];
+  const float* e = reinterpret_cast<const float*>(slot + 11 * 32);
+  if (right) {
+    r.gyR = e[8];
+    r.y0R = e[9];
+    r.y1R = e[10];
+    r.mR = make_float2(e[12], e[13]);
+  } else {
+    r.gyR = r.y0R = r.y1R = 0.f;
+    r.mR = make_float2(-1.f, 0.f);
+  }
+  if (halo) {
+    r.gx1L = e[0];
+    r.gyL = e[1];
+    r.ghL = e[2];
+    r.m1L = make_float2(e[4], e[5]);
+    r.mLL = make_float2(e[6], e[7]);
+  } else {
+    r.gx1L = r.gyL = r.ghL = 0.f;
+    r.m1L = r.mLL = make_float2(-1.f, 0.f);
+  }
+}
+
+template <int kRing, int kMinBlocks>
+__global__ void __launch_bounds__(128, kMinBlocks)
 adj_cell_kernel(const AdjSimDev* __restrict__ sims, const TileWork* __restrict__ tiles, int par, int t) {
+  extern __shared__ float4 adj_ring[];
   const unsigned FULL = 0xffffffffu;
   const TileWork tw = tiles[blockIdx.x];
   const AdjSimDev sd = sims[tw.sim];
@@ -381,11 +470,38 @@ adj_cell_kernel(const AdjSimDev* __restrict__ sims, const TileWork* __restrict__
     }
   }
   AdjRowIn cur, nxt;
-  adj_load_row(cur, sd, gexa, geya, gha, ex0, ex1, ey0, ey1, (size_t)js * P, P, cl, c0, lane, halo, right);
+  float4* ring = adj_ring + (size_t)warp * (kRing > 0 ? kRing : 1) * kAdjSlot4;
+  int slot = 0;
+  if constexpr (kRing > 0) {
+#pragma unroll
+    for (int d = 0; d < kRing - 1; ++d) {
+      if (js + d < j1)
+        adj_issue_row(ring + d * kAdjSlot4, sd, gexa, geya, gha, ex0, ex1, ey0, ey1, (size_t)(js + d) * P, P, cl, c0,
+                      lane, halo, right);
+      else
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+    }
+  } else {
+    adj_load_row(cur, sd, gexa, geya, gha, ex0, ex1, ey0, ey1, (size_t)js * P, P, cl, c0, lane, halo, right);
+  }
   for (int j = js; j < j1; ++j) {
     const size_t row = (size_t)j * P;
-    if (j + 1 < j1)
-      adj_load_row(nxt, sd, gexa, geya, gha, ex0, ex1, ey0, ey1, row + P, P, cl, c0, lane, halo, right);
+    if constexpr (kRing > 0) {
+      int ahead = slot + kRing - 1;
+      ahead -= ahead >= kRing ? kRing : 0;
+      // row j + kRing - 1 (past the tile: an empty group, so the count stays uniform)
+      if (j + kRing - 1 < j1)
+        adj_issue_row(ring + ahead * kAdjSlot4, sd, gexa, geya, gha, ex0, ex1, ey0, ey1, row + (size_t)(kRing - 1) * P,
+                      P, cl, c0, lane, halo, right);
+      else
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+      cp_async_wait_n<kRing - 1>();
+      adj_fetch_row(cur, ring + slot * kAdjSlot4, lane, halo, right);
+      slot = slot + 1 == kRing ? 0 : slot + 1;
+    } else {
+      if (j + 1 < j1)
+        adj_load_row(nxt, sd, gexa, geya, gha, ex0, ex1, ey0, ey1, row + P, P, cl, c0, lane, halo, right);
+    }
     const float2 m1[4] = {make_float2(cur.m1a.x, cur.m1a.y), make_float2(cur.m1a.z, cur.m1a.w),
                           make_float2(cur.m1b.x, cur.m1b.y), make_float2(cur.m1b.z, cur.m1b.w)};
     // Ex edges of row j+1 (cells j, j+1)
@@ -514,7 +630,7 @@ adj_cell_kernel(const AdjSimDev* __restrict__ sims, const TileWork* __restrict__
       ghp[q] = gn[q];
     }
     if (halo) mjL = cur.m1L;
-    cur = nxt;
+    if constexpr (kRing == 0) cur = nxt;
   }
 }
 
@@ -769,6 +885,14 @@ int run_grad(fdtd_ctx* ctx, long long nsteps, const fdtd_source* src, int nsrc,
     CK(cudaMemcpy(run2_d, &rd, sizeof(RunDev), cudaMemcpyHostToDevice));
   }
   const unsigned ntiles = (unsigned)ctx->tiles.size();
+  // The fused cell pass: row loads in registers one row ahead (FDTD_ADJ_RING=0,
+  // 167 registers, 3 CTAs per SM) or staged 1 / 2 rows ahead through shared
+  // memory (FDTD_ADJ_RING=2 / 3; 4 / 3 CTAs per SM); the same arithmetic.
+  int adj_ring = 0;
+  if (const char* er = getenv("FDTD_ADJ_RING")) adj_ring = atoi(er) == 2 ? 2 : atoi(er) == 3 ? 3 : 0;
+  auto cell_fn = adj_ring == 2 ? adj_cell_kernel<2, 4> : adj_ring == 3 ? adj_cell_kernel<3, 3> : adj_cell_kernel<0, 3>;
+  const size_t cell_smem = (size_t)adj_ring * 4 * kAdjSlot4 * sizeof(float4);
+  if (cell_smem > 0) CK(cudaFuncSetAttribute(cell_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cell_smem));
   // the reverse cell pass has its own tile plan (fewer resident CTAs per SM
   // than the forward kernel, so other tile heights fill whole waves)
   TileWork* atiles_d = nullptr;
@@ -777,7 +901,7 @@ int run_grad(fdtd_ctx* ctx, long long nsteps, const fdtd_source* src, int nsrc,
     int dev = 0, nsm = 1, occ = 1;
     CK(cudaGetDevice(&dev));
     CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, adj_cell_kernel, 128, 0));
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, cell_fn, 128, cell_smem));
     const std::vector<TileWork> at = tile_table(ctx->sims, best_tile_rows(ctx->sims, (long long)nsm * std::max(occ, 1)));
     CK(A.alloc(&atiles_d, at.size()));
     CK(cudaMemcpy(atiles_d, at.data(), sizeof(TileWork) * at.size(), cudaMemcpyHostToDevice));
@@ -817,7 +941,7 @@ int run_grad(fdtd_ctx* ctx, long long nsteps, const fdtd_source* src, int nsrc,
       if (nb > 0)
         adj_pre_kernel<<<nb, 128, pre_smem, st>>>(asd_d, aid_d, aw_d, (int)aw.size(), ar_d, par, t, n);
       if (fused) {
-        adj_cell_kernel<<<natiles, 128, 0, st>>>(asd_d, atiles_d, par, t);
+        cell_fn<<<natiles, 128, cell_smem, st>>>(asd_d, atiles_d, par, t);
       } else {
         adj_h_kernel<<<ntiles, 256, 0, st>>>(asd_d, ctx->tiles_d, par, t);
         adj_e_kernel<<<ntiles, 256, 0, st>>>(asd_d, ctx->tiles_d, par);

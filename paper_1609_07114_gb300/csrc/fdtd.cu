@@ -1024,6 +1024,17 @@ struct fdtd_ctx {
   DevBuf<const float*> waves;
   DevBuf<int> probe_sim, probe_cell;
   DevBuf<float> host_waves, host_probes;
+  // sources and probes the device lists were last built for (prepare_run;
+  // empty: rebuild), and the pinned slots the run record and wave pointers
+  // are copied from (a copy from pinned memory does not wait for the stream)
+  std::vector<long long> run_sig;
+  struct RunSlot {
+    unsigned char* host = nullptr;
+    size_t cap = 0;
+    cudaEvent_t done = nullptr;   // recorded after the slot's copies
+  };
+  RunSlot run_slots[4];
+  int run_slot_next = 0;
   // convolutional PML (fdtd_set_pml): per simulation its descriptor and
   // coefficient arrays, and the concatenated cell / edge lists of all
   // simulations with their auxiliaries
@@ -1067,7 +1078,7 @@ struct fdtd_ctx {
   // zone chain (tb.cuh zone_step_kernel / rom_chain_kernel): the last
   // tb_nchain model tiles step their maps outside the tile, on a side stream
   // of the highest priority forked from the context's stream per pair
-  int tb_chain_mode = -1;          // FDTD_TB_CHAIN at creation: 0 never, 1 every model, -1 shared maps
+  int tb_chain_mode = 1;           // FDTD_TB_CHAIN at creation: 0 never, 1 every model, 2 (-1) shared maps
   std::vector<char> in_gemm;       // per instance: stepped in a GEMM group (upload_instances)
   int tb_nchain = 0;
   int chain_nrow = 0;              // rom_chain_kernel blocks stepping single models (romwork prefix)
@@ -1162,6 +1173,7 @@ void drop_graphs(fdtd_ctx* ctx) {
 // step and no model lies within reach (two steps plus the zone margin) of
 // another's tile.
 int plan_tb(fdtd_ctx* ctx) {
+  ctx->run_sig.clear();   // the per-run lists follow the plan
   ctx->tb = false;
   ctx->tb_march = false;
   ctx->tb_nchain = 0;
@@ -1171,39 +1183,48 @@ int plan_tb(fdtd_ctx* ctx) {
   ctx->tbm_zone_rng.clear();
   ctx->tbm_zones.clear();
   // FDTD_TB=0: off; 1: on wherever it applies; unset: the row-marching form
-  // where it applies, unless (measured on GB300, against the one-step path)
-  // a model's work outlasts the march over the cells (small grids: one CTA
-  // stepping a model twice takes longer than the whole march; estimates:
-  // the march 6.6 ps per cell and pair of steps, a fused model tile 0.6 ns
-  // per element of [P | Q] plus 5 us, the zone chain 24 us plus its maps).
-  // (4096^2 benchmark grid: 300.7 against 189.3 Gcell-steps/s.)  The march
-  // reads the materials of background-only strip rows as the one-step kernel
-  // does, so grids of sparse scatterers take it too.  fdtd_autotune times
-  // both choices.
+  // where it applies, unless a fused model tile (one CTA stepping a model
+  // twice between the sub-steps) would make the pair of steps slower than two
+  // one-step launches.  Estimates, measured on GB300: the march 5.8 ps per
+  // cell and pair, a fused model tile 0.6 ns per element of [P | Q] plus
+  // 5 us, a one-step launch at least 3.5 us (5.3 ps per cell) plus 4.5 us for
+  // the model launch.  With every model in the zone chain (the default) two
+  // steps per launch measured faster at every size tried: 128^2 with a q = 400
+  // model 6.9 against 8.1 us per step, 1024^2 with a q = 400 model 7.9
+  // against 10.9, 1536^2 with 8 q = 200 models 11.1 against 11.4, the
+  // 4096^2 benchmark grid 342.8 against 188.2 Gcell-steps/s.  The march
+  // reads the materials of background-only strip rows as the one-step
+  // kernel does, so grids of sparse scatterers take it too.  fdtd_autotune
+  // times both choices.
   const int mode = ctx->tb_mode;
   if (mode == 0) return FDTD_OK;
   if (!ctx->pml_cells.empty()) return FDTD_OK;   // the layers' corrections need the one-step form
   const char* es = getenv("FDTD_TB_SMEM");
   const bool march = !(mode == 1 && es && atoi(es) == 1);
   // Models whose map is stepped outside their zone tile (zone chain):
-  // FDTD_TB_CHAIN=1 every model, 0 none, unset those whose map is shared by
-  // a GEMM group (one [P | Q] panel applied to many simulations' vectors).
+  // FDTD_TB_CHAIN=1 (default) every model, 0 none, 2 those whose map is
+  // shared by a GEMM group (one [P | Q] panel applied to many simulations'
+  // vectors).  Measured on GB300 (Gcell-steps/s, best tile height of each):
+  // every model chained 342.8 / 384.0 / 321.1 / 290.5 on the 4096^2 grid,
+  // the 8192^2 lattice, 256 batched grids and 16 x 1024^2, against 314.8 /
+  // 384.2 / 321.3 / 258.7 with only the shared maps and 315.1 / 349.3 /
+  // 272.0 / 258.5 with none: the chain spreads a model over many CTAs,
+  // where a fused tile holds one CTA for the whole map.
   const size_t ninst = ctx->insts.size();
   std::vector<char> chain(ninst, 0);
   for (size_t k = 0; k < ninst; ++k)
     chain[k] = ctx->tb_chain_mode == 1 ||
                (ctx->tb_chain_mode < 0 && k < ctx->in_gemm.size() && ctx->in_gemm[k]);
   if (mode != 1) {
-    double cells = 0, zone_us = 0, chain_nld = 0;
+    double cells = 0, fused_us = 0;
     for (const SimHost& sh : ctx->sims) cells += (double)sh.nx * sh.ny;
-    for (size_t k = 0; k < ninst; ++k) {
-      const Instance& in = ctx->insts[k];
-      if (chain[k]) chain_nld += (double)in.n * in.map->ld;
-      else zone_us = std::max(zone_us, 0.6e-3 * in.n * (double)in.map->ld + 5.0);
+    for (size_t k = 0; k < ninst; ++k)
+      if (!chain[k]) fused_us = std::max(fused_us, 0.6e-3 * ctx->insts[k].n * (double)ctx->insts[k].map->ld + 5.0);
+    if (fused_us > 0.0) {
+      const double two = std::max(5.8e-6 * cells, fused_us);
+      const double one = 2.0 * (std::max(5.3e-6 * cells, 3.5) + 4.5);
+      if (two >= one) return FDTD_OK;
     }
-    // the chain: four dependent launches (~6 us each) and two map products
-    if (chain_nld > 0) zone_us = std::max(zone_us, 24.0 + 1.33e-7 * chain_nld);
-    if (cells * 6.6e-6 < 1.25 * zone_us) return FDTD_OK;
   }
   const int M = kTbZoneMargin;
   std::vector<int4> zone(ninst);
@@ -1227,10 +1248,14 @@ int plan_tb(fdtd_ctx* ctx) {
     }
   ctx->tb_base.assign(ctx->sims.size(), 0);
   if (march) {
-    // kMarchCols x th tiles; th fills whole waves of resident CTAs:
-    // minimise ceil(T / slots) * (th + 3) (three rows of sub-step halo).
-    // The model tiles run beside the first wave; each takes the registers
-    // of two of this kernel's CTAs, so those slots are left to them.
+    // kMarchCols x th tiles, 8 <= th <= 64; th fills whole waves of
+    // resident CTAs: minimise ceil(T / slots) * (th + 3) (three rows of
+    // sub-step halo).  Fused model tiles run beside the first wave; each
+    // takes the registers of two of this kernel's CTAs, so those slots are
+    // left to them.  Measured on GB300: tiles taller than 64 rows (one
+    // under-filled wave) lose on large grids (8192^2 lattice: 357 rows 284,
+    // 64 rows 384 Gcell-steps/s), and a partial last wave costs a whole one
+    // (4096^2: 64 rows, 576 tiles, 342.8; 48 rows, 774 tiles, 295.9).
     int dev = 0, nsm = 1, occ = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -1261,11 +1286,9 @@ int plan_tb(fdtd_ctx* ctx) {
                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)march_smem(ctx->tbm_ring)));
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, march_fn(ctx->tbm_mb, ctx->tbm_ring, ctx->tbm_sparse), 128,
                                                   march_smem(ctx->tbm_ring));
-    // (a zone chain takes one slot per SM while its kernels run)
     long long nfused = 0;
     for (size_t k = 0; k < ninst; ++k) nfused += chain[k] ? 0 : 1;
-    const long long slots = std::max((long long)nsm, (long long)nsm * std::max(occ, 1) - 2 * nfused -
-                                                         (nfused < (long long)ninst ? (long long)nsm : 0));
+    const long long slots = std::max((long long)nsm, (long long)nsm * std::max(occ, 1) - 2 * nfused);
     auto tiles_for = [&](int th) {
       long long t = 0;
       for (const SimHost& sh : ctx->sims)
@@ -1274,7 +1297,7 @@ int plan_tb(fdtd_ctx* ctx) {
     };
     int th = 8;
     long long best = -1;
-    for (int h = 8; h <= 2048; ++h) {
+    for (int h = 8; h <= 64; ++h) {
       const long long cost = ((tiles_for(h) + slots - 1) / slots) * (h + 3);
       if (best < 0 || cost < best) best = cost, th = h;
     }
@@ -1615,9 +1638,59 @@ bool edge_updated(const SimHost& s, int comp, int i, int j) {
 }
 
 // Uploads the per-run source and probe tables (wave pointers already device).
+RunDev run_record(const fdtd_ctx* ctx, long long nsteps, float* probe_out, int nprobe);
+
+// The run record and the wave pointer table, copied in stream order from the
+// next pinned slot (reused once its previous copies have completed).
+int upload_run(fdtd_ctx* ctx, const RunDev& rd, const float* const* wave_dev, int nsrc) {
+  fdtd_ctx::RunSlot& sl = ctx->run_slots[ctx->run_slot_next];
+  ctx->run_slot_next = (ctx->run_slot_next + 1) % 4;
+  if (sl.done) CK(cudaEventSynchronize(sl.done));
+  else CK(cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming));
+  const size_t off = (sizeof(RunDev) + 15) & ~(size_t)15;
+  const size_t bytes = off + sizeof(float*) * (size_t)std::max(nsrc, 1);
+  if (sl.cap < bytes) {
+    if (sl.host) CK(cudaFreeHost(sl.host));
+    sl.host = nullptr;
+    sl.cap = 0;
+    CK(cudaHostAlloc((void**)&sl.host, bytes, cudaHostAllocDefault));
+    sl.cap = bytes;
+  }
+  std::memcpy(sl.host, &rd, sizeof(RunDev));
+  cudaStream_t st = ctx->stream;
+  if (nsrc > 0) {
+    std::memcpy(sl.host + off, wave_dev, sizeof(float*) * nsrc);
+    CK(cudaMemcpyAsync(ctx->waves.p, sl.host + off, sizeof(float*) * nsrc, cudaMemcpyHostToDevice, st));
+  }
+  CK(cudaMemcpyAsync(ctx->run_d, sl.host, sizeof(RunDev), cudaMemcpyHostToDevice, st));
+  CK(cudaEventRecord(sl.done, st));
+  return FDTD_OK;
+}
+
+// Uploads the per-run source and probe tables (wave pointers already
+// device).  The tables depend only on where the sources and probes sit and on
+// the plan, so when a run repeats the previous run's (a problem driven chunk
+// by chunk) they are kept and only the run record and the wave pointers are
+// copied; neither copy waits for the stream.
 int prepare_run(fdtd_ctx* ctx, long long nsteps, const fdtd_source* src, int nsrc,
                 const float* const* wave_dev, const fdtd_probe* probes, int nprobe,
                 float* probe_out) {
+  std::vector<long long> sig;
+  sig.reserve(2 + 5 * (size_t)nsrc + 3 * (size_t)nprobe);
+  sig.push_back(nsrc);
+  for (int s = 0; s < nsrc; ++s) {
+    const fdtd_source& so = src[s];
+    sig.insert(sig.end(), {(long long)so.sim, (long long)so.comp, (long long)so.i, (long long)so.j, (long long)so.len});
+  }
+  sig.push_back(nprobe);
+  for (int p = 0; p < nprobe; ++p) sig.insert(sig.end(), {(long long)probes[p].sim, (long long)probes[p].i, (long long)probes[p].j});
+  if (nprobe > 0 && !probe_out) return fail(ctx, FDTD_EINVAL, "fdtd_run: probe_out is NULL");
+  if (!ctx->run_sig.empty() && sig == ctx->run_sig) {
+    for (int s = 0; s < nsrc; ++s)
+      if (!wave_dev[s]) return fail(ctx, FDTD_EINVAL, "fdtd_run: malformed source " + std::to_string(s));
+    return upload_run(ctx, run_record(ctx, nsteps, probe_out, nprobe), wave_dev, nsrc);
+  }
+  ctx->run_sig.clear();
   const int ntiles = (int)ctx->tiles.size();
   std::vector<std::vector<SrcEdge>> per(ntiles);
   std::vector<unsigned char> seen;
@@ -1660,7 +1733,6 @@ int prepare_run(fdtd_ctx* ctx, long long nsteps, const fdtd_source* src, int nsr
     psim[p] = pr.sim;
     pcell[p] = pr.j * sh.pitch + pr.i;
   }
-  if (nprobe > 0 && !probe_out) return fail(ctx, FDTD_EINVAL, "fdtd_run: probe_out is NULL");
   CK(ctx->src_range.reserve(ntiles));
   CK(ctx->src_edges.reserve(edges.size()));
   CK(ctx->waves.reserve(std::max(nsrc, 1)));
@@ -1670,8 +1742,6 @@ int prepare_run(fdtd_ctx* ctx, long long nsteps, const fdtd_source* src, int nsr
   CK(cudaMemcpyAsync(ctx->src_range.p, range.data(), sizeof(int2) * ntiles, cudaMemcpyHostToDevice, st));
   if (!edges.empty())
     CK(cudaMemcpyAsync(ctx->src_edges.p, edges.data(), sizeof(SrcEdge) * edges.size(), cudaMemcpyHostToDevice, st));
-  if (nsrc > 0)
-    CK(cudaMemcpyAsync(ctx->waves.p, wave_dev, sizeof(float*) * nsrc, cudaMemcpyHostToDevice, st));
   if (nprobe > 0) {
     CK(cudaMemcpyAsync(ctx->probe_sim.p, psim.data(), sizeof(int) * nprobe, cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(ctx->probe_cell.p, pcell.data(), sizeof(int) * nprobe, cudaMemcpyHostToDevice, st));
@@ -1797,6 +1867,14 @@ int prepare_run(fdtd_ctx* ctx, long long nsteps, const fdtd_source* src, int nsr
       CK(cudaMemcpyAsync(ctx->tbm_d, &tmd, sizeof(TbMarchDev), cudaMemcpyHostToDevice, st));
     }
   }
+  const int rc = upload_run(ctx, run_record(ctx, nsteps, probe_out, nprobe), wave_dev, nsrc);
+  if (rc) return rc;
+  ctx->run_sig = std::move(sig);
+  return FDTD_OK;
+}
+
+// The run record of a run of nsteps from the current step.
+RunDev run_record(const fdtd_ctx* ctx, long long nsteps, float* probe_out, int nprobe) {
   RunDev rd{};
   rd.base = 0;
   rd.nsteps = nsteps;
@@ -1816,10 +1894,7 @@ int prepare_run(fdtd_ctx* ctx, long long nsteps, const fdtd_source* src, int nsr
   rd.nfreq = ctx->dft_nfreq;
   rd.pf1 = ctx->pf1;
   rd.status = ctx->status_d;
-  // Pageable host sources: cudaMemcpyAsync returns once the data are staged,
-  // so the host vectors may go out of scope; the copies stay stream-ordered.
-  CK(cudaMemcpyAsync(ctx->run_d, &rd, sizeof(RunDev), cudaMemcpyHostToDevice, st));
-  return FDTD_OK;
+  return rd;
 }
 
 void launch_tb(fdtd_ctx* ctx, cudaStream_t s, int par, int c);
@@ -2037,6 +2112,7 @@ std::vector<TileWork> tile_table(const std::vector<SimHost>& sims, int th) {
 // FDTD_VEC (2 or 4) and FDTD_TILE_ROWS override the choice (results are
 // identical; only speed changes).
 void plan_tiles(fdtd_ctx* ctx) {
+  ctx->run_sig.clear();
   int vec = 4;
   if (const char* e = getenv("FDTD_VEC")) vec = (atoi(e) == 2) ? 2 : 4;
   ctx->vec = vec;
@@ -2159,6 +2235,13 @@ void fdtd_destroy(fdtd_ctx* ctx) {
   ctx->tbm_src.release();
   ctx->tbm_prb.release();
   cudaFree(ctx->run_d);
+  for (fdtd_ctx::RunSlot& sl : ctx->run_slots) {
+    if (sl.done) {
+      cudaEventSynchronize(sl.done);
+      cudaEventDestroy(sl.done);
+    }
+    if (sl.host) cudaFreeHost(sl.host);
+  }
   cudaFree(ctx->status_d);
   cudaFree(ctx->einst_d);
   cudaFree(ctx->tile_base_d);
@@ -2280,7 +2363,7 @@ int fdtd_create(const fdtd_grid_desc* g, void* cuda_stream, fdtd_ctx** out) {
   }
   plan_tiles(ctx);
   if (const char* e = getenv("FDTD_TB")) ctx->tb_mode = atoi(e) != 0 ? 1 : 0;   // fixed for the context
-  if (const char* e = getenv("FDTD_TB_CHAIN")) ctx->tb_chain_mode = atoi(e) != 0 ? 1 : 0;
+  if (const char* e = getenv("FDTD_TB_CHAIN")) ctx->tb_chain_mode = atoi(e) == 0 ? 0 : atoi(e) == 2 ? -1 : 1;
   if (plan_tb(ctx) != FDTD_OK) return bail(FDTD_ECUDA);
   if (cudaMalloc(&ctx->sims_d, sizeof(SimDev) * sdev.size()) != cudaSuccess ||
       cudaMalloc(&ctx->tiles_d, sizeof(TileWork) * ctx->tiles.size()) != cudaSuccess ||

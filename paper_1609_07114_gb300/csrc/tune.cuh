@@ -246,13 +246,13 @@ int run_autotune(fdtd_ctx* ctx, const char* cache_path, fdtd_tune_report* rep) {
   if (rc) return rc;
   best.tb_mode = ctx->tb ? 1 : 0;   // the fixed rule's choice (timed above), pinned
   {
-    // the other path; two steps also with every model in the zone chain
-    // (a large map on a small grid needs many CTAs to keep up with the march)
+    // the other path; two steps also with each placement of the models'
+    // maps (fused tiles, the zone chain for every model or the shared maps)
     TuneCfg c = best;
     c.tb_mode = 1 - best.tb_mode;
     if ((rc = tryc(c))) return rc;
     if (!ctx->insts.empty())
-      for (int ch : {0, 1}) {
+      for (int ch : {-1, 0, 1}) {
         TuneCfg d = best;
         d.tb_mode = 1;
         d.chain = ch;
@@ -265,7 +265,7 @@ int run_autotune(fdtd_ctx* ctx, const char* cache_path, fdtd_tune_report* rep) {
     if (rc) return rc;
     const bool two = ctx->tb;
     const int cand1[] = {16, 24, 32, 48, 64, 96, 128};
-    const int cand2[] = {16, 24, 32, 48, 64, 96, 128, 192, 256};
+    const int cand2[] = {8, 16, 24, 32, 48, 64, 96, 128, 192, 256};
     if (two) {
       for (int th : cand2) {
         TuneCfg c = best;

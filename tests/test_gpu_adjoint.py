@@ -230,6 +230,33 @@ def test_fused_and_two_pass_reverse_steps_agree(monkeypatch, nx, ny):
     assert rel_l2(res["1"][3], res["0"][3]) < 1e-5
 
 
+@pytest.mark.parametrize("nx,ny", [(100, 80), (300, 230)])
+def test_staged_reverse_rows_are_bit_identical(monkeypatch, nx, ny):
+    """The fused reverse cell pass with its row loads staged one or two rows
+    ahead through shared memory (FDTD_ADJ_RING=2 / 3) against its register
+    form: the same arithmetic, so the same bits (probes kept off the cells
+    beside the models, whose additions would otherwise meet in atomics of
+    either order)."""
+    w = workloads.random_grid(64, nx, ny, 2, 5, 2, 20, 120, n_probes=6)
+    near = set()
+    for rd in w["roms"]:
+        for j in range(rd["j0"] - 1, rd["j0"] + rd["b"] + 1):
+            for i in range(rd["i0"] - 1, rd["i0"] + rd["a"] + 1):
+                near.add((i, j))
+    w["probes"] = [p for p in w["probes"] if p not in near]
+    assert len(w["probes"]) >= 3
+    res = {}
+    for r in ("0", "2", "3"):
+        monkeypatch.setenv("FDTD_ADJ_RING", r)
+        res[r] = gpu_grad([w], 120, 50)
+    assert np.abs(res["0"][1][0]).max() > 0
+    for r in ("2", "3"):
+        assert res[r][0] == res["0"][0]
+        for k in (1, 2):
+            np.testing.assert_array_equal(res[r][k][0], res["0"][k][0])
+        np.testing.assert_array_equal(res[r][3], res["0"][3])
+
+
 def test_multi_strip_gradients_match_oracle():
     """Several 128-column strips and tiles (halo rows and columns of the
     fused reverse pass) against the FP64 adjoint."""

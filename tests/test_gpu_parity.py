@@ -187,6 +187,42 @@ def test_split_runs_equal_one_run():
     assert ctx2.step_count() == 138
 
 
+def test_repeated_runs_reuse_and_rebuild_their_lists(monkeypatch):
+    """Runs that repeat the previous run's sources and probes keep the device
+    lists (only the run record and the wave pointers are copied, without
+    waiting for the stream); a run with other probes, and one after a
+    re-plan, rebuild them.  On the two-step path with chained models, 30 +
+    30 + 20 (other probes) + 20 + 20 (after the autotuner) steps, issued
+    without synchronising in between, equal one run of 120 steps bit for
+    bit."""
+    monkeypatch.setenv("FDTD_TB", "1")
+    w = workloads.random_grid(3, 700, 300, 3, 12, 3, 40, 120)
+    ctx1, _ = gpu_context([w])
+    assert ctx1.steps_per_launch() == 2
+    g1 = gpu_run(ctx1, [w], 120)
+    F1 = ctx1.get_fields(0)
+    ctx2, _ = gpu_context([w])
+    waves = [torch.tensor(np.asarray(so["wave"][:120], np.float32), device="cuda") for so in w["sources"]]
+    probes = [(0, i, j) for (i, j) in w["probes"]]
+    other = probes[4::-1]
+    outs, n0 = [], 0
+    for n, pr in ((30, probes), (30, probes), (20, other), (20, probes), (20, probes)):
+        if n0 == 100:
+            ctx2.autotune()
+        src = [dict(so, sim=0, wave=wv[n0:n0 + n]) for so, wv in zip(w["sources"], waves)]
+        out = torch.zeros((n, len(pr)), dtype=torch.float32, device="cuda")
+        ctx2.fdtd_run(n, src, pr, out)
+        outs.append((n0, n, pr, out))
+        n0 += n
+    torch.cuda.synchronize()
+    for n0, n, pr, out in outs:
+        if pr is probes:
+            np.testing.assert_array_equal(out.cpu().numpy(), g1[n0:n0 + n])
+    for a, b in zip(ctx2.get_fields(0), F1):
+        np.testing.assert_array_equal(a, b)
+    assert ctx2.step_count() == 120
+
+
 def test_invalid_inputs_are_rejected():
     w = workloads.cavity_60(10)
     ctx, _ = gpu_context([w])

@@ -122,26 +122,37 @@ def test_row_marching_form_is_bit_identical_to_one_step(monkeypatch, rows):
 
 
 def test_default_choice_of_the_two_step_path(monkeypatch):
-    """Unset FDTD_TB: the benchmark grid (4096^2, 8 models) steps in pairs;
-    a 1024^2 grid with the same 8 models and the 64-model lattice at 2048^2
-    (whose model tiles would outlast the march over so few cells) singly;
-    FDTD_TB=0 / 1 force the choice."""
+    """Unset FDTD_TB: with every model in the zone chain (the default) the
+    two-step path is taken at every size (the 4096^2 benchmark grid, a 128^2
+    grid with one q = 400 model, the 64-model lattice at 2048^2); with the
+    maps fused into their zone tiles (FDTD_TB_CHAIN=0) the small grid, where
+    one CTA stepping the model twice outlasts two one-step launches, steps
+    singly and the benchmark grid still in pairs; FDTD_TB=0 / 1 force the
+    choice."""
     import test_gpu_lattice as tl
     monkeypatch.delenv("FDTD_TB", raising=False)
+    monkeypatch.delenv("FDTD_TB_CHAIN", raising=False)
     w = workloads.grid_4096(10)
     ctx, _ = tp.gpu_context([w])
     assert ctx.steps_per_launch() == 2
     ctx.close()
-    ws = workloads.random_grid(1, 1024, 1024, 8, 16, 4, 200, 10)
-    assert tp.gpu_context([ws])[0].steps_per_launch() == 1
+    ws = workloads.random_grid(1, 128, 128, 1, 16, 4, 400, 10)
+    assert tp.gpu_context([ws])[0].steps_per_launch() == 2
     wl = workloads.lattice_8192(10, n=2048, pitch=256)
     ctxl, _ = tl.lattice_context(wl)
-    assert len(wl["roms"]) == 64 and ctxl.steps_per_launch() == 1
+    assert len(wl["roms"]) == 64 and ctxl.steps_per_launch() == 2
+    ctxl.close()
+    monkeypatch.setenv("FDTD_TB_CHAIN", "0")
+    assert tp.gpu_context([ws])[0].steps_per_launch() == 1
+    ctx, _ = tp.gpu_context([w])
+    assert ctx.steps_per_launch() == 2
+    ctx.close()
+    monkeypatch.delenv("FDTD_TB_CHAIN", raising=False)
     monkeypatch.setenv("FDTD_TB", "0")
     assert tp.gpu_context([w])[0].steps_per_launch() == 1
     monkeypatch.setenv("FDTD_TB", "1")
-    assert tl.lattice_context(wl)[0].steps_per_launch() == 2
-
+    monkeypatch.setenv("FDTD_TB_CHAIN", "0")
+    assert tp.gpu_context([ws])[0].steps_per_launch() == 2
 
 
 _BATCHED_MODELS = {}
