@@ -72,11 +72,20 @@ __device__ __forceinline__ void cb_ca(float2 m1, float2 m2, float& ca, float& cb
 }
 
 // ROM transpose, probe and source terms of reverse step n (segment index t).
-__global__ void __launch_bounds__(128)
+// A CTA of the model part takes kPreCols columns of one instance's [P | Q]
+// and splits each column's sum over the rows into kPreSlices consecutive row
+// slices, one warp each (in order r = r0, r0 + 1, ... within a slice, the
+// loads of 16 rows in flight together); the slices' partial sums are added in
+// slice order, so the result does not depend on scheduling.
+constexpr int kPreCols = 32, kPreSlices = 8;
+
+__global__ void __launch_bounds__(kPreCols * kPreSlices)
 adj_pre_kernel(const AdjSimDev* __restrict__ sims, const AdjInstDev* __restrict__ insts,
                const AdjWork* __restrict__ work, int nwork, const AdjRun* __restrict__ ar,
                int par, int t, long long n) {
-  extern __shared__ float gsh[];
+  extern __shared__ float gsh[];   // g_s (n floats), then the slices' partial sums
+  pdl_trigger();   // launched with programmatic serialisation: nothing read before pdl_wait
+  pdl_wait();
   const int b = blockIdx.x;
   if (b < nwork) {
     const AdjWork w = work[b];
@@ -96,28 +105,38 @@ adj_pre_kernel(const AdjSimDev* __restrict__ sims, const AdjInstDev* __restrict_
       gsh[k] = g;
     }
     __syncthreads();
-    for (int c = w.c0 + threadIdx.x; c < w.c1; c += blockDim.x) {
-      // column c of [P | Q] against g_s, in order r = 0, 1, ...; the loads of
-      // 16 rows are issued before their products so they are in flight together
-      float acc = 0.f;
+    const int lane = threadIdx.x & 31, sl = threadIdx.x >> 5;
+    const int c = w.c0 + lane;
+    const int rps = (ai.n + kPreSlices - 1) / kPreSlices;
+    const int r0 = sl * rps, r1 = min(ai.n, r0 + rps);
+    float acc = 0.f;
+    if (c < w.c1) {
       const float* __restrict__ Mc = ai.M + c;
-      for (int r0 = 0; r0 < ai.n; r0 += 16) {
+      for (int rb = r0; rb < r1; rb += 16) {
         float mv[16];
 #pragma unroll
-        for (int u = 0; u < 16; ++u) mv[u] = r0 + u < ai.n ? Mc[(size_t)(r0 + u) * ai.ld] : 0.f;
+        for (int u = 0; u < 16; ++u) mv[u] = rb + u < r1 ? Mc[(size_t)(rb + u) * ai.ld] : 0.f;
 #pragma unroll
         for (int u = 0; u < 16; ++u)
-          if (r0 + u < ai.n) acc = fmaf(mv[u], gsh[r0 + u], acc);
+          if (rb + u < r1) acc = fmaf(mv[u], gsh[rb + u], acc);
       }
+    }
+    float* part = gsh + ai.n;
+    part[sl * kPreCols + lane] = acc;
+    __syncthreads();
+    if (sl == 0 && c < w.c1) {
+      float tot = part[lane];
+#pragma unroll
+      for (int q = 1; q < kPreSlices; ++q) tot += part[q * kPreCols + lane];
       if (c < ai.n) {
-        gsb[c] = acc;
+        gsb[c] = tot;
       } else {
         const int k = c - ai.n;
-        atomicAdd(ghza + ai.h_cell[k], acc);
+        atomicAdd(ghza + ai.h_cell[k], tot);
         const float y0 = ai.sF[(size_t)t * ai.n + k];
         const float y1 = ai.sF[(size_t)(t + 1) * ai.n + k];
-        ai.geps_b[k] += (double)ai.lh_dt[k] * acc * ((double)y0 - y1);
-        ai.gsig_b[k] -= (double)ai.lh_2[k] * acc * ((double)y0 + y1);
+        ai.geps_b[k] += (double)ai.lh_dt[k] * tot * ((double)y0 - y1);
+        ai.gsig_b[k] -= (double)ai.lh_2[k] * tot * ((double)y0 + y1);
       }
     }
     return;
@@ -414,6 +433,8 @@ template <int kRing, int kMinBlocks>
 __global__ void __launch_bounds__(128, kMinBlocks)
 adj_cell_kernel(const AdjSimDev* __restrict__ sims, const TileWork* __restrict__ tiles, int par, int t) {
   extern __shared__ float4 adj_ring[];
+  pdl_trigger();   // launched with programmatic serialisation: nothing read before pdl_wait
+  pdl_wait();
   const unsigned FULL = 0xffffffffu;
   const TileWork tw = tiles[blockIdx.x];
   const AdjSimDev sd = sims[tw.sim];
@@ -811,8 +832,9 @@ int run_grad(fdtd_ctx* ctx, long long nsteps, const fdtd_source* src, int nsrc,
     CK(A.alloc(&a.geps_b, in.ny));
     CK(A.alloc(&a.gsig_b, in.ny));
     a.n = in.n, a.ny = in.ny, a.ld = in.map->ld, a.sim = in.sim;
-    for (int c0 = 0; c0 < in.n + in.ny; c0 += 128) aw.push_back({k, c0, std::min(in.n + in.ny, c0 + 128), 0});
-    pre_smem = std::max(pre_smem, sizeof(float) * (size_t)in.n);
+    for (int c0 = 0; c0 < in.n + in.ny; c0 += kPreCols)
+      aw.push_back({k, c0, std::min(in.n + in.ny, c0 + kPreCols), 0});
+    pre_smem = std::max(pre_smem, sizeof(float) * ((size_t)in.n + kPreCols * kPreSlices));
   }
   if (pre_smem > 48 * 1024) {
     if (pre_smem > 200 * 1024) return fail(ctx, FDTD_EINVAL, "fdtd_grad: reduced model too large");
@@ -907,7 +929,7 @@ int run_grad(fdtd_ctx* ctx, long long nsteps, const fdtd_source* src, int nsrc,
     CK(cudaMemcpy(atiles_d, at.data(), sizeof(TileWork) * at.size(), cudaMemcpyHostToDevice));
     natiles = (unsigned)at.size();
   }
-  const int npre_extra = (nprobe + nedges + 127) / 128;
+  const int npre_extra = (nprobe + nedges + kPreCols * kPreSlices - 1) / (kPreCols * kPreSlices);
   // one fused cell pass per reverse step (FDTD_ADJ_FUSED=0: the two-pass form)
   const char* fe = getenv("FDTD_ADJ_FUSED");
   const bool fused = !(fe && atoi(fe) == 0);
@@ -925,23 +947,31 @@ int run_grad(fdtd_ctx* ctx, long long nsteps, const fdtd_source* src, int nsrc,
     const long long base = k * C;
     CK(cudaMemcpyAsync(&run2_d->base, &base, sizeof(long long), cudaMemcpyHostToDevice, st));
     CK(cudaStreamSynchronize(st));
+    // (programmatic dependent launch where the context uses it, as the
+    // forward pass does: each kernel's launch overlaps the previous one's tail)
     for (int t = 0; t < L; ++t) {
+      const SimDev* sdt = simtab_d + (size_t)t * nsim;
       if (ctx->vec == 2)
-        yee_step_kernel<2><<<ntiles, kCtaCols / 2, 0, st>>>(simtab_d + (size_t)t * nsim, ctx->tiles_d, run2_d, 0, t);
+        launch_k(yee_step_kernel<2>, ntiles, kCtaCols / 2, 0, st, ctx->pdl, sdt, (const TileWork*)ctx->tiles_d,
+                 (const RunDev*)run2_d, 0, t);
       else
-        yee_step_kernel<4><<<ntiles, kCtaCols / 4, 0, st>>>(simtab_d + (size_t)t * nsim, ctx->tiles_d, run2_d, 0, t);
+        launch_k(yee_step_kernel<4>, ntiles, kCtaCols / 4, 0, st, ctx->pdl, sdt, (const TileWork*)ctx->tiles_d,
+                 (const RunDev*)run2_d, 0, t);
       if (ctx->nromwork + ctx->ngwork > 0)
-        rom_post_kernel<<<ctx->nromwork + ctx->ngwork, kRomRowsPerCta * 32, ctx->post_smem, st>>>(
-            simtab_d + (size_t)t * nsim, insttab_d + (size_t)t * ninst, ctx->romwork_d, ctx->nromwork,
-            run2_d, 0, t, ctx->groups_d, ctx->gwork_d, ctx->ngwork, ctx->ginst_d);
+        launch_k(rom_post_kernel, (unsigned)(ctx->nromwork + ctx->ngwork), kRomRowsPerCta * 32, ctx->post_smem, st,
+                 ctx->pdl, sdt, (const RomInstDev*)(insttab_d + (size_t)t * ninst), (const RomWork*)ctx->romwork_d,
+                 ctx->nromwork, (const RunDev*)run2_d, 0, t, (const GemmGroupDev*)ctx->groups_d,
+                 (const GemmWork*)ctx->gwork_d, ctx->ngwork, (const int*)ctx->ginst_d);
     }
     for (int t = L - 1; t >= 0; --t) {
       const long long n = k * C + t;
       const int nb = (int)aw.size() + npre_extra;
       if (nb > 0)
-        adj_pre_kernel<<<nb, 128, pre_smem, st>>>(asd_d, aid_d, aw_d, (int)aw.size(), ar_d, par, t, n);
+        launch_k(adj_pre_kernel, (unsigned)nb, kPreCols * kPreSlices, pre_smem, st, ctx->pdl, (const AdjSimDev*)asd_d,
+                 (const AdjInstDev*)aid_d, (const AdjWork*)aw_d, (int)aw.size(), (const AdjRun*)ar_d, par, t, n);
       if (fused) {
-        cell_fn<<<natiles, 128, cell_smem, st>>>(asd_d, atiles_d, par, t);
+        launch_k(cell_fn, natiles, 128, cell_smem, st, ctx->pdl, (const AdjSimDev*)asd_d, (const TileWork*)atiles_d,
+                 par, t);
       } else {
         adj_h_kernel<<<ntiles, 256, 0, st>>>(asd_d, ctx->tiles_d, par, t);
         adj_e_kernel<<<ntiles, 256, 0, st>>>(asd_d, ctx->tiles_d, par);

@@ -243,7 +243,9 @@ def test_staged_reverse_rows_are_bit_identical(monkeypatch, nx, ny):
         for j in range(rd["j0"] - 1, rd["j0"] + rd["b"] + 1):
             for i in range(rd["i0"] - 1, rd["i0"] + rd["a"] + 1):
                 near.add((i, j))
-    w["probes"] = [p for p in w["probes"] if p not in near]
+    si, sj = w["sources"][0]["i"], w["sources"][0]["j"]
+    cand = w["probes"] + [(min(si + 4, nx - 1), sj), (si, min(sj + 5, ny - 1)), (max(si - 6, 0), sj)]
+    w["probes"] = [p for p in cand if p not in near]
     assert len(w["probes"]) >= 3
     res = {}
     for r in ("0", "2", "3"):
