@@ -42,7 +42,7 @@ struct AdjSimDev {
 struct AdjInstDev {
   const float* M;        // [P | Q] FP32, n x ld (the forward's)
   float* gs[2];          // adjoint of [y; x~]
-  const float* sF;       // state frames: frame t at sF + t * n
+  const float* sF;       // state frames: frame t at sF + t * ld
   const int* y_edge;
   const int* h_cell;
   const float* lh_dt;    // (Dl Dl')_k / dt / (Dl G^T)_k
@@ -133,8 +133,8 @@ adj_pre_kernel(const AdjSimDev* __restrict__ sims, const AdjInstDev* __restrict_
       } else {
         const int k = c - ai.n;
         atomicAdd(ghza + ai.h_cell[k], tot);
-        const float y0 = ai.sF[(size_t)t * ai.n + k];
-        const float y1 = ai.sF[(size_t)(t + 1) * ai.n + k];
+        const float y0 = ai.sF[(size_t)t * ai.ld + k];
+        const float y1 = ai.sF[(size_t)(t + 1) * ai.ld + k];
         ai.geps_b[k] += (double)ai.lh_dt[k] * tot * ((double)y0 - y1);
         ai.gsig_b[k] -= (double)ai.lh_2[k] * tot * ((double)y0 + y1);
       }
@@ -814,7 +814,7 @@ int run_grad(fdtd_ctx* ctx, long long nsteps, const fdtd_source* src, int nsrc,
     a.M = in.map->M_d;
     CK(A.alloc(&a.gs[0], in.n));
     CK(A.alloc(&a.gs[1], in.n));
-    CK(A.alloc(&sF[k], (size_t)in.n * (C + 1)));
+    CK(A.alloc(&sF[k], (size_t)in.map->ld * (C + 1)));   // ld: room for the two-step path's h tail
     a.sF = sF[k];
     a.y_edge = in.y_edge_d;
     a.h_cell = in.h_cell_d;
@@ -865,9 +865,25 @@ int run_grad(fdtd_ctx* ctx, long long nsteps, const fdtd_source* src, int nsrc,
     AdjRun ar{probe_d, vjp ? seed : nullptr, ctx->probe_sim.p, ctx->probe_cell.p, ctx->src_edges.p, dsrc, nsteps, nprobe, nedges};
     CK(cudaMemcpy(ar_d, &ar, sizeof(AdjRun), cudaMemcpyHostToDevice));
   }
-  // per-step tables of the recomputation (frame t -> t+1), the same for every segment
-  std::vector<SimDev> simtab((size_t)C * nsim);
-  std::vector<RomInstDev> insttab((size_t)C * std::max(ninst, 1));
+  // The recomputation takes two steps per launch where the context does, with
+  // every model in the zone chain (FDTD_ADJ_RECOMP2=0: one step per launch):
+  // the march and the zone chain also write the E frame between the two
+  // sub-steps, and the chain's intermediate model state is that step's state
+  // frame; 40 B per cell and pair of steps against 64.  The fields are those
+  // of the one-step kernels bit for bit.
+  const char* er2 = getenv("FDTD_ADJ_RECOMP2");
+  MarchFn mframes = nullptr;
+  if (ctx->tb && ctx->tb_march && ctx->dft_nmon == 0 && ctx->tb_tiles.size() == (size_t)ctx->tb_nchain &&
+      !(er2 && atoi(er2) == 0))
+    mframes = march_frames_fn(ctx->tbm_mb, ctx->tbm_ring, ctx->tbm_sparse);
+  if (mframes && ctx->tbm_ring > 0)
+    CK(cudaFuncSetAttribute(mframes, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)march_smem(ctx->tbm_ring)));
+  const int npair = mframes ? C / 2 : 0;
+  // per-step tables of the recomputation (frame t -> t+1), and per pair of
+  // steps (frames 2p -> 2p+1 -> 2p+2), the same for every segment
+  std::vector<SimDev> simtab((size_t)C * nsim), simtab2((size_t)std::max(npair, 1) * nsim);
+  std::vector<RomInstDev> insttab((size_t)C * std::max(ninst, 1)),
+      insttab2((size_t)std::max(npair, 1) * std::max(ninst, 1));
   {
     std::vector<SimDev> base(nsim);
     CK(cudaMemcpy(base.data(), ctx->sims_d, sizeof(SimDev) * nsim, cudaMemcpyDeviceToHost));
@@ -885,11 +901,40 @@ int run_grad(fdtd_ctx* ctx, long long nsteps, const fdtd_source* src, int nsrc,
       }
       for (int k = 0; k < ninst; ++k) {
         RomInstDev d = ib[k];
-        d.state[0] = sF[k] + (size_t)ctx->insts[k].n * t;
-        d.state[1] = sF[k] + (size_t)ctx->insts[k].n * (t + 1);
+        d.state[0] = sF[k] + (size_t)ctx->insts[k].map->ld * t;
+        d.state[1] = sF[k] + (size_t)ctx->insts[k].map->ld * (t + 1);
         insttab[(size_t)t * ninst + k] = d;
       }
     }
+    for (int p = 0; p < npair; ++p) {
+      for (int s = 0; s < nsim; ++s) {
+        SimDev d = base[s];
+        const size_t fs = sim_off[s + 1] - sim_off[s];
+        d.ex[0] = exF[s] + fs * (2 * p), d.exm = exF[s] + fs * (2 * p + 1), d.ex[1] = exF[s] + fs * (2 * p + 2);
+        d.ey[0] = eyF[s] + fs * (2 * p), d.eym = eyF[s] + fs * (2 * p + 1), d.ey[1] = eyF[s] + fs * (2 * p + 2);
+        d.hz[0] = (p & 1) ? hB[s] : hA[s];
+        d.hz[1] = (p & 1) ? hA[s] : hB[s];
+        simtab2[(size_t)p * nsim + s] = d;
+      }
+      for (int k = 0; k < ninst; ++k) {
+        RomInstDev d = ib[k];
+        const size_t ld = (size_t)ctx->insts[k].map->ld;
+        d.state[0] = sF[k] + ld * (2 * p);
+        d.state_mid = sF[k] + ld * (2 * p + 1);
+        d.state[1] = sF[k] + ld * (2 * p + 2);
+        insttab2[(size_t)p * ninst + k] = d;
+      }
+    }
+  }
+  SimDev* simtab2_d = nullptr;
+  RomInstDev* insttab2_d = nullptr;
+  SimDev* tail_d = nullptr;   // the one step after the pairs of an odd segment
+  if (npair > 0) {
+    CK(A.alloc(&simtab2_d, simtab2.size()));
+    CK(A.alloc(&insttab2_d, insttab2.size()));
+    CK(A.alloc(&tail_d, nsim));
+    CK(cudaMemcpy(simtab2_d, simtab2.data(), sizeof(SimDev) * simtab2.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(insttab2_d, insttab2.data(), sizeof(RomInstDev) * insttab2.size(), cudaMemcpyHostToDevice));
   }
   SimDev* simtab_d = nullptr;
   RomInstDev* insttab_d = nullptr;
@@ -902,8 +947,11 @@ int run_grad(fdtd_ctx* ctx, long long nsteps, const fdtd_source* src, int nsrc,
   {
     RunDev rd;
     CK(cudaMemcpy(&rd, ctx->run_d, sizeof(RunDev), cudaMemcpyDeviceToHost));
-    rd.nprobe = 0;
-    rd.probe_out = nullptr;
+    // the two-step kernels write the probes they own: the forward's values
+    // again, into the forward's buffer; the one-step path launches no probe
+    // blocks
+    rd.nprobe = npair > 0 ? nprobe : 0;
+    rd.probe_out = npair > 0 ? probe_d : nullptr;
     CK(cudaMemcpy(run2_d, &rd, sizeof(RunDev), cudaMemcpyHostToDevice));
   }
   const unsigned ntiles = (unsigned)ctx->tiles.size();
@@ -949,8 +997,23 @@ int run_grad(fdtd_ctx* ctx, long long nsteps, const fdtd_source* src, int nsrc,
     CK(cudaStreamSynchronize(st));
     // (programmatic dependent launch where the context uses it, as the
     // forward pass does: each kernel's launch overlaps the previous one's tail)
-    for (int t = 0; t < L; ++t) {
-      const SimDev* sdt = simtab_d + (size_t)t * nsim;
+    int t0 = 0;
+    if (npair > 0) {
+      const int np = L / 2;
+      for (int p = 0; p < np; ++p)
+        launch_tb(ctx, st, 0, p, TbTables{simtab2_d + (size_t)p * nsim, insttab2_d + (size_t)p * ninst, run2_d, mframes});
+      t0 = 2 * np;
+      if (t0 < L && np > 0) {   // Hz of the last pair's output as the one-step tail's input
+        std::vector<SimDev> tail(simtab.begin() + (size_t)t0 * nsim, simtab.begin() + (size_t)(t0 + 1) * nsim);
+        for (int s = 0; s < nsim; ++s) {
+          tail[s].hz[0] = ((np - 1) & 1) ? hA[s] : hB[s];
+          tail[s].hz[1] = ((np - 1) & 1) ? hB[s] : hA[s];
+        }
+        CK(cudaMemcpyAsync(tail_d, tail.data(), sizeof(SimDev) * nsim, cudaMemcpyHostToDevice, st));
+      }
+    }
+    for (int t = t0; t < L; ++t) {
+      const SimDev* sdt = t > 0 && npair > 0 ? tail_d : simtab_d + (size_t)t * nsim;
       if (ctx->vec == 2)
         launch_k(yee_step_kernel<2>, ntiles, kCtaCols / 2, 0, st, ctx->pdl, sdt, (const TileWork*)ctx->tiles_d,
                  (const RunDev*)run2_d, 0, t);

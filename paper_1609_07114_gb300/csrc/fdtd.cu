@@ -1977,43 +1977,53 @@ int march_timed(fdtd_ctx* ctx, long long nsteps, int nprobe) {
 // The zone chain of one pair of steps on the side stream (highest priority,
 // so that its blocks are scheduled ahead of the march's pending ones),
 // forked from and joined back into s: half 0, map, half 1, map.
-void launch_chain(fdtd_ctx* ctx, cudaStream_t s, int par, int c) {
+// Device tables of a two-step launch: the context's own, or the gradient
+// recomputation's per-pair tables (frames of E and the model states).
+struct TbTables {
+  const SimDev* sims;
+  const RomInstDev* insts;
+  const RunDev* run;
+  MarchFn march;
+};
+
+TbTables own_tables(const fdtd_ctx* ctx) {
+  return {ctx->sims_d, ctx->insts_d, ctx->run_d, ctx->tb_march ? march_fn(ctx->tbm_mb, ctx->tbm_ring, ctx->tbm_sparse)
+                                                               : nullptr};
+}
+
+void launch_chain(fdtd_ctx* ctx, cudaStream_t s, int par, int c, const TbTables& tt) {
   const unsigned nz = (unsigned)ctx->tb_nchain;
   const TbTile* zt = ctx->tb_tiles_d + (ctx->tb_tiles.size() - nz);
   cudaStream_t q = ctx->side_stream;
   cudaEventRecord(ctx->ev_fork, s);
   cudaStreamWaitEvent(q, ctx->ev_fork, 0);
   const unsigned nmap = (unsigned)(ctx->chain_nrow + ctx->ngwork);
-  launch_k(zone_step_kernel<0>, nz, kTbThreads, ctx->zone_smem, q, false, ctx->prio_hi, (const SimDev*)ctx->sims_d,
-           zt, (const RomInstDev*)ctx->insts_d, (const RunDev*)ctx->run_d, (const TbRun*)ctx->tb_run_d,
-           ctx->zone_scratch.p, par, c);
-  launch_k(rom_chain_kernel, nmap, kRomRowsPerCta * 32, ctx->chain_smem, q, false, ctx->prio_hi,
-           (const SimDev*)ctx->sims_d, (const RomInstDev*)ctx->insts_d, (const RomWork*)ctx->romwork_d,
-           ctx->chain_nrow, (const GemmGroupDev*)ctx->groups_d, (const GemmWork*)ctx->gwork_d,
-           (const int*)ctx->ginst_d, par, 0);
-  launch_k(zone_step_kernel<1>, nz, kTbThreads, ctx->zone_smem, q, false, ctx->prio_hi, (const SimDev*)ctx->sims_d,
-           zt, (const RomInstDev*)ctx->insts_d, (const RunDev*)ctx->run_d, (const TbRun*)ctx->tb_run_d,
-           ctx->zone_scratch.p, par, c);
-  launch_k(rom_chain_kernel, nmap, kRomRowsPerCta * 32, ctx->chain_smem, q, false, ctx->prio_hi,
-           (const SimDev*)ctx->sims_d, (const RomInstDev*)ctx->insts_d, (const RomWork*)ctx->romwork_d,
-           ctx->chain_nrow, (const GemmGroupDev*)ctx->groups_d, (const GemmWork*)ctx->gwork_d,
-           (const int*)ctx->ginst_d, par, 1);
+  launch_k(zone_step_kernel<0>, nz, kTbThreads, ctx->zone_smem, q, false, ctx->prio_hi, tt.sims, zt, tt.insts, tt.run,
+           (const TbRun*)ctx->tb_run_d, ctx->zone_scratch.p, par, c);
+  launch_k(rom_chain_kernel, nmap, kRomRowsPerCta * 32, ctx->chain_smem, q, false, ctx->prio_hi, tt.sims, tt.insts,
+           (const RomWork*)ctx->romwork_d, ctx->chain_nrow, (const GemmGroupDev*)ctx->groups_d,
+           (const GemmWork*)ctx->gwork_d, (const int*)ctx->ginst_d, par, 0);
+  launch_k(zone_step_kernel<1>, nz, kTbThreads, ctx->zone_smem, q, false, ctx->prio_hi, tt.sims, zt, tt.insts, tt.run,
+           (const TbRun*)ctx->tb_run_d, ctx->zone_scratch.p, par, c);
+  launch_k(rom_chain_kernel, nmap, kRomRowsPerCta * 32, ctx->chain_smem, q, false, ctx->prio_hi, tt.sims, tt.insts,
+           (const RomWork*)ctx->romwork_d, ctx->chain_nrow, (const GemmGroupDev*)ctx->groups_d,
+           (const GemmWork*)ctx->gwork_d, (const int*)ctx->ginst_d, par, 1);
   cudaEventRecord(ctx->ev_join, q);
 }
 
-void launch_tb(fdtd_ctx* ctx, cudaStream_t s, int par, int c) {
+void launch_tb(fdtd_ctx* ctx, cudaStream_t s, int par, int c, const TbTables& tt) {
   const unsigned ntb = (unsigned)(ctx->tb_tiles.size() - ctx->tb_nchain);   // ordinary and fused model tiles
-  if (ctx->tb_nchain > 0) launch_chain(ctx, s, par, c);
+  if (ctx->tb_nchain > 0) launch_chain(ctx, s, par, c, tt);
   if (ntb > 0)
-    yee_tb2_kernel<<<ntb, kTbThreads, kTbSmemFields, s>>>(ctx->sims_d, ctx->tb_tiles_d, ctx->insts_d, ctx->run_d,
-                                                          ctx->tb_run_d, par, c);
+    yee_tb2_kernel<<<ntb, kTbThreads, kTbSmemFields, s>>>(tt.sims, ctx->tb_tiles_d, tt.insts, tt.run, ctx->tb_run_d,
+                                                          par, c);
   if (ctx->tb_march)   // overlaps the model tiles (programmatic serialisation) when there are any
-    launch_k(march_fn(ctx->tbm_mb, ctx->tbm_ring, ctx->tbm_sparse), (unsigned)ctx->tbm_tiles.size(), 128,
-             march_smem(ctx->tbm_ring), s,
-             ctx->pdl && ntb > 0, (const SimDev*)ctx->sims_d, (const TileWork*)ctx->tbm_tiles_d,
-             (const RunDev*)ctx->run_d, (const TbMarchDev*)ctx->tbm_d, par, c, ctx->tbm_pf);
+    launch_k(tt.march, (unsigned)ctx->tbm_tiles.size(), 128, march_smem(ctx->tbm_ring), s, ctx->pdl && ntb > 0,
+             tt.sims, (const TileWork*)ctx->tbm_tiles_d, tt.run, (const TbMarchDev*)ctx->tbm_d, par, c, ctx->tbm_pf);
   if (ctx->tb_nchain > 0) cudaStreamWaitEvent(s, ctx->ev_join, 0);
 }
+
+void launch_tb(fdtd_ctx* ctx, cudaStream_t s, int par, int c) { launch_tb(ctx, s, par, c, own_tables(ctx)); }
 
 int ensure_tb_graph(fdtd_ctx* ctx, int par, int nprobe) {
   if (ctx->tb_graph[par] && ctx->tb_graph_nprobe[par] == nprobe) return FDTD_OK;

@@ -44,6 +44,8 @@ struct SimDev {
   float rdx;   // 1/dx: Ey -= cb (Hz_i - Hz_{i-1}) / dx
   float rdy2;  // 2/dy, 2/dx: the same products from r = cb / 2
   float rdx2;
+  float* exm;  // two-step launches that keep every step's E (the gradient's
+  float* eym;  // recomputation): E^{n+1} between the sub-steps; else null
 };
 
 struct TileWork {   // one CTA of yee_step: columns [x0, x0 + kCtaCols), rows [y0, y1)

@@ -469,6 +469,15 @@ zone_step_kernel(const SimDev* __restrict__ sims, const TbTile* __restrict__ til
       (code >> 30 ? sEy : sEx)[S(off % P, off / P)] = ri.state_mid[k];
     }
     __syncthreads();
+    if (sd.exm) {   // E^{n+1} of the zone into the intermediate frame
+      const int w = X1 - X0;
+      for (int e = tid; e < w * (Y1 - Y0); e += kTbThreads) {
+        const int i = X0 + e % w, j = Y0 + e / w;
+        const size_t off = (size_t)j * P + i;
+        sd.exm[off] = sEx[S(i, j)];
+        sd.eym[off] = sEy[S(i, j)];
+      }
+    }
     h_update();
     __syncthreads();
     probes(n0 + 1);

@@ -214,7 +214,7 @@ __device__ __forceinline__ void cp_async_wait_n() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-template <int kMinBlocks, int kRing, bool kSparse>
+template <int kMinBlocks, int kRing, bool kSparse, bool kFrames = false>
 __global__ void __launch_bounds__(128, kMinBlocks)
 yee_tb2m_kernel(const SimDev* __restrict__ sims, const TileWork* __restrict__ tiles,
                 const RunDev* __restrict__ run, const TbMarchDev* __restrict__ tm, int par, int c, int pf) {
@@ -424,6 +424,19 @@ yee_tb2m_kernel(const SimDev* __restrict__ sims, const TileWork* __restrict__ ti
       march_source(ya, sa, cl, JA);
       sa = march_src_at(tm->src, ++kA, sr.y);
     }
+    if constexpr (kFrames) {
+      // E^{n+1}(j) into the intermediate frame (zone cells: the zone chain)
+      bool keep = owner && j >= j0 && j < j1;
+      for (int z = zr.x; z < zr.y; ++z) {
+        const int4 zn = tm->zones[z];
+        if (j >= zn.y && j < zn.w && cl < zn.z && cl + 4 > zn.x) keep = false;
+      }
+      if (keep) {
+        const size_t off = (size_t)j * P + cl;
+        st4(sd.exm + off, make_float4(xa[0], xa[1], xa[2], xa[3]));
+        st4(sd.eym + off, make_float4(ya[0], ya[1], ya[2], ya[3]));
+      }
+    }
     // ---- carry to row j + 1
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
@@ -462,5 +475,14 @@ MarchFn march_fn(int mb, int ring, bool sparse) {
   }
 }
 size_t march_smem(int ring) { return ring > 0 ? (size_t)ring * kMarchRingBytesPerRow : 0; }
+
+// The form that also writes the intermediate E frame (sd.exm, sd.eym), for
+// the plans the gradient's recomputation supports (else null).
+MarchFn march_frames_fn(int mb, int ring, bool sparse) {
+  if (mb != 4) return nullptr;
+  if (ring == 0 && !sparse) return yee_tb2m_kernel<4, 0, false, true>;
+  if (ring == 2) return sparse ? yee_tb2m_kernel<4, 2, true, true> : yee_tb2m_kernel<4, 2, false, true>;
+  return nullptr;
+}
 
 }  // namespace

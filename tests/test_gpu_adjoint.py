@@ -230,14 +230,11 @@ def test_fused_and_two_pass_reverse_steps_agree(monkeypatch, nx, ny):
     assert rel_l2(res["1"][3], res["0"][3]) < 1e-5
 
 
-@pytest.mark.parametrize("nx,ny", [(100, 80), (300, 230)])
-def test_staged_reverse_rows_are_bit_identical(monkeypatch, nx, ny):
-    """The fused reverse cell pass with its row loads staged one or two rows
-    ahead through shared memory (FDTD_ADJ_RING=2 / 3) against its register
-    form: the same arithmetic, so the same bits (probes kept off the cells
-    beside the models, whose additions would otherwise meet in atomics of
-    either order)."""
-    w = workloads.random_grid(64, nx, ny, 2, 5, 2, 20, 120, n_probes=6)
+def _off_ring_case(nx, ny, nsteps=120):
+    """A gradient case whose probes sit off the cells beside the models
+    (their probe and model additions would otherwise meet in atomics of
+    either order, so two runs could differ in the last bit)."""
+    w = workloads.random_grid(64, nx, ny, 2, 5, 2, 20, nsteps, n_probes=6)
     near = set()
     for rd in w["roms"]:
         for j in range(rd["j0"] - 1, rd["j0"] + rd["b"] + 1):
@@ -247,6 +244,35 @@ def test_staged_reverse_rows_are_bit_identical(monkeypatch, nx, ny):
     cand = w["probes"] + [(min(si + 4, nx - 1), sj), (si, min(sj + 5, ny - 1)), (max(si - 6, 0), sj)]
     w["probes"] = [p for p in cand if p not in near]
     assert len(w["probes"]) >= 3
+    return w
+
+
+@pytest.mark.parametrize("nx,ny,ckpt", [(100, 80, 7), (100, 80, 50), (300, 230, 25)])
+def test_two_step_recomputation_is_bit_identical(monkeypatch, nx, ny, ckpt):
+    """The recomputation in pairs of steps (the march and the zone chain also
+    writing the E frame between the sub-steps; odd segments end with one
+    single step) against one step per launch (FDTD_ADJ_RECOMP2=0): the same
+    frames, so the same gradient bits."""
+    monkeypatch.delenv("FDTD_TB", raising=False)
+    w = _off_ring_case(nx, ny)
+    res = {}
+    for r in ("0", "1"):
+        monkeypatch.setenv("FDTD_ADJ_RECOMP2", r)
+        res[r] = gpu_grad([w], 120, ckpt)
+        assert res[r][4].steps_per_launch() == 2
+    assert np.abs(res["0"][1][0]).max() > 0
+    assert res["1"][0] == res["0"][0]
+    for k in (1, 2):
+        np.testing.assert_array_equal(res["1"][k][0], res["0"][k][0])
+    np.testing.assert_array_equal(res["1"][3], res["0"][3])
+
+
+@pytest.mark.parametrize("nx,ny", [(100, 80), (300, 230)])
+def test_staged_reverse_rows_are_bit_identical(monkeypatch, nx, ny):
+    """The fused reverse cell pass with its row loads staged one or two rows
+    ahead through shared memory (FDTD_ADJ_RING=2 / 3) against its register
+    form: the same arithmetic, so the same bits."""
+    w = _off_ring_case(nx, ny)
     res = {}
     for r in ("0", "2", "3"):
         monkeypatch.setenv("FDTD_ADJ_RING", r)
