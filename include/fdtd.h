@@ -442,8 +442,11 @@ typedef struct {
  * one-step and two-step kernels, how many rows the two-step kernel stages
  * ahead or prefetches, where the models' maps run on the two-step path, and from how many
  * sharing simulations (and with which CTA shape) a map runs as a GEMM.  Search: one pass of coordinate descent from the fixed
- * rule, each candidate marched from the current state (no sources or probes,
- * a few ms of steps timed with CUDA events on the context's stream); a
+ * rule, each candidate marched from the current state with the source and
+ * probe positions of the context's most recent fdtd_run / fdtd_run_host (the
+ * sources at zero amplitude, the probe samples into a scratch buffer; none
+ * before the first run), a few ms of steps timed with CUDA events on the
+ * context's stream; a
  * candidate wins only if more than 1% faster.  The marching state (fields,
  * model states, step count, PML auxiliaries, DFT sums) is restored after
  * every candidate, so the context continues where it was.  cache_path (NULL:

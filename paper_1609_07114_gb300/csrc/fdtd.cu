@@ -1028,6 +1028,10 @@ struct fdtd_ctx {
   // empty: rebuild), and the pinned slots the run record and wave pointers
   // are copied from (a copy from pinned memory does not wait for the stream)
   std::vector<long long> run_sig;
+  // sources (waveforms left out) and probes of the most recent fdtd_run /
+  // fdtd_run_host: the autotuner times its candidates with them
+  std::vector<fdtd_source> last_src;
+  std::vector<fdtd_probe> last_prb;
   struct RunSlot {
     unsigned char* host = nullptr;
     size_t cap = 0;
@@ -2524,6 +2528,13 @@ int fdtd_get_rom_map(const fdtd_ctx* ctx, int inst, int* n, int* ny, double* P, 
   return FDTD_OK;
 }
 
+// The sources' positions (waveforms dropped) and the probes of a run.
+static void remember_layout(fdtd_ctx* ctx, const fdtd_source* src, int nsrc, const fdtd_probe* probes, int nprobe) {
+  ctx->last_src.assign(src, src + nsrc);
+  for (fdtd_source& s : ctx->last_src) s.wave = nullptr;
+  ctx->last_prb.assign(probes, probes + nprobe);
+}
+
 int fdtd_run(fdtd_ctx* ctx, long long nsteps, const fdtd_source* src, int nsrc,
              const fdtd_probe* probes, int nprobe, float* probe_out) {
   NvtxRange nvtx_("fdtd_run");
@@ -2534,6 +2545,7 @@ int fdtd_run(fdtd_ctx* ctx, long long nsteps, const fdtd_source* src, int nsrc,
   for (int s = 0; s < nsrc; ++s) w[s] = src[s].wave;
   int rc = prepare_run(ctx, nsteps, src, nsrc, w.data(), probes, nprobe, probe_out);
   if (rc) return rc;
+  remember_layout(ctx, src, nsrc, probes, nprobe);
   return march(ctx, nsteps, nprobe);
 }
 
@@ -2555,6 +2567,7 @@ int fdtd_run_host(fdtd_ctx* ctx, long long nsteps, const fdtd_source* src, int n
   }
   int rc = prepare_run(ctx, nsteps, src, nsrc, w.data(), probes, nprobe, ctx->host_probes.p);
   if (rc) return rc;
+  remember_layout(ctx, src, nsrc, probes, nprobe);
   rc = march(ctx, nsteps, nprobe);
   if (rc) return rc;
   if (nprobe > 0)

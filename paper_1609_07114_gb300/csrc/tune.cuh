@@ -13,8 +13,10 @@
 //     CTA shape (rows per warp).
 // The search is one pass of coordinate descent from the fixed rule, in that
 // order; each candidate is re-planned, marched warm-up + K steps from the
-// current state (no sources or probes) with the K steps timed by CUDA events
-// on the context's stream, and the state restored from a device snapshot.
+// current state (with the source and probe positions of the context's most
+// recent run, the sources at zero amplitude) with the K steps timed by CUDA
+// events on the context's stream, and the state restored from a device
+// snapshot.
 // A candidate replaces the best only if it is faster by more than 1% (graph
 // replays repeat to a fraction of that).  The winner is kept for the
 // context's life and, when a cache file is given, stored under a key of the
@@ -105,16 +107,44 @@ int snap_restore(fdtd_ctx* ctx, const TuneSnap& sn) {
 
 // Device ms per time step of the applied configuration over K steps (after
 // `warm` untimed ones); the state is restored afterwards.
-int time_cfg(fdtd_ctx* ctx, const TuneSnap& sn, int warm, int K, double* ms) {
-  int rc = prepare_run(ctx, warm + K, nullptr, 0, nullptr, nullptr, 0, nullptr);
+// The most recent run's sources (sharing one zero waveform, so the fields do
+// not change) and probes (into a scratch buffer): the candidates are timed
+// with the source and probe lists they will run with.
+struct TuneRun {
+  std::vector<fdtd_source> src;
+  std::vector<const float*> wv;
+  DevBuf<float> zero, pout;
+  ~TuneRun() {
+    zero.release();
+    pout.release();
+  }
+};
+constexpr int kTuneMaxSteps = kChunk + 512;   // warm-up + timed steps of one candidate
+
+int tune_run_init(fdtd_ctx* ctx, TuneRun& tr) {
+  tr.src = ctx->last_src;
+  if (!tr.src.empty()) {
+    CK(tr.zero.reserve(kTuneMaxSteps));
+    CK(cudaMemsetAsync(tr.zero.p, 0, sizeof(float) * kTuneMaxSteps, ctx->stream));
+    for (fdtd_source& s : tr.src) s.wave = tr.zero.p;
+  }
+  tr.wv.assign(std::max<size_t>(tr.src.size(), 1), tr.zero.p);
+  if (!ctx->last_prb.empty()) CK(tr.pout.reserve((size_t)kTuneMaxSteps * ctx->last_prb.size()));
+  return FDTD_OK;
+}
+
+int time_cfg(fdtd_ctx* ctx, const TuneSnap& sn, const TuneRun& tr, int warm, int K, double* ms) {
+  const int nprobe = (int)ctx->last_prb.size();
+  int rc = prepare_run(ctx, warm + K, tr.src.empty() ? nullptr : tr.src.data(), (int)tr.src.size(), tr.wv.data(),
+                       nprobe ? ctx->last_prb.data() : nullptr, nprobe, tr.pout.p);
   if (rc) return rc;
-  rc = march(ctx, warm, 0);
+  rc = march(ctx, warm, nprobe);
   if (rc) return rc;
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
   CK(cudaEventRecord(e0, ctx->stream));
-  rc = march(ctx, K, 0);
+  rc = march(ctx, K, nprobe);
   CK(cudaEventRecord(e1, ctx->stream));
   CK(cudaEventSynchronize(e1));
   float t = 0.f;
@@ -214,6 +244,9 @@ int run_autotune(fdtd_ctx* ctx, const char* cache_path, fdtd_tune_report* rep) {
   TuneSnap sn;
   int rc = snap_take(ctx, sn);
   if (rc) return rc;
+  TuneRun tr;
+  rc = tune_run_init(ctx, tr);
+  if (rc) return rc;
   // the fixed rule (as the context was created), then per dimension
   bool shared = false;   // some map is used by two or more instances
   for (size_t a = 0; a < ctx->insts.size() && !shared; ++a)
@@ -223,11 +256,11 @@ int run_autotune(fdtd_ctx* ctx, const char* cache_path, fdtd_tune_report* rep) {
   rc = apply_cfg(ctx, best);
   if (rc) return rc;
   double t_def = 0;
-  rc = time_cfg(ctx, sn, kChunk, kChunk, &t_def);
+  rc = time_cfg(ctx, sn, tr, kChunk, kChunk, &t_def);
   if (rc) return rc;
   // K: a multiple of the graph chunk lasting a few ms
   const int K = std::max(kChunk, std::min(512, (int)std::ceil(4.0 / std::max(t_def, 1e-4) / kChunk) * kChunk));
-  rc = time_cfg(ctx, sn, kChunk, K, &t_def);
+  rc = time_cfg(ctx, sn, tr, kChunk, K, &t_def);
   if (rc) return rc;
   double t_best = t_def;
   int ncand = 2;
@@ -236,7 +269,7 @@ int run_autotune(fdtd_ctx* ctx, const char* cache_path, fdtd_tune_report* rep) {
     if (r) return r;
     if (c.tb_mode == 1 && !ctx->tb) return FDTD_OK;   // the two-step path does not apply here
     double t = 0;
-    r = time_cfg(ctx, sn, kChunk, K, &t);
+    r = time_cfg(ctx, sn, tr, kChunk, K, &t);
     if (r) return r;
     ++ncand;
     if (t < 0.99 * t_best) t_best = t, best = c;
