@@ -433,14 +433,16 @@ typedef struct {
   int candidates;          /* configurations timed (0: taken from the cache file) */
   double ms_default;       /* device ms per time step of the fixed rule */
   double ms_best;          /* ... and of the chosen configuration */
+  int march_ctas;          /* resident CTAs per SM the row-marching kernel is built for, 4 or 3 (0: unused) */
 } fdtd_tune_report;
 
 /* Autotuner of the launch configuration (no counterpart in the paper): times
  * candidate configurations on the context itself and keeps the fastest for
  * the context's life.  The candidates are the choices that leave every
  * result bit-identical: one or two steps per launch, the tile heights of the
- * one-step and two-step kernels, how many rows the two-step kernel stages
- * ahead or prefetches, where the models' maps run on the two-step path, and from how many
+ * one-step and two-step kernels, the two-step kernel's resident CTAs per SM
+ * (4 or 3) and how many rows it stages ahead or prefetches, where the
+ * models' maps run on the two-step path, and from how many
  * sharing simulations (and with which CTA shape) a map runs as a GEMM.  Search: one pass of coordinate descent from the fixed
  * rule, each candidate marched from the current state with the source and
  * probe positions of the context's most recent fdtd_run / fdtd_run_host (the

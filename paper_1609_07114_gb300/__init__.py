@@ -70,7 +70,7 @@ class fdtd_tune_report(C.Structure):
                 ("march_ring", C.c_int), ("march_prefetch", C.c_int),
                 ("gemm_min", C.c_int), ("gemm_rows_per_warp", C.c_int), ("chain", C.c_int),
                 ("chained_models", C.c_int), ("candidates", C.c_int), ("ms_default", C.c_double),
-                ("ms_best", C.c_double)]
+                ("ms_best", C.c_double), ("march_ctas", C.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

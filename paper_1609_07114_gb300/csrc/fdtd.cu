@@ -1114,7 +1114,7 @@ struct fdtd_ctx {
   // configuration chosen by fdtd_autotune (0: the fixed rule or the
   // environment): one-step tile rows, row-marching tile rows, simulations per
   // shared map from which it steps as a GEMM, GEMM rows per warp
-  int ov_th1 = 0, ov_thm = 0, ov_gemm_min = 0, ov_rpw = 0, ov_ring = -1, ov_pf = kNoOverride;
+  int ov_th1 = 0, ov_thm = 0, ov_gemm_min = 0, ov_rpw = 0, ov_ring = -1, ov_pf = kNoOverride, ov_mb = 0;
   // measurement mode (fdtd_set_timing)
   bool timing = false;
   std::vector<cudaEvent_t> ev;
@@ -1267,6 +1267,7 @@ int plan_tb(fdtd_ctx* ctx) {
     // against 280.1 Gcell-steps/s for 3 CTAs at 162 registers, 4096^2)
     ctx->tbm_mb = 4;
     if (const char* em = getenv("FDTD_TB_MB")) ctx->tbm_mb = atoi(em) == 3 ? 3 : 4;
+    if (ctx->ov_mb) ctx->tbm_mb = ctx->ov_mb;
     // the sparse-material form where some strip row holds only background
     // material (a background alone, e.g. the vacuum rings of random grids,
     // saves nothing: every strip row is read)

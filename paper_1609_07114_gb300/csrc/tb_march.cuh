@@ -479,6 +479,7 @@ size_t march_smem(int ring) { return ring > 0 ? (size_t)ring * kMarchRingBytesPe
 // The form that also writes the intermediate E frame (sd.exm, sd.eym), for
 // the plans the gradient's recomputation supports (else null).
 MarchFn march_frames_fn(int mb, int ring, bool sparse) {
+  if (mb == 3) return sparse ? yee_tb2m_kernel<3, 0, true, true> : yee_tb2m_kernel<3, 0, false, true>;
   if (mb != 4) return nullptr;
   if (ring == 0 && !sparse) return yee_tb2m_kernel<4, 0, false, true>;
   if (ring == 2) return sparse ? yee_tb2m_kernel<4, 2, true, true> : yee_tb2m_kernel<4, 2, false, true>;

@@ -5,8 +5,9 @@
 // share one operation sequence per update; the model map's row and GEMM forms
 // add in the same order), so only time is at stake:
 //   - one or two steps per launch (FDTD_TB),
-//   - the one-step tile height, or the row-marching tile height, how many
-//     rows it stages ahead through shared memory or prefetches into L1,
+//   - the one-step tile height, or the row-marching kernel's resident CTAs
+//     per SM (4 or 3), tile height, and how many rows it stages ahead
+//     through shared memory or prefetches into L1,
 //   - where the models' maps run on the two-step path (fused in the zone
 //     tiles, or in the zone chain: every model, or the shared maps),
 //   - from how many sharing simulations a map runs as a GEMM, and the GEMM
@@ -26,7 +27,7 @@
 namespace {
 
 struct TuneCfg {
-  int tb_mode, chain, th1, thm, gmin, rpw, ring, pf;
+  int tb_mode, chain, th1, thm, gmin, rpw, ring, pf, mb;
 };
 
 // The one-step tile table and per-simulation tile offsets on the device.
@@ -51,6 +52,7 @@ int apply_cfg(fdtd_ctx* ctx, const TuneCfg& c) {
   ctx->ov_rpw = c.rpw;
   ctx->ov_ring = c.ring;
   ctx->ov_pf = c.pf;
+  ctx->ov_mb = c.mb;
   drop_graphs(ctx);
   plan_tiles(ctx);
   int rc = upload_tiles(ctx);
@@ -196,8 +198,8 @@ bool cache_lookup(const char* path, const std::string& key, TuneCfg* c) {
   while (fgets(line, sizeof(line), f)) {
     char k[64];
     TuneCfg t{};
-    if (sscanf(line, "%63s tb=%d chain=%d th1=%d thm=%d gmin=%d rpw=%d ring=%d pf=%d", k, &t.tb_mode, &t.chain,
-               &t.th1, &t.thm, &t.gmin, &t.rpw, &t.ring, &t.pf) == 9 &&
+    if (sscanf(line, "%63s tb=%d chain=%d th1=%d thm=%d gmin=%d rpw=%d ring=%d pf=%d mb=%d", k, &t.tb_mode,
+               &t.chain, &t.th1, &t.thm, &t.gmin, &t.rpw, &t.ring, &t.pf, &t.mb) == 10 &&
         key == k) {
       *c = t;   // the last entry of a key wins
       found = true;
@@ -210,8 +212,8 @@ bool cache_lookup(const char* path, const std::string& key, TuneCfg* c) {
 void cache_store(const char* path, const std::string& key, const TuneCfg& c, double ms) {
   FILE* f = path ? fopen(path, "a") : nullptr;
   if (!f) return;
-  fprintf(f, "%s tb=%d chain=%d th1=%d thm=%d gmin=%d rpw=%d ring=%d pf=%d ms_per_step=%.6f\n", key.c_str(),
-          c.tb_mode, c.chain, c.th1, c.thm, c.gmin, c.rpw, c.ring, c.pf, ms);
+  fprintf(f, "%s tb=%d chain=%d th1=%d thm=%d gmin=%d rpw=%d ring=%d pf=%d mb=%d ms_per_step=%.6f\n", key.c_str(),
+          c.tb_mode, c.chain, c.th1, c.thm, c.gmin, c.rpw, c.ring, c.pf, c.mb, ms);
   fclose(f);
 }
 
@@ -226,6 +228,7 @@ void fill_report(const fdtd_ctx* ctx, fdtd_tune_report* rep) {
   rep->march_ring = ctx->tb && ctx->tb_march ? ctx->tbm_ring : 0;
   rep->march_prefetch = ctx->tb && ctx->tb_march && ctx->tbm_ring == 0 ? ctx->tbm_pf : 0;
   rep->chained_models = ctx->tb ? ctx->tb_nchain : 0;
+  rep->march_ctas = ctx->tb && ctx->tb_march ? ctx->tbm_mb : 0;
 }
 
 int run_autotune(fdtd_ctx* ctx, const char* cache_path, fdtd_tune_report* rep) {
@@ -252,7 +255,7 @@ int run_autotune(fdtd_ctx* ctx, const char* cache_path, fdtd_tune_report* rep) {
   for (size_t a = 0; a < ctx->insts.size() && !shared; ++a)
     for (size_t b = a + 1; b < ctx->insts.size() && !shared; ++b)
       shared = ctx->insts[a].map == ctx->insts[b].map;
-  TuneCfg best{ctx->tb_mode, ctx->tb_chain_mode, 0, 0, 0, 0, -1, kNoOverride};
+  TuneCfg best{ctx->tb_mode, ctx->tb_chain_mode, 0, 0, 0, 0, -1, kNoOverride, 0};
   rc = apply_cfg(ctx, best);
   if (rc) return rc;
   double t_def = 0;
@@ -300,12 +303,18 @@ int run_autotune(fdtd_ctx* ctx, const char* cache_path, fdtd_tune_report* rep) {
     const int cand1[] = {16, 24, 32, 48, 64, 96, 128};
     const int cand2[] = {8, 16, 24, 32, 48, 64, 96, 128, 192, 256};
     if (two) {
+      {   // 3 resident CTAs per SM (more registers per thread, loads in registers)
+        TuneCfg c = best;
+        c.mb = 3;
+        if ((rc = tryc(c))) return rc;
+      }
       for (int th : cand2) {
         TuneCfg c = best;
         c.thm = th;
         if ((rc = tryc(c))) return rc;
       }
       for (int rg : {0, 2, 3, 4}) {
+        if (best.mb == 3) break;   // that form loads into registers only
         TuneCfg c = best;
         c.ring = rg;
         if ((rc = tryc(c))) return rc;

@@ -266,6 +266,23 @@ def test_zone_chain_on_tile_boundaries_is_bit_identical(monkeypatch, rows):
     _assert_same_bits(res, "one")
 
 
+def test_three_cta_form_is_bit_identical(monkeypatch):
+    """The row-marching kernel built for 3 resident CTAs per SM (FDTD_TB_MB=3,
+    an autotuner candidate: more registers per thread) against the 4-CTA
+    form and one step per launch."""
+    n = 203
+    ws = _boundary_workloads(n)
+    monkeypatch.setenv("FDTD_TB_SMEM", "0")
+    monkeypatch.delenv("FDTD_TB_ROWS", raising=False)
+    res = _run_forms(monkeypatch, ws, n, {
+        "one": {"FDTD_TB": "0"},
+        "four": {"FDTD_TB": "1", "FDTD_TB_RING": "0"},
+        "three": {"FDTD_TB": "1", "FDTD_TB_MB": "3"},
+    })
+    assert res["three"][2] == 2
+    _assert_same_bits(res, "one")
+
+
 @pytest.mark.parametrize("ring", ["2", "3", "4"])
 def test_staged_rows_are_bit_identical(monkeypatch, ring):
     """The row-marching kernel with its loads staged 1-3 rows ahead through

@@ -54,6 +54,30 @@ def test_tuning_keeps_state_and_bits(monkeypatch, case):
             assert np.array_equal(a, b)
 
 
+def test_tuning_after_a_run_leaves_its_probe_buffer(monkeypatch):
+    """The tuner times its candidates with the most recent run's sources (at
+    zero amplitude) and probes, writing the probe samples into a buffer of
+    its own: the run's probe buffer keeps the run's samples."""
+    monkeypatch.delenv("FDTD_TB", raising=False)
+    ws = tt._boundary_workloads(60)
+    ctx, _ = tt.context_for(ws)
+    srcs, probes = [], []
+    for s, w in enumerate(ws):
+        for so in w["sources"]:
+            srcs.append(dict(so, sim=s, wave=torch.tensor(np.asarray(so["wave"][:60], np.float32), device="cuda")))
+        probes += [(s, i, j) for (i, j) in w["probes"]]
+    out = torch.zeros((60, len(probes)), dtype=torch.float32, device="cuda")
+    ctx.fdtd_run(60, srcs, probes, out)
+    torch.cuda.synchronize()
+    before = out.clone()
+    assert before.abs().max() > 0
+    rep = ctx.autotune()
+    torch.cuda.synchronize()
+    assert rep["candidates"] >= 3
+    assert torch.equal(out, before)
+    assert ctx.step_count() == 60
+
+
 def test_cached_choice_is_taken_without_timing(tmp_path, monkeypatch):
     monkeypatch.delenv("FDTD_TB", raising=False)
     path = str(tmp_path / "tune.txt")
