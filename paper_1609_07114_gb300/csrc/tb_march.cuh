@@ -60,17 +60,30 @@ struct MarchIn {        // the loads of row j for sub-step A
 // Sparse materials: whether row j of the warp's 128 columns [c0 - 4, c0 + 124),
 // which lie in at most two of the 128-column strips of the simulation's bits,
 // holds a cell other than the background (or the cell left of a strip does).
-// Rows are asked in ascending order; the word of 32 rows is fetched at the
-// first row asked and at every multiple of 32.  Warp-uniform.
-__device__ __forceinline__ bool march_dense(const SimDev& sd, int j, int c0, bool first, uint32_t& wbits) {
-  if (first || (j & 31) == 0) {
-    wbits = 0xffffffffu;   // rows past the grid are not loaded anyway
-    if ((j >> 5) <= ((sd.ny - 1) >> 5)) {
-      const uint32_t* w = sd.mbits + (size_t)(j >> 5) * sd.nstrip;
-      wbits = w[max(c0 - 4, 0) >> 7] | w[min(c0 + 123, sd.pitch - 1) >> 7];
+// The warp gathers the words of its tile's rows (one per 32 rows, both strips
+// OR-ed) into shared memory once; a row's bit is then one shared load.
+// Warp-uniform.
+constexpr int kMarchBitWords = 4096 / 32 + 3;   // tiles of up to 4096 rows (FDTD_TB_ROWS is clamped to that)
+
+__device__ __forceinline__ void march_gather_bits(uint32_t* sbits, const SimDev& sd, int jA0, int jAe, int c0,
+                                                  int lane) {
+  const int jw0 = jA0 >> 5;
+  const int nw = min((jAe >> 5) - jw0 + 1, kMarchBitWords);
+  const int s0 = max(c0 - 4, 0) >> 7, s1 = min(c0 + 123, sd.pitch - 1) >> 7;
+  for (int k = lane; k < nw; k += 32) {
+    const int wj = jw0 + k;
+    uint32_t b = 0xffffffffu;   // rows past the grid are not loaded anyway
+    if (wj <= ((sd.ny - 1) >> 5)) {
+      const uint32_t* w = sd.mbits + (size_t)wj * sd.nstrip;
+      b = w[s0] | w[s1];
     }
+    sbits[k] = b;
   }
-  return ((wbits >> (j & 31)) & 1u) != 0u;
+  __syncwarp();
+}
+
+__device__ __forceinline__ bool march_dense(const uint32_t* sbits, int j, int jw0) {
+  return ((sbits[(j >> 5) - jw0] >> (j & 31)) & 1u) != 0u;
 }
 
 // Lanes outside the pitched row and rows >= ny read nothing (dead cells);
@@ -277,19 +290,22 @@ yee_tb2m_kernel(const SimDev* __restrict__ sims, const TileWork* __restrict__ ti
   MarchIn cur, nxt;
   // sparse-material bits of the row being loaded; the background material
   const float2* __restrict__ bg = &sims[tw.sim].mbg;
-  uint32_t wbits = 0;
+  __shared__ uint32_t march_bits[kSparse ? 4 : 1][kSparse ? kMarchBitWords : 1];
+  uint32_t* sbits = march_bits[kSparse ? warp : 0];
+  const int jw0 = jA0 >> 5;
+  if constexpr (kSparse) march_gather_bits(sbits, sd, jA0, jAe, c0, lane);
   float4* ring = march_ring + (size_t)warp * (kRing > 0 ? kRing : 1) * 5 * 32;
   int slot = 0;
   unsigned dslots = 0;   // ring: slot k holds a row whose materials were read
   if constexpr (kRing > 0) {
 #pragma unroll
     for (int d = 0; d < kRing - 1; ++d) {
-      const bool dn = !kSparse || march_dense(sd, jA0 + d, c0, d == 0, wbits);
+      const bool dn = !kSparse || march_dense(sbits, jA0 + d, jw0);
       dslots = dn ? dslots | (1u << d) : dslots & ~(1u << d);
       march_issue(ring + d * 5 * 32, ex, ey, hz, mat, jA0 + d, ny, P, cl, inb, lane, dn);
     }
   } else {
-    march_load(cur, ex, ey, hz, mat, jA0, ny, P, cl, inb, !kSparse || march_dense(sd, jA0, c0, true, wbits), bg);
+    march_load(cur, ex, ey, hz, mat, jA0, ny, P, cl, inb, !kSparse || march_dense(sbits, jA0, jw0), bg);
   }
   for (int j = jA0; j <= jAe; ++j) {
     if constexpr (kRing > 0) {
@@ -297,7 +313,7 @@ yee_tb2m_kernel(const SimDev* __restrict__ sims, const TileWork* __restrict__ ti
       ahead -= ahead >= kRing ? kRing : 0;
       // row j + kRing - 1 (past the tile: an empty group, so the count stays uniform)
       if (j + kRing - 1 <= jAe) {
-        const bool dn = !kSparse || march_dense(sd, j + kRing - 1, c0, false, wbits);
+        const bool dn = !kSparse || march_dense(sbits, j + kRing - 1, jw0);
         dslots = dn ? dslots | (1u << ahead) : dslots & ~(1u << ahead);
         march_issue(ring + ahead * 5 * 32, ex, ey, hz, mat, j + kRing - 1, ny, P, cl, inb, lane, dn);
       } else {
@@ -310,7 +326,7 @@ yee_tb2m_kernel(const SimDev* __restrict__ sims, const TileWork* __restrict__ ti
       if (pf > 0 && j + pf <= jAe && j + pf < ny) march_prefetch(ex, ey, hz, mat, j + pf, P, c0, lane);
       if (pf < 0 && j - pf <= jAe && j - pf < ny && inb) march_prefetch_l1(ex, ey, hz, mat, j - pf, P, cl);
       if (j + 1 <= jAe)
-        march_load(nxt, ex, ey, hz, mat, j + 1, ny, P, cl, inb, !kSparse || march_dense(sd, j + 1, c0, false, wbits),
+        march_load(nxt, ex, ey, hz, mat, j + 1, ny, P, cl, inb, !kSparse || march_dense(sbits, j + 1, jw0),
                    bg);
     }
     const float2 m[4] = {make_float2(cur.ma.x, cur.ma.y), make_float2(cur.ma.z, cur.ma.w),
