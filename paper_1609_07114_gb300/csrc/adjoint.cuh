@@ -82,7 +82,7 @@ constexpr int kPreCols = 32, kPreSlices = 8;
 __global__ void __launch_bounds__(kPreCols * kPreSlices)
 adj_pre_kernel(const AdjSimDev* __restrict__ sims, const AdjInstDev* __restrict__ insts,
                const AdjWork* __restrict__ work, int nwork, const AdjRun* __restrict__ ar,
-               int par, int t, long long n) {
+               int par, int gpar, int t, long long n) {
   extern __shared__ float gsh[];   // g_s (n floats), then the slices' partial sums
   pdl_trigger();   // launched with programmatic serialisation: nothing read before pdl_wait
   pdl_wait();
@@ -91,8 +91,8 @@ adj_pre_kernel(const AdjSimDev* __restrict__ sims, const AdjInstDev* __restrict_
     const AdjWork w = work[b];
     const AdjInstDev ai = insts[w.inst];
     const AdjSimDev sd = sims[ai.sim];
-    const float* __restrict__ gsa = par ? ai.gs[1] : ai.gs[0];
-    float* __restrict__ gsb = par ? ai.gs[0] : ai.gs[1];
+    const float* __restrict__ gsa = gpar ? ai.gs[1] : ai.gs[0];
+    float* __restrict__ gsb = gpar ? ai.gs[0] : ai.gs[1];
     const float* __restrict__ gexa = par ? sd.gex[1] : sd.gex[0];
     const float* __restrict__ geya = par ? sd.gey[1] : sd.gey[0];
     float* __restrict__ ghza = par ? sd.ghz[1] : sd.ghz[0];
@@ -655,6 +655,407 @@ adj_cell_kernel(const AdjSimDev* __restrict__ sims, const TileWork* __restrict__
   }
 }
 
+// ---------------------------------------------------------------------------
+// Two reverse steps per pass (row marching, like the forward's
+// yee_tb2m_kernel).  Iteration j runs
+//   A: reverse step t at row j (adj_cell_kernel's arithmetic: g_H' of the
+//      row's cells from g_E of rows j and j + 1, then g_E' of row j), and
+//   B: reverse step t - 1 at row j - 1, from A's rows j - 1 and j,
+// holding A's results in registers, and stores B's row (and the accumulators
+// of both steps) when the tile owns it.  A and B start two rows below the
+// tile (their first row's carried edge terms are not known, which reaches
+// only rows that are not stored).  The additions that precede reverse step
+// t - 1 (the transposed maps' Q^T g_s on the cells beside each model, the
+// probe seeds) are left out here and made afterwards by adj_fix_kernel: the
+// reverse step is linear in (g_E, g_H) for fixed frames, and adding d to
+// g_H of a cell before it adds d to that cell's g_H' and -chx d, +chx d,
+// +chy d, -chy d to the g_E' of its lower, upper, left and right edges, and
+// nothing else (the material terms read g_E and the frames only).  A exports
+// its g_E of the edges those additions read (interface and source edges).
+// A warp computes the 128 columns [c0 - 4, c0 + 124) and stores
+// [c0, c0 + 120): lane l holds c0 - 4 + 4 l .. + 3 and neighbour values come
+// from shuffles (wrong in the outer columns, which nothing stored reads).
+// The row loads are staged one row ahead through shared memory (cp.async).
+
+struct AdjExp {     // an edge whose g_E after reverse step t is exported
+  int j, i, comp, slot;
+};
+
+struct AdjMarchDev {
+  const int2* exp_rng;   // per warp (tile * 4 + warp): [begin, end) into exp, rows ascending
+  const AdjExp* exp;
+  float* expv;           // the exported values, by slot
+};
+
+constexpr int kAdj2Vals = 13;               // float4 per lane and row in the ring
+constexpr int kAdj2Slot4 = kAdj2Vals * 32;  // per warp and ring slot
+constexpr size_t kAdj2Smem = (size_t)2 * 4 * kAdj2Slot4 * sizeof(float4);
+
+// Row j's loads: g_Ex(j + 1), g_Ey(j), g_H(j), mat(j + 1), the Ex frames of
+// edge row j + 1 and the Ey frames of row j at t - 1, t, t + 1, and the
+// accumulators of row j (one commit group).
+__device__ __forceinline__ void adj2_issue(float4* slot, const AdjSimDev& sd, const float* gexa, const float* geya,
+                                           const float* gha, const float* xm, const float* y_m, size_t fs,
+                                           size_t row, int P, int cl, int lane, bool ok) {
+  asm volatile("" ::: "memory");   // after the reads of the slot's previous row
+  const size_t r0 = ok ? row + cl : 0, r1 = ok ? row + P + cl : 0;
+  cp_async16(slot + 0 * 32 + lane, gexa + r1, ok);
+  cp_async16(slot + 1 * 32 + lane, geya + r0, ok);
+  cp_async16(slot + 2 * 32 + lane, gha + r0, ok);
+  cp_async16(slot + 3 * 32 + lane, sd.mat + r1, ok);
+  cp_async16(slot + 4 * 32 + lane, sd.mat + r1 + 2, ok);
+  cp_async16(slot + 5 * 32 + lane, xm + r1, ok);
+  cp_async16(slot + 6 * 32 + lane, xm + fs + r1, ok);
+  cp_async16(slot + 7 * 32 + lane, xm + 2 * fs + r1, ok);
+  cp_async16(slot + 8 * 32 + lane, y_m + r0, ok);
+  cp_async16(slot + 9 * 32 + lane, y_m + fs + r0, ok);
+  cp_async16(slot + 10 * 32 + lane, y_m + 2 * fs + r0, ok);
+  cp_async16(slot + 11 * 32 + lane, sd.geps + r0, ok);
+  cp_async16(slot + 12 * 32 + lane, sd.gsig + r0, ok);
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+
+// One reverse step at row j (adj_cell_kernel's operations in its order):
+// from the row's inputs and the carried terms of the Ex edges of row j
+// (mux, edx, esx, cgx) and g_H'(j - 1) (ghp), the row's g_H' (gn), g_E' of
+// its Ex and Ey edges (vx, vy) and its cells' material terms (qe, qs, taken
+// where live); the carried terms move on to the Ex edges of row j + 1.
+__device__ __forceinline__ void adj2_row(const AdjSimDev& sd, int j, int cl, const float2 (&mj)[4],
+                                         const float2 (&m1)[4], const float4& gx1, const float4& gy, const float4& gh,
+                                         const float4& x0, const float4& x1, const float4& y0, const float4& y1,
+                                         float (&mux)[4], float (&edx)[4], float (&esx)[4], float (&cgx)[4],
+                                         const float (&ghp)[4], float (&gn)[4], float (&vx)[4], float (&vy)[4],
+                                         float (&qe)[4], float (&qs)[4], bool (&live)[4]) {
+  const unsigned FULL = 0xffffffffu;
+  const int nx = sd.nx, ny = sd.ny;
+  float mux1[4], edx1[4], esx1[4], cgx1[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    mux1[q] = edx1[q] = esx1[q] = cgx1[q] = 0.f;
+    if (j + 1 <= ny - 1 && cl + q < nx && mj[q].x >= 0.f && m1[q].x >= 0.f) {
+      float ca, cb;
+      cb_ca(mj[q], m1[q], ca, cb);
+      const float mu = cb * comp(gx1, q);
+      mux1[q] = mu;
+      edx1[q] = mu * (comp(x0, q) - comp(x1, q));
+      esx1[q] = mu * (comp(x0, q) + comp(x1, q));
+      cgx1[q] = ca * comp(gx1, q);
+    }
+  }
+  const float2 mleft = make_float2(__shfl_up_sync(FULL, mj[3].x, 1), __shfl_up_sync(FULL, mj[3].y, 1));
+  float muy[4], edy[4], esy[4], cay[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int i = cl + q;
+    const float2 ml = q == 0 ? mleft : mj[q - 1];
+    muy[q] = edy[q] = esy[q] = cay[q] = 0.f;
+    if (i >= 1 && i <= nx - 1 && ml.x >= 0.f && mj[q].x >= 0.f) {
+      float ca, cb;
+      cb_ca(ml, mj[q], ca, cb);
+      const float mu = cb * comp(gy, q);
+      muy[q] = mu;
+      edy[q] = mu * (comp(y0, q) - comp(y1, q));
+      esy[q] = mu * (comp(y0, q) + comp(y1, q));
+      cay[q] = ca;
+    }
+  }
+  const float muyR = __shfl_down_sync(FULL, muy[0], 1);
+  const float edyR = __shfl_down_sync(FULL, edy[0], 1);
+  const float esyR = __shfl_down_sync(FULL, esy[0], 1);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    live[q] = cl + q < nx && mj[q].x >= 0.f;
+    const float mr = q < 3 ? muy[q + 1] : muyR;
+    gn[q] = live[q] ? comp(gh, q) + sd.rdy * mux[q] - sd.rdy * mux1[q] - sd.rdx * muy[q] + sd.rdx * mr : 0.f;
+    const float er = q < 3 ? edy[q + 1] : edyR;
+    const float sr = q < 3 ? esy[q + 1] : esyR;
+    qe[q] = edx[q] + edx1[q] + edy[q] + er;
+    qs[q] = esx[q] + esx1[q] + esy[q] + sr;
+  }
+  const float gL = __shfl_up_sync(FULL, gn[3], 1);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int i = cl + q;
+    float v = 0.f;
+    if (j >= 1 && i < nx) {
+      v = sd.chx * (ghp[q] - gn[q]);
+      v += cgx[q];
+    }
+    vx[q] = v;
+    float w = 0.f;
+    if (i >= 1 && i < nx) {
+      w = sd.chy * (gn[q] - (q == 0 ? gL : gn[q - 1]));
+      w += cay[q] * comp(gy, q);
+    }
+    vy[q] = w;
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    mux[q] = mux1[q];
+    edx[q] = edx1[q];
+    esx[q] = esx1[q];
+    cgx[q] = cgx1[q];
+  }
+}
+
+__device__ __forceinline__ float adj2_pick(const float (&v)[4], int t) {
+  return t == 0 ? v[0] : (t == 1 ? v[1] : (t == 2 ? v[2] : v[3]));
+}
+
+__global__ void __launch_bounds__(128, 3)
+adj_march_kernel(const AdjSimDev* __restrict__ sims, const TileWork* __restrict__ tiles,
+                 const AdjMarchDev* __restrict__ am, int par, int t) {
+  extern __shared__ float4 adj2_ring[];
+  pdl_trigger();   // launched with programmatic serialisation: nothing read before pdl_wait
+  pdl_wait();
+  const TileWork tw = tiles[blockIdx.x];
+  const AdjSimDev sd = sims[tw.sim];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int c0 = tw.x0 + kMarchOut * warp;
+  const int nx = sd.nx, ny = sd.ny, P = sd.pitch;
+  if (c0 >= nx) return;
+  const float* __restrict__ gexa = par ? sd.gex[1] : sd.gex[0];
+  const float* __restrict__ geya = par ? sd.gey[1] : sd.gey[0];
+  const float* __restrict__ gha = par ? sd.ghz[1] : sd.ghz[0];
+  float* __restrict__ gexb = par ? sd.gex[0] : sd.gex[1];
+  float* __restrict__ geyb = par ? sd.gey[0] : sd.gey[1];
+  float* __restrict__ ghb = par ? sd.ghz[0] : sd.ghz[1];
+  const size_t fs = (size_t)sd.fstride;
+  const float* xm = sd.exF + (size_t)(t - 1) * fs;   // frames t - 1, t, t + 1 at xm, xm + fs, xm + 2 fs
+  const float* y_m = sd.eyF + (size_t)(t - 1) * fs;
+  const int cl = c0 - 4 + 4 * lane;
+  const bool inb = cl >= 0 && cl < P;
+  const bool owner = lane >= 1 && lane <= 30 && cl < nx;
+  const int j0 = tw.y0, j1 = tw.y1;
+  const int jA0 = j0 >= 2 ? j0 - 2 : 0;       // A's and B's first row
+  const int jAe = j1 < ny ? j1 : ny - 1;      // A's last row (row ny: the boundary's Ex edges, zero)
+  const int wi = blockIdx.x * 4 + warp;
+  const int2 er = am->exp_rng[wi];
+  int ke = er.x;
+  AdjExp ea = ke < er.y ? am->exp[ke] : AdjExp{kMarchNone, 0, 0, 0};
+  const float2 dead = make_float2(-1.f, 0.f);
+  // A's carried state at its first row: mat(jA0), the Ex edges of row jA0
+  float2 mj[4];
+  float muxA[4], edxA[4], esxA[4], cgxA[4], ghpA[4];
+  {
+    const size_t row = (size_t)jA0 * P;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      mj[q] = inb ? sd.mat[row + cl + q] : dead;
+      muxA[q] = edxA[q] = esxA[q] = cgxA[q] = ghpA[q] = 0.f;
+      if (inb && jA0 >= 1 && cl + q < nx) {
+        const float2 mo = sd.mat[row - P + cl + q];
+        if (mo.x >= 0.f && mj[q].x >= 0.f) {
+          float ca, cb;
+          cb_ca(mo, mj[q], ca, cb);
+          muxA[q] = cb * gexa[row + cl + q];
+        }
+      }
+    }
+  }
+  // B's carried state (its first row's Ex-edge terms start at zero) and what
+  // it takes from A's previous row: mat, g_Ey', the frames, the accumulators
+  float2 mP[4];
+  float muxB[4], edxB[4], esxB[4], cgxB[4], ghpB[4], vyP[4], aeP[4], asP[4];
+  float4 xbm = make_float4(0.f, 0.f, 0.f, 0.f), xb0 = xbm, ybm = xbm, yb0 = xbm;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    mP[q] = dead;
+    muxB[q] = edxB[q] = esxB[q] = cgxB[q] = ghpB[q] = vyP[q] = aeP[q] = asP[q] = 0.f;
+  }
+  float4* ring = adj2_ring + (size_t)warp * 2 * kAdj2Slot4;
+  adj2_issue(ring, sd, gexa, geya, gha, xm, y_m, fs, (size_t)jA0 * P, P, cl, lane, inb);
+  int slot = 0;
+  for (int j = jA0; j <= j1; ++j) {
+    if (j + 1 <= jAe)
+      adj2_issue(ring + (slot ^ 1) * kAdj2Slot4, sd, gexa, geya, gha, xm, y_m, fs, (size_t)(j + 1) * P, P, cl, lane,
+                 inb);
+    else
+      asm volatile("cp.async.commit_group;\n" ::: "memory");
+    cp_async_wait_n<1>();
+    const float4* cs = ring + slot * kAdj2Slot4;
+    slot ^= 1;
+    // ---- A: reverse step t at row j
+    float gnA[4], vxA[4], vyA[4], aeA[4], asA[4];
+    float2 m1[4];
+    float4 xfm = make_float4(0.f, 0.f, 0.f, 0.f), xf0 = xfm, yfm = xfm, yf0 = xfm;
+    if (j <= jAe) {
+      const float4 gx1 = cs[0 * 32 + lane], gy = cs[1 * 32 + lane], gh = cs[2 * 32 + lane];
+      const float4 ma = cs[3 * 32 + lane], mb = cs[4 * 32 + lane];
+      m1[0] = make_float2(ma.x, ma.y), m1[1] = make_float2(ma.z, ma.w);
+      m1[2] = make_float2(mb.x, mb.y), m1[3] = make_float2(mb.z, mb.w);
+      if (!inb) m1[0] = m1[1] = m1[2] = m1[3] = dead;
+      xfm = cs[5 * 32 + lane], xf0 = cs[6 * 32 + lane];
+      const float4 xfp = cs[7 * 32 + lane];
+      yfm = cs[8 * 32 + lane], yf0 = cs[9 * 32 + lane];
+      const float4 yfp = cs[10 * 32 + lane];
+      const float4 ae4 = cs[11 * 32 + lane], as4 = cs[12 * 32 + lane];
+      float qe[4], qs[4];
+      bool live[4];
+      adj2_row(sd, j, cl, mj, m1, gx1, gy, gh, xf0, xfp, yf0, yfp, muxA, edxA, esxA, cgxA, ghpA, gnA, vxA, vyA, qe,
+               qs, live);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        aeA[q] = comp(ae4, q);
+        asA[q] = comp(as4, q);
+        if (live[q]) {
+          aeA[q] += 0.5f * sd.inv_dt * qe[q];
+          asA[q] -= 0.25f * qs[q];
+        }
+      }
+      // the exported edges of this row (owned rows only, in the lists)
+      while (ea.j == j) {
+        const int q = ea.i - cl;
+        if (owner && q >= 0 && q < 4) am->expv[ea.slot] = adj2_pick(ea.comp == 0 ? vxA : vyA, q);
+        ++ke;
+        ea = ke < er.y ? am->exp[ke] : AdjExp{kMarchNone, 0, 0, 0};
+      }
+    } else {   // j = ny: only B's last row remains
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        gnA[q] = vxA[q] = vyA[q] = aeA[q] = asA[q] = 0.f;
+        m1[q] = dead;
+      }
+    }
+    // ---- B: reverse step t - 1 at row r = j - 1
+    const int r = j - 1;
+    if (r >= jA0) {
+      const float4 gx1 = make_float4(vxA[0], vxA[1], vxA[2], vxA[3]);
+      const float4 gy = make_float4(vyP[0], vyP[1], vyP[2], vyP[3]);
+      const float4 gh = make_float4(ghpA[0], ghpA[1], ghpA[2], ghpA[3]);
+      float gnB[4], vxB[4], vyB[4], qe[4], qs[4];
+      bool live[4];
+      adj2_row(sd, r, cl, mP, mj, gx1, gy, gh, xbm, xb0, ybm, yb0, muxB, edxB, esxB, cgxB, ghpB, gnB, vxB, vyB, qe,
+               qs, live);
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (live[q]) {
+          aeP[q] += 0.5f * sd.inv_dt * qe[q];
+          asP[q] -= 0.25f * qs[q];
+        }
+      if (owner && r >= j0) {
+        const size_t off = (size_t)r * P + cl;
+        st4(gexb + off, make_float4(vxB[0], vxB[1], vxB[2], vxB[3]));
+        st4(geyb + off, make_float4(vyB[0], vyB[1], vyB[2], vyB[3]));
+        st4(ghb + off, make_float4(gnB[0], gnB[1], gnB[2], gnB[3]));
+        st4(sd.geps + off, make_float4(aeP[0], aeP[1], aeP[2], aeP[3]));
+        st4(sd.gsig + off, make_float4(asP[0], asP[1], asP[2], asP[3]));
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) ghpB[q] = gnB[q];
+    }
+    // ---- carry to row j + 1
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      mP[q] = mj[q];
+      mj[q] = m1[q];
+      ghpA[q] = gnA[q];
+      vyP[q] = vyA[q];
+      aeP[q] = aeA[q];
+      asP[q] = asA[q];
+    }
+    xbm = xfm, xb0 = xf0, ybm = yfm, yb0 = yf0;
+  }
+}
+
+// After adj_march_kernel: the additions that precede reverse step n (the
+// second step of the pass, segment index t): the transposed maps with the
+// exported g_E of the interface edges (adj_pre_kernel's model part, into the
+// other g_s buffer; its Q^T g_s on the cells beside the model), the probe
+// seeds and the source gradients; each addition d to g_H of a live cell is
+// applied to the pass's output as the cell pass would have carried it (the
+// cell's g_H' and its four edges' g_E').
+__device__ __forceinline__ void adj_fix_cell(const AdjSimDev& sd, float* gexb, float* geyb, float* ghb, int cell,
+                                             float d) {
+  const int P = sd.pitch, i = cell % P, j = cell / P;
+  if (sd.mat[cell].x < 0.f) return;   // the cell pass leaves covered cells at zero
+  atomicAdd(ghb + cell, d);
+  if (j >= 1) atomicAdd(gexb + cell, -(sd.chx * d));
+  if (j + 1 <= sd.ny - 1) atomicAdd(gexb + cell + P, sd.chx * d);
+  if (i >= 1) atomicAdd(geyb + cell, sd.chy * d);
+  if (i + 1 <= sd.nx - 1) atomicAdd(geyb + cell + 1, -(sd.chy * d));
+}
+
+__global__ void __launch_bounds__(kPreCols * kPreSlices)
+adj_fix_kernel(const AdjSimDev* __restrict__ sims, const AdjInstDev* __restrict__ insts,
+               const AdjWork* __restrict__ work, int nwork, const AdjRun* __restrict__ ar,
+               const float* __restrict__ expv, const int* __restrict__ inst_exp, int src_exp, int bpar, int gpar,
+               int t, long long n) {
+  extern __shared__ float gsh[];   // g_s (n floats), then the slices' partial sums
+  pdl_trigger();
+  pdl_wait();
+  const int b = blockIdx.x;
+  if (b < nwork) {
+    const AdjWork w = work[b];
+    const AdjInstDev ai = insts[w.inst];
+    const AdjSimDev sd = sims[ai.sim];
+    const float* __restrict__ gsa = gpar ? ai.gs[1] : ai.gs[0];
+    float* __restrict__ gsb = gpar ? ai.gs[0] : ai.gs[1];
+    float* __restrict__ gexb = bpar ? sd.gex[1] : sd.gex[0];
+    float* __restrict__ geyb = bpar ? sd.gey[1] : sd.gey[0];
+    float* __restrict__ ghb = bpar ? sd.ghz[1] : sd.ghz[0];
+    const float* __restrict__ ev = expv + inst_exp[w.inst];
+    for (int k = threadIdx.x; k < ai.n; k += blockDim.x) {
+      float g = gsa[k];
+      if (k < ai.ny) g += ev[k];
+      gsh[k] = g;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, sl = threadIdx.x >> 5;
+    const int c = w.c0 + lane;
+    const int rps = (ai.n + kPreSlices - 1) / kPreSlices;
+    const int r0 = sl * rps, r1 = min(ai.n, r0 + rps);
+    float acc = 0.f;
+    if (c < w.c1) {
+      const float* __restrict__ Mc = ai.M + c;
+      for (int rb = r0; rb < r1; rb += 16) {
+        float mv[16];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) mv[u] = rb + u < r1 ? Mc[(size_t)(rb + u) * ai.ld] : 0.f;
+#pragma unroll
+        for (int u = 0; u < 16; ++u)
+          if (rb + u < r1) acc = fmaf(mv[u], gsh[rb + u], acc);
+      }
+    }
+    float* part = gsh + ai.n;
+    part[sl * kPreCols + lane] = acc;
+    __syncthreads();
+    if (sl == 0 && c < w.c1) {
+      float tot = part[lane];
+#pragma unroll
+      for (int q = 1; q < kPreSlices; ++q) tot += part[q * kPreCols + lane];
+      if (c < ai.n) {
+        gsb[c] = tot;
+      } else {
+        const int k = c - ai.n;
+        adj_fix_cell(sd, gexb, geyb, ghb, ai.h_cell[k], tot);
+        const float y0 = ai.sF[(size_t)t * ai.ld + k];
+        const float y1 = ai.sF[(size_t)(t + 1) * ai.ld + k];
+        ai.geps_b[k] += (double)ai.lh_dt[k] * tot * ((double)y0 - y1);
+        ai.gsig_b[k] -= (double)ai.lh_2[k] * tot * ((double)y0 + y1);
+      }
+    }
+    return;
+  }
+  const int idx = (b - nwork) * blockDim.x + threadIdx.x;
+  if (idx < ar->nprobe) {
+    const AdjSimDev* sd = sims + ar->probe_sim[idx];
+    const size_t k = (size_t)n * ar->nprobe + idx;
+    adj_fix_cell(*sd, bpar ? sd->gex[1] : sd->gex[0], bpar ? sd->gey[1] : sd->gey[0], bpar ? sd->ghz[1] : sd->ghz[0],
+                 ar->probe_cell[idx], ar->seed ? ar->seed[k] : 2.f * ar->probe_out[k]);
+  } else if (idx - ar->nprobe < ar->nedges) {
+    const int e = idx - ar->nprobe;
+    const SrcEdge se = ar->src_edges[e];
+    const AdjSimDev* sd = sims + se.sim;
+    const size_t off = (size_t)se.j * sd->pitch + se.i;
+    const float2 m2 = sd->mat[off];
+    const float2 m1 = se.comp == 0 ? sd->mat[off - sd->pitch] : sd->mat[off - 1];
+    float ca, cb;
+    cb_ca(m1, m2, ca, cb);
+    atomicAdd(ar->dsrc + (size_t)se.src * ar->nsteps + n, -cb * expv[src_exp + e]);
+  }
+}
+
 // Moves a segment's FP32 accumulators into the FP64 totals and clears them.
 __global__ void adj_flush_kernel(float* __restrict__ g32, double* __restrict__ g64, size_t n) {
   for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
@@ -981,7 +1382,99 @@ int run_grad(fdtd_ctx* ctx, long long nsteps, const fdtd_source* src, int nsrc,
   // one fused cell pass per reverse step (FDTD_ADJ_FUSED=0: the two-pass form)
   const char* fe = getenv("FDTD_ADJ_FUSED");
   const bool fused = !(fe && atoi(fe) == 0);
-  int par = 0;
+  // Two reverse steps per launch (adj_march_kernel + adj_fix_kernel;
+  // FDTD_ADJ_TB2=0: one step per launch): kMarchCols x th2 tiles (th2 of
+  // 8..64 rows filling whole waves of resident CTAs), per warp the edges
+  // whose g_E after the first step it exports (the models' interface edges,
+  // the source edges).
+  const char* et2 = getenv("FDTD_ADJ_TB2");
+  const bool tb2 = fused && !(et2 && atoi(et2) == 0);
+  TileWork* a2tiles_d = nullptr;
+  unsigned na2 = 0;
+  AdjMarchDev* am_d = nullptr;
+  float* expv_d = nullptr;
+  int* iexp_d = nullptr;
+  int src_exp = 0;
+  if (tb2) {
+    CK(cudaFuncSetAttribute(adj_march_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kAdj2Smem));
+    if (pre_smem > 48 * 1024)
+      CK(cudaFuncSetAttribute(adj_fix_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pre_smem));
+    int dev = 0, nsm = 1, occ = 1;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, adj_march_kernel, 128, kAdj2Smem));
+    const long long slots = (long long)nsm * std::max(occ, 1);
+    auto tiles_for = [&](int th) {
+      long long c = 0;
+      for (const SimHost& sh : ctx->sims)
+        c += (long long)((sh.nx + kMarchCols - 1) / kMarchCols) * ((sh.ny + th - 1) / th);
+      return c;
+    };
+    int th2 = 8;
+    long long best = -1;
+    for (int h = 8; h <= 64; ++h) {
+      const long long cost = ((tiles_for(h) + slots - 1) / slots) * (h + 3);
+      if (best < 0 || cost < best) best = cost, th2 = h;
+    }
+    if (const char* er = getenv("FDTD_ADJ_TB2_ROWS")) th2 = std::min(4096, std::max(4, atoi(er)));
+    std::vector<TileWork> t2;
+    std::vector<int> tbase(nsim);
+    for (int s = 0; s < nsim; ++s) {
+      const SimHost& sh = ctx->sims[s];
+      tbase[s] = (int)t2.size();
+      for (int y0 = 0; y0 < sh.ny; y0 += th2)
+        for (int x0 = 0; x0 < sh.nx; x0 += kMarchCols) t2.push_back({s, x0, y0, std::min(y0 + th2, sh.ny)});
+    }
+    na2 = (unsigned)t2.size();
+    std::vector<std::vector<AdjExp>> lists(4 * t2.size());
+    auto add = [&](int sim, int comp, int i, int j, int slot) {
+      const SimHost& sh = ctx->sims[sim];
+      const int ncx = (sh.nx + kMarchCols - 1) / kMarchCols;
+      const int tile = tbase[sim] + (j / th2) * ncx + i / kMarchCols;
+      lists[4 * (size_t)tile + (i % kMarchCols) / kMarchOut].push_back({j, i, comp, slot});
+    };
+    std::vector<int> iexp(std::max(ninst, 1), 0);
+    int nexp = 0;
+    for (int q = 0; q < ninst; ++q) {
+      const Instance& in = ctx->insts[q];
+      const int P = ctx->sims[in.sim].pitch;
+      iexp[q] = nexp;
+      for (int e = 0; e < in.ny; ++e) {
+        const int code = in.y_edge[e], off = code & 0x3fffffff;
+        add(in.sim, code >> 30, off % P, off / P, nexp + e);
+      }
+      nexp += in.ny;
+    }
+    src_exp = nexp;
+    if (nedges > 0) {
+      std::vector<SrcEdge> se(nedges);
+      CK(cudaMemcpy(se.data(), ctx->src_edges.p, sizeof(SrcEdge) * nedges, cudaMemcpyDeviceToHost));
+      for (int e = 0; e < nedges; ++e) add(se[e].sim, se[e].comp, se[e].i, se[e].j, nexp + e);
+      nexp += nedges;
+    }
+    std::vector<int2> rng(lists.size());
+    std::vector<AdjExp> flat;
+    for (size_t w = 0; w < lists.size(); ++w) {
+      std::stable_sort(lists[w].begin(), lists[w].end(), [](const AdjExp& a, const AdjExp& b) { return a.j < b.j; });
+      rng[w] = make_int2((int)flat.size(), (int)(flat.size() + lists[w].size()));
+      flat.insert(flat.end(), lists[w].begin(), lists[w].end());
+    }
+    int2* rng_d = nullptr;
+    AdjExp* exp_d = nullptr;
+    CK(A.alloc(&a2tiles_d, t2.size()));
+    CK(A.alloc(&rng_d, rng.size()));
+    CK(A.alloc(&exp_d, std::max<size_t>(flat.size(), 1)));
+    CK(A.alloc(&expv_d, std::max(nexp, 1)));
+    CK(A.alloc(&iexp_d, iexp.size()));
+    CK(A.alloc(&am_d, 1));
+    CK(cudaMemcpy(a2tiles_d, t2.data(), sizeof(TileWork) * t2.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(rng_d, rng.data(), sizeof(int2) * rng.size(), cudaMemcpyHostToDevice));
+    if (!flat.empty()) CK(cudaMemcpy(exp_d, flat.data(), sizeof(AdjExp) * flat.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(iexp_d, iexp.data(), sizeof(int) * iexp.size(), cudaMemcpyHostToDevice));
+    const AdjMarchDev amh{rng_d, exp_d, expv_d};
+    CK(cudaMemcpy(am_d, &amh, sizeof(AdjMarchDev), cudaMemcpyHostToDevice));
+  }
+  int par = 0, gpar = 0;   // the adjoint fields' and the model adjoints' current buffers
   for (long long k = S - 1; k >= 0; --k) {
     const int L = (int)std::min<long long>(C, nsteps - k * C);
     for (int s = 0; s < nsim; ++s) {
@@ -1031,7 +1524,20 @@ int run_grad(fdtd_ctx* ctx, long long nsteps, const fdtd_source* src, int nsrc,
       const int nb = (int)aw.size() + npre_extra;
       if (nb > 0)
         launch_k(adj_pre_kernel, (unsigned)nb, kPreCols * kPreSlices, pre_smem, st, ctx->pdl, (const AdjSimDev*)asd_d,
-                 (const AdjInstDev*)aid_d, (const AdjWork*)aw_d, (int)aw.size(), (const AdjRun*)ar_d, par, t, n);
+                 (const AdjInstDev*)aid_d, (const AdjWork*)aw_d, (int)aw.size(), (const AdjRun*)ar_d, par, gpar, t, n);
+      if (tb2 && t >= 1) {   // reverse steps t and t - 1, then the additions before t - 1
+        launch_k(adj_march_kernel, na2, 128, kAdj2Smem, st, ctx->pdl, (const AdjSimDev*)asd_d,
+                 (const TileWork*)a2tiles_d, (const AdjMarchDev*)am_d, par, t);
+        if (nb > 0)
+          launch_k(adj_fix_kernel, (unsigned)nb, kPreCols * kPreSlices, pre_smem, st, ctx->pdl,
+                   (const AdjSimDev*)asd_d, (const AdjInstDev*)aid_d, (const AdjWork*)aw_d, (int)aw.size(),
+                   (const AdjRun*)ar_d, (const float*)expv_d, (const int*)iexp_d, src_exp, 1 - par, 1 - gpar, t - 1,
+                   n - 1);
+        par ^= 1;
+        --t;
+        continue;
+      }
+      gpar ^= 1;
       if (fused) {
         launch_k(cell_fn, natiles, 128, cell_smem, st, ctx->pdl, (const AdjSimDev*)asd_d, (const TileWork*)atiles_d,
                  par, t);

@@ -252,8 +252,10 @@ def test_two_step_recomputation_is_bit_identical(monkeypatch, nx, ny, ckpt):
     """The recomputation in pairs of steps (the march and the zone chain also
     writing the E frame between the sub-steps; odd segments end with one
     single step) against one step per launch (FDTD_ADJ_RECOMP2=0): the same
-    frames, so the same gradient bits."""
+    frames, so the same gradient bits (one reverse step per launch, whose
+    additions are in a fixed order)."""
     monkeypatch.delenv("FDTD_TB", raising=False)
+    monkeypatch.setenv("FDTD_ADJ_TB2", "0")
     w = _off_ring_case(nx, ny)
     res = {}
     for r in ("0", "1"):
@@ -271,7 +273,9 @@ def test_two_step_recomputation_is_bit_identical(monkeypatch, nx, ny, ckpt):
 def test_staged_reverse_rows_are_bit_identical(monkeypatch, nx, ny):
     """The fused reverse cell pass with its row loads staged one or two rows
     ahead through shared memory (FDTD_ADJ_RING=2 / 3) against its register
-    form: the same arithmetic, so the same bits."""
+    form: the same arithmetic, so the same bits (one reverse step per
+    launch)."""
+    monkeypatch.setenv("FDTD_ADJ_TB2", "0")
     w = _off_ring_case(nx, ny)
     res = {}
     for r in ("0", "2", "3"):
@@ -283,6 +287,26 @@ def test_staged_reverse_rows_are_bit_identical(monkeypatch, nx, ny):
         for k in (1, 2):
             np.testing.assert_array_equal(res[r][k][0], res["0"][k][0])
         np.testing.assert_array_equal(res[r][3], res["0"][3])
+
+
+@pytest.mark.parametrize("nx,ny,ckpt", [(100, 80, 50), (100, 80, 7), (300, 230, 25), (700, 300, 40)])
+def test_two_step_reverse_agrees_with_one_step(monkeypatch, nx, ny, ckpt):
+    """Two reverse steps per launch (the additions before the second step,
+    from the models' transposed maps and the probe seeds, made afterwards as
+    local corrections) against one reverse step per launch: the same
+    gradients up to FP32 rounding at the corrected cells (several strips,
+    tiles and halo columns; odd segments end with one single step; probes on
+    the cells beside the models and by the source)."""
+    w = grad_case(seed=65, nx=nx, ny=ny, nsteps=120)
+    res = {}
+    for r in ("0", "1"):
+        monkeypatch.setenv("FDTD_ADJ_TB2", r)
+        res[r] = gpu_grad([w], 120, ckpt)
+    assert np.abs(res["0"][1][0]).max() > 0
+    assert res["1"][0] == res["0"][0]
+    for k in (1, 2):
+        assert rel_l2(res["1"][k][0], res["0"][k][0]) < 1e-5
+    assert rel_l2(res["1"][3], res["0"][3]) < 1e-5
 
 
 def test_multi_strip_gradients_match_oracle():
