@@ -675,6 +675,9 @@ adj_cell_kernel(const AdjSimDev* __restrict__ sims, const TileWork* __restrict__
 // A warp computes the 128 columns [c0 - 4, c0 + 124) and stores
 // [c0, c0 + 120): lane l holds c0 - 4 + 4 l .. + 3 and neighbour values come
 // from shuffles (wrong in the outer columns, which nothing stored reads).
+// A CTA has W = 3 or 4 warps (blockDim.x / 32) and covers W x 120 columns:
+// W is chosen per run so that the grids' last column blocks leave the
+// fewest warps idle (1024 columns: three CTAs of three warps, no idle warp).
 // The row loads are staged one row ahead through shared memory (cp.async).
 
 struct AdjExp {     // an edge whose g_E after reverse step t is exported
@@ -689,7 +692,7 @@ struct AdjMarchDev {
 
 constexpr int kAdj2Vals = 13;               // float4 per lane and row in the ring
 constexpr int kAdj2Slot4 = kAdj2Vals * 32;  // per warp and ring slot
-constexpr size_t kAdj2Smem = (size_t)2 * 4 * kAdj2Slot4 * sizeof(float4);
+constexpr size_t kAdj2SmemPerWarp = (size_t)2 * kAdj2Slot4 * sizeof(float4);
 
 // Row j's loads: g_Ex(j + 1), g_Ey(j), g_H(j), mat(j + 1), the Ex frames of
 // edge row j + 1 and the Ey frames of row j at t - 1, t, t + 1, and the
@@ -814,6 +817,7 @@ adj_march_kernel(const AdjSimDev* __restrict__ sims, const TileWork* __restrict_
   const int c0 = tw.x0 + kMarchOut * warp;
   const int nx = sd.nx, ny = sd.ny, P = sd.pitch;
   if (c0 >= nx) return;
+  const int wi = blockIdx.x * (blockDim.x >> 5) + warp;
   const float* __restrict__ gexa = par ? sd.gex[1] : sd.gex[0];
   const float* __restrict__ geya = par ? sd.gey[1] : sd.gey[0];
   const float* __restrict__ gha = par ? sd.ghz[1] : sd.ghz[0];
@@ -829,7 +833,6 @@ adj_march_kernel(const AdjSimDev* __restrict__ sims, const TileWork* __restrict_
   const int j0 = tw.y0, j1 = tw.y1;
   const int jA0 = j0 >= 2 ? j0 - 2 : 0;       // A's and B's first row
   const int jAe = j1 < ny ? j1 : ny - 1;      // A's last row (row ny: the boundary's Ex edges, zero)
-  const int wi = blockIdx.x * 4 + warp;
   const int2 er = am->exp_rng[wi];
   int ke = er.x;
   AdjExp ea = ke < er.y ? am->exp[ke] : AdjExp{kMarchNone, 0, 0, 0};
@@ -1395,19 +1398,31 @@ int run_grad(fdtd_ctx* ctx, long long nsteps, const fdtd_source* src, int nsrc,
   float* expv_d = nullptr;
   int* iexp_d = nullptr;
   int src_exp = 0;
+  int aw2 = 4;                    // warps per CTA of adj_march_kernel
+  size_t a2smem = 0;
   if (tb2) {
-    CK(cudaFuncSetAttribute(adj_march_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kAdj2Smem));
+    {   // 3 or 4 warps per CTA: the fewer idle warps in the grids' last column blocks
+      long long idle3 = 0, idle4 = 0;
+      for (const SimHost& sh : ctx->sims) {
+        const long long nwc = (sh.nx + kMarchOut - 1) / kMarchOut, nr = sh.ny;
+        idle3 += ((nwc + 2) / 3 * 3 - nwc) * nr;
+        idle4 += ((nwc + 3) / 4 * 4 - nwc) * nr;
+      }
+      aw2 = idle3 < idle4 ? 3 : 4;
+    }
+    a2smem = kAdj2SmemPerWarp * aw2;
+    CK(cudaFuncSetAttribute(adj_march_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)a2smem));
     if (pre_smem > 48 * 1024)
       CK(cudaFuncSetAttribute(adj_fix_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pre_smem));
     int dev = 0, nsm = 1, occ = 1;
     CK(cudaGetDevice(&dev));
     CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, adj_march_kernel, 128, kAdj2Smem));
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, adj_march_kernel, 32 * aw2, a2smem));
     const long long slots = (long long)nsm * std::max(occ, 1);
+    const int cw = kMarchOut * aw2;   // columns per CTA
     auto tiles_for = [&](int th) {
       long long c = 0;
-      for (const SimHost& sh : ctx->sims)
-        c += (long long)((sh.nx + kMarchCols - 1) / kMarchCols) * ((sh.ny + th - 1) / th);
+      for (const SimHost& sh : ctx->sims) c += (long long)((sh.nx + cw - 1) / cw) * ((sh.ny + th - 1) / th);
       return c;
     };
     int th2 = 8;
@@ -1423,15 +1438,15 @@ int run_grad(fdtd_ctx* ctx, long long nsteps, const fdtd_source* src, int nsrc,
       const SimHost& sh = ctx->sims[s];
       tbase[s] = (int)t2.size();
       for (int y0 = 0; y0 < sh.ny; y0 += th2)
-        for (int x0 = 0; x0 < sh.nx; x0 += kMarchCols) t2.push_back({s, x0, y0, std::min(y0 + th2, sh.ny)});
+        for (int x0 = 0; x0 < sh.nx; x0 += cw) t2.push_back({s, x0, y0, std::min(y0 + th2, sh.ny)});
     }
     na2 = (unsigned)t2.size();
-    std::vector<std::vector<AdjExp>> lists(4 * t2.size());
+    std::vector<std::vector<AdjExp>> lists((size_t)aw2 * t2.size());
     auto add = [&](int sim, int comp, int i, int j, int slot) {
       const SimHost& sh = ctx->sims[sim];
-      const int ncx = (sh.nx + kMarchCols - 1) / kMarchCols;
-      const int tile = tbase[sim] + (j / th2) * ncx + i / kMarchCols;
-      lists[4 * (size_t)tile + (i % kMarchCols) / kMarchOut].push_back({j, i, comp, slot});
+      const int ncx = (sh.nx + cw - 1) / cw;
+      const int tile = tbase[sim] + (j / th2) * ncx + i / cw;
+      lists[(size_t)aw2 * tile + (i % cw) / kMarchOut].push_back({j, i, comp, slot});
     };
     std::vector<int> iexp(std::max(ninst, 1), 0);
     int nexp = 0;
@@ -1474,6 +1489,11 @@ int run_grad(fdtd_ctx* ctx, long long nsteps, const fdtd_source* src, int nsrc,
     const AdjMarchDev amh{rng_d, exp_d, expv_d};
     CK(cudaMemcpy(am_d, &amh, sizeof(AdjMarchDev), cudaMemcpyHostToDevice));
   }
+  // the reverse sweep's kernels launch in plain stream order (measured: 2.82
+  // against 2.85 s per gradient at 16 x 1024^2 with programmatic dependent
+  // launch; FDTD_ADJ_PDL=1 turns it on)
+  const char* ep2 = getenv("FDTD_ADJ_PDL");
+  const bool rpdl = ctx->pdl && ep2 && atoi(ep2) == 1;
   int par = 0, gpar = 0;   // the adjoint fields' and the model adjoints' current buffers
   for (long long k = S - 1; k >= 0; --k) {
     const int L = (int)std::min<long long>(C, nsteps - k * C);
@@ -1523,13 +1543,13 @@ int run_grad(fdtd_ctx* ctx, long long nsteps, const fdtd_source* src, int nsrc,
       const long long n = k * C + t;
       const int nb = (int)aw.size() + npre_extra;
       if (nb > 0)
-        launch_k(adj_pre_kernel, (unsigned)nb, kPreCols * kPreSlices, pre_smem, st, ctx->pdl, (const AdjSimDev*)asd_d,
+        launch_k(adj_pre_kernel, (unsigned)nb, kPreCols * kPreSlices, pre_smem, st, rpdl, (const AdjSimDev*)asd_d,
                  (const AdjInstDev*)aid_d, (const AdjWork*)aw_d, (int)aw.size(), (const AdjRun*)ar_d, par, gpar, t, n);
       if (tb2 && t >= 1) {   // reverse steps t and t - 1, then the additions before t - 1
-        launch_k(adj_march_kernel, na2, 128, kAdj2Smem, st, ctx->pdl, (const AdjSimDev*)asd_d,
+        launch_k(adj_march_kernel, na2, 32 * aw2, a2smem, st, rpdl, (const AdjSimDev*)asd_d,
                  (const TileWork*)a2tiles_d, (const AdjMarchDev*)am_d, par, t);
         if (nb > 0)
-          launch_k(adj_fix_kernel, (unsigned)nb, kPreCols * kPreSlices, pre_smem, st, ctx->pdl,
+          launch_k(adj_fix_kernel, (unsigned)nb, kPreCols * kPreSlices, pre_smem, st, rpdl,
                    (const AdjSimDev*)asd_d, (const AdjInstDev*)aid_d, (const AdjWork*)aw_d, (int)aw.size(),
                    (const AdjRun*)ar_d, (const float*)expv_d, (const int*)iexp_d, src_exp, 1 - par, 1 - gpar, t - 1,
                    n - 1);
@@ -1539,7 +1559,7 @@ int run_grad(fdtd_ctx* ctx, long long nsteps, const fdtd_source* src, int nsrc,
       }
       gpar ^= 1;
       if (fused) {
-        launch_k(cell_fn, natiles, 128, cell_smem, st, ctx->pdl, (const AdjSimDev*)asd_d, (const TileWork*)atiles_d,
+        launch_k(cell_fn, natiles, 128, cell_smem, st, rpdl, (const AdjSimDev*)asd_d, (const TileWork*)atiles_d,
                  par, t);
       } else {
         adj_h_kernel<<<ntiles, 256, 0, st>>>(asd_d, ctx->tiles_d, par, t);
