@@ -1281,7 +1281,7 @@ int run_grad(fdtd_ctx* ctx, long long nsteps, const fdtd_source* src, int nsrc,
       !(er2 && atoi(er2) == 0))
     mframes = march_frames_fn(ctx->tbm_mb, ctx->tbm_ring, ctx->tbm_sparse);
   if (mframes && ctx->tbm_ring > 0)
-    CK(cudaFuncSetAttribute(mframes, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)march_smem(ctx->tbm_ring)));
+    CK(cudaFuncSetAttribute(mframes, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)march_smem(ctx->tbm_ring, 4)));
   const int npair = mframes ? C / 2 : 0;
   // per-step tables of the recomputation (frame t -> t+1), and per pair of
   // steps (frames 2p -> 2p+1 -> 2p+2), the same for every segment
@@ -1386,7 +1386,7 @@ int run_grad(fdtd_ctx* ctx, long long nsteps, const fdtd_source* src, int nsrc,
   const char* fe = getenv("FDTD_ADJ_FUSED");
   const bool fused = !(fe && atoi(fe) == 0);
   // Two reverse steps per launch (adj_march_kernel + adj_fix_kernel;
-  // FDTD_ADJ_TB2=0: one step per launch): kMarchCols x th2 tiles (th2 of
+  // FDTD_ADJ_TB2=0: one step per launch): (W x kMarchOut) x th2 tiles (th2 of
   // 8..64 rows filling whole waves of resident CTAs), per warp the edges
   // whose g_E after the first step it exports (the models' interface edges,
   // the source edges).

@@ -1110,6 +1110,7 @@ struct fdtd_ctx {
   int tbm_pf = 0;                  // rows prefetched ahead of the loads (FDTD_TB_PF: > 0 into L2, < 0 into L1)
   int tbm_mb = 4;                  // resident CTAs per SM the kernel is compiled for (FDTD_TB_MB)
   int tbm_ring = 0;                // rows staged ahead through shared memory (FDTD_TB_RING; 0: registers)
+  int tbm_w = 4;                   // warps per CTA, 3 or 4 (kMarchOut columns each)
   bool tbm_sparse = false;         // some simulation has a background material (sparse-material form)
   // configuration chosen by fdtd_autotune (0: the fixed rule or the
   // environment): one-step tile rows, row-marching tile rows, simulations per
@@ -1170,7 +1171,7 @@ void drop_graphs(fdtd_ctx* ctx) {
 
 // Plan of the two-steps-per-pass path: one tile per model whose output is
 // the model's zone (yee_tb2_kernel), and for the rest either the row-marching
-// kernel's kMarchCols x th tiles (default) or, with FDTD_TB_SMEM=1, ordinary
+// kernel's (W x kMarchOut) x th tiles (default) or, with FDTD_TB_SMEM=1, ordinary
 // kTbW x kTbH shared-memory tiles of yee_tb2_kernel (issue-bound: measured
 // 118 against 186 Gcell-steps/s for the one-step kernel at 4096^2); and the
 // zone lists.  The path is used only when every model fits the in-CTA model
@@ -1252,7 +1253,7 @@ int plan_tb(fdtd_ctx* ctx) {
     }
   ctx->tb_base.assign(ctx->sims.size(), 0);
   if (march) {
-    // kMarchCols x th tiles, 8 <= th <= 64; th fills whole waves of
+    // (W x kMarchOut) x th tiles, 8 <= th <= 64; th fills whole waves of
     // resident CTAs: minimise ceil(T / slots) * (th + 3) (three rows of
     // sub-step halo).  Fused model tiles run beside the first wave; each
     // takes the registers of two of this kernel's CTAs, so those slots are
@@ -1286,18 +1287,32 @@ int plan_tb(fdtd_ctx* ctx) {
     if (const char* eg = getenv("FDTD_TB_RING")) ctx->tbm_ring = std::min(4, std::max(0, atoi(eg)));
     if (ctx->ov_ring >= 0) ctx->tbm_ring = ctx->ov_ring;
     if (ctx->tbm_ring == 1 || ctx->tbm_mb == 3) ctx->tbm_ring = 0;
+    // 3 or 4 warps per CTA (kMarchOut columns each): whichever leaves fewer
+    // warps idle in the grids' last column blocks (FDTD_TB_WARPS overrides);
+    // 1024 columns are 9 warp columns: three CTAs of three warps
+    {
+      long long idle3 = 0, idle4 = 0;
+      for (const SimHost& sh : ctx->sims) {
+        const long long nwc = (sh.nx + kMarchOut - 1) / kMarchOut;
+        idle3 += ((nwc + 2) / 3 * 3 - nwc) * sh.ny;
+        idle4 += ((nwc + 3) / 4 * 4 - nwc) * sh.ny;
+      }
+      ctx->tbm_w = idle3 < idle4 ? 3 : 4;
+      if (const char* ew = getenv("FDTD_TB_WARPS")) ctx->tbm_w = atoi(ew) == 3 ? 3 : 4;
+    }
+    const int cw = kMarchOut * ctx->tbm_w;   // columns per CTA
     if (ctx->tbm_ring > 0)
       CK(cudaFuncSetAttribute(march_fn(4, ctx->tbm_ring, ctx->tbm_sparse),
-                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)march_smem(ctx->tbm_ring)));
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, march_fn(ctx->tbm_mb, ctx->tbm_ring, ctx->tbm_sparse), 128,
-                                                  march_smem(ctx->tbm_ring));
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)march_smem(ctx->tbm_ring, 4)));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, march_fn(ctx->tbm_mb, ctx->tbm_ring, ctx->tbm_sparse),
+                                                  32 * ctx->tbm_w, march_smem(ctx->tbm_ring, ctx->tbm_w));
     long long nfused = 0;
     for (size_t k = 0; k < ninst; ++k) nfused += chain[k] ? 0 : 1;
     const long long slots = std::max((long long)nsm, (long long)nsm * std::max(occ, 1) - 2 * nfused);
     auto tiles_for = [&](int th) {
       long long t = 0;
       for (const SimHost& sh : ctx->sims)
-        t += (long long)((sh.nx + kMarchCols - 1) / kMarchCols) * ((sh.ny + th - 1) / th);
+        t += (long long)((sh.nx + cw - 1) / cw) * ((sh.ny + th - 1) / th);
       return t;
     };
     int th = 8;
@@ -1320,13 +1335,13 @@ int plan_tb(fdtd_ctx* ctx) {
       const SimHost& sh = ctx->sims[s];
       ctx->tb_base[s] = (int)ctx->tbm_tiles.size();
       for (int y0 = 0; y0 < sh.ny; y0 += th)
-        for (int x0 = 0; x0 < sh.nx; x0 += kMarchCols) {
+        for (int x0 = 0; x0 < sh.nx; x0 += cw) {
           const TileWork t{s, x0, y0, std::min(y0 + th, sh.ny)};
           int2 zr{(int)ctx->tbm_zones.size(), 0};
           for (size_t k = 0; k < ctx->insts.size(); ++k) {
             if (ctx->insts[k].sim != s) continue;
             const int4 z = zone[k];
-            if (z.x < x0 + kMarchCols && z.z > x0 && z.y < t.y1 && z.w > t.y0) ctx->tbm_zones.push_back(z);
+            if (z.x < x0 + cw && z.z > x0 && z.y < t.y1 && z.w > t.y0) ctx->tbm_zones.push_back(z);
           }
           zr.y = (int)ctx->tbm_zones.size();
           ctx->tbm_tiles.push_back(t);
@@ -1756,7 +1771,8 @@ int prepare_run(fdtd_ctx* ctx, long long nsteps, const fdtd_source* src, int nsr
     std::vector<std::vector<SrcEdge>> ts(nt);
     std::vector<std::vector<int>> tp(nt);
     const int first_rom_tile = nt - (int)ctx->insts.size();
-    const int nw = ctx->tb_march ? 4 * (int)ctx->tbm_tiles.size() : 0;
+    const int W = ctx->tbm_w, cw = kMarchOut * W;
+    const int nw = ctx->tb_march ? W * (int)ctx->tbm_tiles.size() : 0;
     std::vector<std::vector<MarchSrc>> ms(nw);
     std::vector<std::vector<MarchPrb>> mq(nw);
     const int th = ctx->tbm_th;
@@ -1765,15 +1781,15 @@ int prepare_run(fdtd_ctx* ctx, long long nsteps, const fdtd_source* src, int nsr
       if (ctx->tb_march) {
         // every warp whose computed columns [c0 - 4, c0 + 124) and rows
         // [max(y0 - 2, 0), min(y1, ny)] hold the edge; c0 = 120 k
-        const int ncx = (sh.nx + kMarchCols - 1) / kMarchCols, ncy = (sh.ny + th - 1) / th;
+        const int ncx = (sh.nx + cw - 1) / cw, ncy = (sh.ny + th - 1) / th;
         for (int ty = std::max(0, e.j / th - 1); ty <= std::min(ncy - 1, (e.j + 2) / th); ++ty) {
           const int y0 = ty * th, y1 = std::min(y0 + th, sh.ny);
           if (e.j < std::max(y0 - 2, 0) || e.j > std::min(y1, sh.ny)) continue;
           for (int k = std::max(0, (e.i + 4) / kMarchOut - 1); k <= (e.i + 4) / kMarchOut; ++k) {
             const int c0 = kMarchOut * k;
             if (c0 >= sh.nx || e.i < c0 - 4 || e.i >= c0 + 124) continue;
-            const int t = ctx->tb_base[e.sim] + ty * ncx + k / 4;
-            ms[4 * t + k % 4].push_back({e.j, e.i, e.comp | (e.src << 1), 0.f});
+            const int t = ctx->tb_base[e.sim] + ty * ncx + k / W;
+            ms[W * t + k % W].push_back({e.j, e.i, e.comp | (e.src << 1), 0.f});
           }
         }
       } else {
@@ -1804,9 +1820,9 @@ int prepare_run(fdtd_ctx* ctx, long long nsteps, const fdtd_source* src, int nsr
       }
       const SimHost& sh = ctx->sims[sim];
       if (ctx->tb_march) {
-        const int ncx = (sh.nx + kMarchCols - 1) / kMarchCols;
-        const int t = ctx->tb_base[sim] + (j / th) * ncx + i / kMarchCols;
-        mq[4 * t + (i % kMarchCols) / kMarchOut].push_back({j, i, p, 0});
+        const int ncx = (sh.nx + cw - 1) / cw;
+        const int t = ctx->tb_base[sim] + (j / th) * ncx + i / cw;
+        mq[W * t + (i % cw) / kMarchOut].push_back({j, i, p, 0});
       } else {
         tp[ctx->tb_base[sim] + (j / kTbH) * ((sh.nx + kTbW - 1) / kTbW) + i / kTbW].push_back(p);
       }
@@ -1847,7 +1863,7 @@ int prepare_run(fdtd_ctx* ctx, long long nsteps, const fdtd_source* src, int nsr
         std::stable_sort(mq[w].begin(), mq[w].end(), [](const MarchPrb& a, const MarchPrb& b) { return a.j < b.j; });
         srng[w] = make_int2((int)fms.size(), (int)(fms.size() + ms[w].size()));
         fms.insert(fms.end(), ms[w].begin(), ms[w].end());
-        fsim.insert(fsim.end(), ms[w].size(), ctx->tbm_tiles[w / 4].sim);
+        fsim.insert(fsim.end(), ms[w].size(), ctx->tbm_tiles[w / W].sim);
         prng[w] = make_int2((int)fmq.size(), (int)(fmq.size() + mq[w].size()));
         fmq.insert(fmq.end(), mq[w].begin(), mq[w].end());
       }
@@ -2023,7 +2039,8 @@ void launch_tb(fdtd_ctx* ctx, cudaStream_t s, int par, int c, const TbTables& tt
     yee_tb2_kernel<<<ntb, kTbThreads, kTbSmemFields, s>>>(tt.sims, ctx->tb_tiles_d, tt.insts, tt.run, ctx->tb_run_d,
                                                           par, c);
   if (ctx->tb_march)   // overlaps the model tiles (programmatic serialisation) when there are any
-    launch_k(tt.march, (unsigned)ctx->tbm_tiles.size(), 128, march_smem(ctx->tbm_ring), s, ctx->pdl && ntb > 0,
+    launch_k(tt.march, (unsigned)ctx->tbm_tiles.size(), 32 * ctx->tbm_w, march_smem(ctx->tbm_ring, ctx->tbm_w), s,
+             ctx->pdl && ntb > 0,
              tt.sims, (const TileWork*)ctx->tbm_tiles_d, tt.run, (const TbMarchDev*)ctx->tbm_d, par, c, ctx->tbm_pf);
   if (ctx->tb_nchain > 0) cudaStreamWaitEvent(s, ctx->ev_join, 0);
 }
@@ -2795,8 +2812,8 @@ int fdtd_time_stencil(fdtd_ctx* ctx, int launches, int reps, double* ms_per_laun
   CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
   for (int k = 0; k < launches; ++k) {
     if (ctx->tb && ctx->tb_march)
-      launch_k(march_fn(ctx->tbm_mb, ctx->tbm_ring, ctx->tbm_sparse), (unsigned)ctx->tbm_tiles.size(), 128,
-               march_smem(ctx->tbm_ring), cs, false, (const SimDev*)ctx->sims_d, (const TileWork*)ctx->tbm_tiles_d, (const RunDev*)ctx->run_d,
+      launch_k(march_fn(ctx->tbm_mb, ctx->tbm_ring, ctx->tbm_sparse), (unsigned)ctx->tbm_tiles.size(), 32 * ctx->tbm_w,
+               march_smem(ctx->tbm_ring, ctx->tbm_w), cs, false, (const SimDev*)ctx->sims_d, (const TileWork*)ctx->tbm_tiles_d, (const RunDev*)ctx->run_d,
                (const TbMarchDev*)ctx->tbm_d, par, 0, ctx->tbm_pf);
     else if (ctx->tb && nord > 0)
       yee_tb2_kernel<<<nord, kTbThreads, kTbSmemFields, cs>>>(ctx->sims_d, ctx->tb_tiles_d, ctx->insts_d, ctx->run_d,

@@ -6,7 +6,9 @@
 // c0 - 4 + 4 l .. + 3, so the left two and right one halo columns that two
 // steps need are ordinary lane columns (lanes 0 and 31) and every neighbour
 // value comes from a shuffle; values in the outermost columns of lanes 0 and
-// 31 are wrong (their shuffles wrap) but nothing stored depends on them.
+// 31 are wrong (their shuffles wrap) but nothing stored depends on them.  A
+// CTA has W = 3 or 4 warps (blockDim.x / 32, the plan's choice: the fewer
+// idle warps in the grids' last column blocks) and a tile W x 120 columns.
 // Marching up the rows, iteration j computes
 //   A: row j of Hz^{n+1/2}, Ex^{n+1}, Ey^{n+1} from E^n, Hz^{n-1/2} (Eq. (5),
 //      then Eq. (3), sources J^n), and
@@ -30,7 +32,6 @@
 namespace {
 
 constexpr int kMarchOut = 120;                // output columns per warp
-constexpr int kMarchCols = 4 * kMarchOut;     // output columns per CTA (4 warps)
 
 struct MarchSrc {   // a driven edge within a warp's computed columns and rows
   int j, i;
@@ -254,7 +255,7 @@ yee_tb2m_kernel(const SimDev* __restrict__ sims, const TileWork* __restrict__ ti
   const int jA0 = j0 >= 2 ? j0 - 2 : 0, jAe = j1 < ny ? j1 : ny, jB0 = j0 >= 1 ? j0 - 1 : 0;
   const long long nA = run->base + 2 * (long long)c, nB = nA + 1;
   const int nprobe = run->nprobe;
-  const int wi = blockIdx.x * 4 + warp;
+  const int wi = blockIdx.x * (blockDim.x >> 5) + warp;
   const int2 sr = tm->src_rng[wi], pr = tm->prb_rng[wi], zr = tm->zone_rng[blockIdx.x];
   int kA = sr.x, kB = sr.x, pA = pr.x, pB = pr.x;
   while (kB < sr.y && tm->src[kB].j < jB0) ++kB;
@@ -490,7 +491,8 @@ MarchFn march_fn(int mb, int ring, bool sparse) {
     default: return sparse ? yee_tb2m_kernel<4, 0, true> : yee_tb2m_kernel<4, 0, false>;
   }
 }
-size_t march_smem(int ring) { return ring > 0 ? (size_t)ring * kMarchRingBytesPerRow : 0; }
+// Dynamic shared memory of a CTA of w warps (the ring of rows of each warp).
+size_t march_smem(int ring, int w) { return ring > 0 ? (size_t)ring * (kMarchRingBytesPerRow / 4) * w : 0; }
 
 // The form that also writes the intermediate E frame (sd.exm, sd.eym), for
 // the plans the gradient's recomputation supports (else null).
