@@ -233,7 +233,13 @@ int fdtd_run_host(fdtd_ctx* ctx, long long nsteps, const fdtd_source* src, int n
  * any of them may be NULL.  J_out: host double (may be NULL).  The context
  * ends in the state reached by the forward pass (as after fdtd_run).
  * Ring-cell gradients assume a nonsingular coupling (dual rule, or the paper
- * rule with a full-order model).  Synchronises. */
+ * rule with a full-order model).  The recomputation and the reverse sweep
+ * take two steps per launch where the context does; the reverse sweep then
+ * adds the model, probe and source terms of its second step afterwards as
+ * local corrections (FDTD_ADJ_TB2=0: one reverse step per launch), which
+ * changes the FP32 rounding at the cells beside the models and at the probes
+ * only; additions that meet in one cell or edge are atomic, so the last bit
+ * there can vary between calls.  Synchronises. */
 int fdtd_grad(fdtd_ctx* ctx, long long nsteps, const fdtd_source* src, int nsrc,
               const fdtd_probe* probes, int nprobe, int ckpt_every, float* dJ_deps,
               float* dJ_dsigma, float* dJ_dsrc, double* J_out);
