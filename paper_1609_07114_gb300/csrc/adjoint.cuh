@@ -685,7 +685,7 @@ struct AdjExp {     // an edge whose g_E after reverse step t is exported
 };
 
 struct AdjMarchDev {
-  const int2* exp_rng;   // per warp (tile * 4 + warp): [begin, end) into exp, rows ascending
+  const int2* exp_rng;   // per warp (tile * W + warp): [begin, end) into exp, rows ascending
   const AdjExp* exp;
   float* expv;           // the exported values, by slot
 };

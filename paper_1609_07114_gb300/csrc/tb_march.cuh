@@ -45,7 +45,7 @@ struct MarchPrb {   // a probe cell owned by a warp (outside every zone)
 };
 
 struct TbMarchDev {
-  const int2* src_rng;    // per warp (tile * 4 + warp): [begin, end) into src, rows ascending
+  const int2* src_rng;    // per warp (tile * W + warp): [begin, end) into src, rows ascending
   const MarchSrc* src;
   const int2* prb_rng;    // per warp: [begin, end) into prb, rows ascending
   const MarchPrb* prb;
